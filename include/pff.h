@@ -1,0 +1,209 @@
+/*
+ * pff.h -- C ABI of the GB300 solver for pressurized phase-field fracture.
+ *
+ * The library solves, on one GPU, the loading steps of Formulation 1 of
+ * Heister & Wick (arXiv 1806.09924, Section 2): displacements u and a phase
+ * field phi on a tensor-product Q1 mesh (Section 3), with the irreversibility
+ * constraint phi <= phi_old, by the combined semi-smooth Newton / primal-dual
+ * active-set method of Section 3 whose linear systems are solved by FGMRES with
+ * the block-diagonal preconditioner of Section 3.1 (one smoothed-aggregation
+ * AMG V-cycle per diagonal block).  The crack functionals TCV and COD of
+ * Section 4 are evaluated on the device.
+ *
+ * Conventions shared by every entry point
+ *   - Return value: PFF_OK (0) on success, a negative PFF_ERR_* code on failure;
+ *     pff_last_error() then returns a thread-local message.  A failed call
+ *     leaves the problem usable unless the code is PFF_ERR_CUDA.
+ *   - Ownership: a pff_problem is created and owned by the library and holds
+ *     all its state in device memory until pff_destroy.  Input arrays are
+ *     copied, never retained.  Output arrays are owned by the caller.
+ *   - "host" pointers point to CPU memory; "_dev" entry points take pointers
+ *     to device memory of the current CUDA device (for example tensors
+ *     allocated by PyTorch) and enqueue work on the problem's stream without
+ *     synchronizing.  All other entry points synchronize the stream before
+ *     they return.
+ *   - Layout: node (i,j,k) has index i + (nx+1)(j + (ny+1)k) (x fastest);
+ *     u is [n_nodes][dim] row-major; phi, phi_old are [n_nodes].  A full
+ *     solution / residual vector is [u (dim*n_nodes) ; phi (n_nodes)], the
+ *     basis order of Section 3.1 (all displacement DoFs, then the phase field).
+ *   - Thread safety: calls on one problem must not overlap; distinct problems
+ *     are independent.
+ */
+#ifndef PFF_H
+#define PFF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PFF_OK 0
+#define PFF_ERR_INVALID_ARG (-1)   /* bad size, pointer, option or call order */
+#define PFF_ERR_OOM (-2)           /* device allocation failed */
+#define PFF_ERR_NOT_CONVERGED (-3) /* Newton or Krylov iteration cap reached */
+#define PFF_ERR_LINESEARCH (-4)    /* reserved: line-search failures are reported, not fatal */
+#define PFF_ERR_CYCLE (-5)         /* reserved: active-set locks are reported, not fatal */
+#define PFF_ERR_NAN (-6)           /* a NaN / Inf appeared in a residual or norm */
+#define PFF_ERR_TIMEOUT (-7)       /* a bounded device-side wait gave up */
+#define PFF_ERR_CUDA (-8)          /* CUDA runtime error; the problem may be unusable */
+#define PFF_ERR_CAPACITY (-9)      /* an internal fixed-size table overflowed */
+
+#define PFF_PREC_FP64 0   /* FP64 everywhere */
+#define PFF_PREC_MIXED 1  /* FP32 AMG preconditioner inside FP64 FGMRES / Newton */
+
+#define PFF_APPLY_AUTO 0        /* pick the faster FP64 Jacobian apply (timed once) */
+#define PFF_APPLY_ASSEMBLED 1   /* stencil-assembled Section 3.1 blocks */
+#define PFF_APPLY_MATFREE 2     /* matrix-free element-batched apply */
+
+#define PFF_PC_AMG 0     /* block-diagonal preconditioner, one SA-AMG V-cycle per block */
+#define PFF_PC_JACOBI 1  /* point Jacobi (diagnostics only) */
+
+typedef struct pff_problem pff_problem;
+
+/* Solver options.  pff_default_options fills the defaults given here. */
+typedef struct pff_options {
+  int precision;        /* PFF_PREC_FP64 (default) or PFF_PREC_MIXED */
+  double c;             /* active-set constant c > 0 (Section 3 algorithm, step 2); 1 */
+  double tol_newton;    /* stop when the scaled reduced residual (inf-norm) fell by this; 1e-10 */
+  double tol_step;      /* ... and the last Newton step is below this, relative per block; 1e-9 */
+  double tol_linear;    /* FGMRES relative residual (Table 1 uses 1e-8); 1e-8 */
+  int max_newton;       /* Newton / active-set iterations per loading step; 50 */
+  int max_halvings;     /* line-search halvings; 10 */
+  int cycle_lock;       /* lock an index active after this many membership changes; 3 */
+  int krylov_restart;   /* FGMRES restart length m; 40 */
+  int max_krylov;       /* FGMRES iterations per linear solve; 600 */
+  int cheb_degree;      /* Chebyshev smoother degree; 2 */
+  double amg_theta;     /* strength-of-connection threshold; 0.08 */
+  int amg_coarse_max;   /* largest coarse level (scalar rows) solved directly; 320 */
+  int apply_variant;    /* PFF_APPLY_*; PFF_APPLY_AUTO */
+  int precond;          /* PFF_PC_*; PFF_PC_AMG */
+  int reserved[8];
+} pff_options;
+
+/* Per loading step (or per Newton iteration for pff_newton_step) report. */
+typedef struct pff_step_report {
+  int status;           /* PFF_OK or the error code of the step */
+  int converged;        /* 1 when the stopping test of the Section 3 algorithm held */
+  int newton_its;       /* Newton / active-set iterations taken */
+  int krylov_its;       /* total FGMRES iterations */
+  int krylov_its_max;   /* largest FGMRES iteration count of one Newton step (cf. Table 1) */
+  int active;           /* size of the final active set */
+  int changed;          /* active-set changes in the last iteration */
+  int locked;           /* indices locked active by the cycle rule */
+  int ties;             /* nodes whose active-set indicator is within round-off of 0 */
+  int linesearch_fails; /* line searches that fell back to the full step */
+  double rho0;          /* scaled reduced residual (inf-norm) at the first iteration */
+  double rho;           /* ... at the last iteration */
+  double time_ms;       /* wall time of the step */
+} pff_step_report;
+
+void pff_default_options(pff_options* opts);
+
+/* Mesh and problem set-up -------------------------------------------------- */
+
+/* Tensor-product Q1 mesh of the box spanned by axis_coords (Section 3: Q1^c on
+ * quadrilaterals / hexahedra).  dim is 2 or 3; n_cells[a] >= 1 cells along
+ * axis a; axis_coords[a] points to n_cells[a]+1 strictly increasing host
+ * doubles (copied).  Homogeneous Dirichlet conditions on u at the whole outer
+ * boundary (Section 2).  Initial state: u = 0, phi = phi_old = 1.
+ * *out receives the new problem (owned by the library until pff_destroy). */
+int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_coords,
+                    pff_problem** out);
+
+/* Material of Formulation 1 (Section 2): Young's modulus E > 0, Poisson ratio
+ * 0 <= nu < 0.5 (Lame coefficients; plane strain in 2d), critical energy
+ * release rate G_c > 0, stiffness floor kappa >= 0, regularization eps > 0. */
+int pff_set_material(pff_problem* prob, double E, double nu, double Gc, double kappa, double eps);
+
+/* Start a loading step with constant pressure p (Section 4 uses p = 1e-3):
+ * forms the extrapolation phi~ (phi_old in the first step, clamp(2 phi_old -
+ * phi_prev, 0, 1) afterwards) and resets the per-step Newton state. */
+int pff_set_pressure(pff_problem* prob, double p);
+
+/* Crack of half length / radius l0 centred at the origin (Section 4): phi =
+ * phi_old = 0 on all nodes of cells cut by the segment |x| < l0, y = 0 (2d)
+ * or the disc x^2+y^2 < l0^2, z = 0 (3d), 1 elsewhere; u = 0; history reset. */
+int pff_set_crack(pff_problem* prob, double l0);
+
+/* General state (host arrays, copied; NULL keeps the current value).
+ * steps_done = number of completed loading steps (selects phi~). */
+int pff_set_state(pff_problem* prob, const double* u, const double* phi, const double* phi_old,
+                  const double* phi_prev, int steps_done);
+
+/* Solver entry points ------------------------------------------------------ */
+
+/* One iteration of the Section 3 algorithm within the current loading step:
+ * residual, active set, reduced Jacobian, FGMRES solve, line search, update.
+ * report->converged = 1 (and no update) once the stopping test holds. */
+int pff_newton_step(pff_problem* prob, const pff_options* opts, pff_step_report* report);
+
+/* Finish the current loading step: phi_prev <- phi_old, phi_old <- phi. */
+int pff_end_loading_step(pff_problem* prob);
+
+/* Solve n_steps loading steps with pressures p_schedule[0..n_steps-1] (host),
+ * each to convergence; reports[n_steps] (host, caller-owned) may be NULL.
+ * Returns PFF_ERR_NOT_CONVERGED if a step hit max_newton (reports say which). */
+int pff_solve_loading_steps(pff_problem* prob, int n_steps, const double* p_schedule,
+                            const pff_options* opts, pff_step_report* reports);
+
+/* TCV_h = int u . grad phi over the domain and the crack opening
+ * COD_h = int u . grad phi along lines normal to the crack (Section 4).
+ * pts: n_pts abscissae x (2d) or (x, y) pairs (3d), host; a point on a mesh
+ * line averages the adjacent cells.  tcv (1 double) and cod (n_pts doubles)
+ * are host outputs; either may be NULL. */
+int pff_eval_tcv_cod(pff_problem* prob, int n_pts, const double* pts, double* tcv, double* cod);
+
+/* Copy the state out to host arrays (any may be NULL): u [n_nodes*dim],
+ * phi [n_nodes], active [n_nodes] (1 = phase-field index in the last active set). */
+int pff_get_solution(pff_problem* prob, double* u, double* phi, uint8_t* active);
+
+/* Use this CUDA stream (a cudaStream_t, e.g. torch.cuda.current_stream()) for
+ * all later work of the problem; NULL selects the legacy default stream. */
+int pff_set_stream(pff_problem* prob, void* stream);
+
+int pff_get_sizes(const pff_problem* prob, int* dim, int64_t* n_nodes, int64_t* n_dofs);
+
+void pff_destroy(pff_problem* prob);
+
+const char* pff_last_error(void);
+
+/* Component entry points (device pointers, asynchronous on the problem's
+ * stream).  They expose the steps of the hot path one by one for parity tests
+ * and benchmarks; all vectors use the full [u ; phi] layout of n_dofs doubles. */
+
+/* F = -r(U): Eq. (E22ATW) and (E33ATW) tested with every basis function at the
+ * current state, pressure and phi~ (no elimination). */
+int pff_residual_dev(pff_problem* prob, double* F_dev);
+
+/* Active set of the Section 3 algorithm (step 2) at the current state:
+ * indicator[i] = F_phi,i / m_i + c (phi_i - phi_old,i) with the lumped mass m;
+ * active[i] = indicator > 0.  Stores the set in the problem (used by the
+ * reduced Jacobian below).  Either output may be NULL. */
+int pff_active_set_dev(pff_problem* prob, double c, uint8_t* active_dev, double* indicator_dev);
+
+/* Assemble the Section 3.1 Jacobian blocks (M_uu, M_phi_u, M_phi_phi) at the
+ * current state in the node-stencil format, reduced by the Dirichlet set and
+ * the stored active set. */
+int pff_assemble(pff_problem* prob);
+
+/* y = G~ x, the reduced Jacobian (identity rows and zero columns for Dirichlet
+ * displacement DoFs and active phase-field DoFs; M_u_phi = 0).  variant:
+ * PFF_APPLY_ASSEMBLED (needs pff_assemble) or PFF_APPLY_MATFREE. */
+int pff_apply_jacobian_dev(pff_problem* prob, int variant, const double* x_dev, double* y_dev);
+
+/* Build the block-diagonal SA-AMG preconditioner of the assembled blocks and
+ * apply it: z = diag(V_uu, V_phiphi) r (one V-cycle per block). */
+int pff_precond_setup(pff_problem* prob, const pff_options* opts);
+int pff_precond_apply_dev(pff_problem* prob, const double* r_dev, double* z_dev);
+
+/* Solve G~ x = b with preconditioned FGMRES (relative tolerance tol_linear on
+ * the Jacobi-scaled residual).  *iters receives the iteration count. */
+int pff_linear_solve_dev(pff_problem* prob, const pff_options* opts, const double* b_dev,
+                         double* x_dev, int* iters);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PFF_H */

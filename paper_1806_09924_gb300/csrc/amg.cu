@@ -1,0 +1,1148 @@
+// Smoothed-aggregation algebraic multigrid, built and applied on the device.
+//
+// Section 3.1 preconditions each diagonal block (M_uu: linear elasticity;
+// M_phi_phi: mass + Laplacian) with one AMG V-cycle.  The paper uses Trilinos
+// ML; this is an independent GPU design:
+//   setup (per level, all on the device, deterministic):
+//     1. strength graph: block (I,J) is strong iff ||A_IJ||_F^2 > theta^2
+//        ||A_II||_F ||A_JJ||_F, symmetrized; rows without strong off-diagonal
+//        blocks (Dirichlet / active identity rows, kappa-degenerate crack
+//        nodes) are isolated and left to the smoother
+//     2. aggregation: distance-2 maximal independent set (hash-keyed parallel
+//        MIS(2)) as roots; every node joins the root it is most strongly
+//        connected to, or else the aggregate of its most strongly connected
+//        neighbour
+//     3. tentative prolongator: per-aggregate thin QR (modified Gram-Schmidt,
+//        twice) of the near-null space (rigid-body modes / constants); R gives
+//        the coarse near-null space
+//     4. P = (I - omega D^-1 A) P_tent, omega = 4 / (3 lambda_max(D^-1 A))
+//     5. R = P^T, A_c = R A P (two row-wise SpGEMMs with sorted unique columns)
+//     6. coarsest level: dense inverse (Gauss-Jordan with partial pivoting)
+//   V-cycle: Chebyshev(D^-1 A) pre/post smoothing, restriction, coarse solve,
+//   prolongation; FP64 or FP32 (mixed precision) values and vectors.
+#include <algorithm>
+#include <cmath>
+
+#include "pff_internal.h"
+
+namespace pff {
+
+namespace {
+
+constexpr int CAP = 512;   // per-row unique-column capacity of the setup SpGEMMs
+
+enum : int { ST_OUT = 0, ST_UND = 1, ST_IN = 2 };
+
+__device__ __forceinline__ uint32_t hash32(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+__device__ __forceinline__ unsigned long long mis_key(int state, int i) {
+  return ((unsigned long long)state << 62) |
+         ((unsigned long long)(hash32((uint32_t)i) & 0x3fffffffU) << 32) | (unsigned)i;
+}
+
+// -------------------------------------------------------------- diagonals --
+__global__ void k_diag(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
+                       const double* __restrict__ val, double* __restrict__ dnorm,
+                       double* __restrict__ dinv, int* __restrict__ err) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  int kd = -1;
+  for (int k = rp[I]; k < rp[I + 1]; ++k)
+    if (col[k] == I) {
+      kd = k;
+      break;
+    }
+  if (kd < 0) {
+    atomicExch(err, 1);
+    dnorm[I] = 0.0;
+    for (int a = 0; a < b; ++a) dinv[(int64_t)I * b + a] = 0.0;
+    return;
+  }
+  const double* v = val + (int64_t)kd * b * b;
+  double s = 0.0;
+  for (int e = 0; e < b * b; ++e) s += v[e] * v[e];
+  dnorm[I] = sqrt(s);
+  for (int a = 0; a < b; ++a) {
+    const double dv = v[a * b + a];
+    dinv[(int64_t)I * b + a] = dv != 0.0 ? 1.0 / dv : 0.0;
+  }
+}
+
+// ---------------------------------------------------------------- strength --
+__global__ void k_strength(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ dnorm,
+                           double theta2, uint8_t* __restrict__ strong, double* __restrict__ snorm) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int J = col[k];
+    const double* v = val + (int64_t)k * b * b;
+    double s = 0.0;
+    for (int e = 0; e < b * b; ++e) s += v[e] * v[e];
+    snorm[k] = s;
+    strong[k] = (J != I) && (s > theta2 * dnorm[I] * dnorm[J]);
+  }
+}
+
+__device__ __forceinline__ int find_col(const int* __restrict__ col, int lo, int hi, int c) {
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    const int v = col[mid];
+    if (v == c) return mid;
+    if (v < c) lo = mid + 1;
+    else hi = mid;
+  }
+  return -1;
+}
+
+// union with the transpose: out[k] = in[k] | in[k^T]
+__global__ void k_symmetrize(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                             const uint8_t* __restrict__ in, uint8_t* __restrict__ out) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int J = col[k];
+    uint8_t s = in[k];
+    if (!s && J != I) {
+      const int kt = find_col(col, rp[J], rp[J + 1], I);
+      if (kt >= 0) s = in[kt];
+    }
+    out[k] = s;
+  }
+}
+
+// -------------------------------------------------------------------- MIS --
+__global__ void k_mis_init(int n, const int* __restrict__ rp, const uint8_t* __restrict__ strong,
+                           int* __restrict__ state, uint8_t* __restrict__ iso) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  bool any = false;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) any |= strong[k] != 0;
+  iso[I] = !any;
+  state[I] = any ? ST_UND : ST_OUT;
+}
+
+__global__ void k_mis_max1(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                           const uint8_t* __restrict__ strong, const int* __restrict__ state,
+                           unsigned long long* __restrict__ M1) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  unsigned long long m = mis_key(state[I], I);
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    if (!strong[k]) continue;
+    const int J = col[k];
+    const unsigned long long kj = mis_key(state[J], J);
+    m = kj > m ? kj : m;
+  }
+  M1[I] = m;
+}
+
+__global__ void k_mis_max2(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                           const uint8_t* __restrict__ strong,
+                           const unsigned long long* __restrict__ M1,
+                           unsigned long long* __restrict__ M2) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  unsigned long long m = M1[I];
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    if (!strong[k]) continue;
+    const unsigned long long kj = M1[col[k]];
+    m = kj > m ? kj : m;
+  }
+  M2[I] = m;
+}
+
+__global__ void k_mis_decide(int n, int* __restrict__ state, const unsigned long long* __restrict__ M2,
+                             int* __restrict__ undecided) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  if (state[I] != ST_UND) return;
+  const unsigned long long me = mis_key(ST_UND, I);
+  if (M2[I] == me) state[I] = ST_IN;
+  else if ((int)(M2[I] >> 62) == ST_IN) state[I] = ST_OUT;
+  else atomicAdd(undecided, 1);
+}
+
+__global__ void k_root_flags(int n, const int* __restrict__ state, int* __restrict__ flag) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I < n) flag[I] = state[I] == ST_IN;
+}
+
+// pass 1: roots keep their id; neighbours join the most strongly connected root
+__global__ void k_agg_pass1(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                            const uint8_t* __restrict__ strong, const double* __restrict__ snorm,
+                            const int* __restrict__ state, const uint8_t* __restrict__ iso,
+                            const int* __restrict__ rootid, int* __restrict__ agg1) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  if (iso[I]) {
+    agg1[I] = -1;
+    return;
+  }
+  if (state[I] == ST_IN) {
+    agg1[I] = rootid[I];
+    return;
+  }
+  int best = -1;
+  double bs = -1.0;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    if (!strong[k]) continue;
+    const int J = col[k];
+    if (state[J] != ST_IN) continue;
+    if (snorm[k] > bs || (snorm[k] == bs && J < best)) {
+      bs = snorm[k];
+      best = J;
+    }
+  }
+  agg1[I] = best >= 0 ? rootid[best] : -2;
+}
+
+// pass 2: the rest join the aggregate of their most strongly connected assigned neighbour
+__global__ void k_agg_pass2(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                            const uint8_t* __restrict__ strong, const double* __restrict__ snorm,
+                            const int* __restrict__ agg1, int* __restrict__ agg) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  const int a = agg1[I];
+  if (a != -2) {
+    agg[I] = a;
+    return;
+  }
+  int best = -1, ba = -1;
+  double bs = -1.0;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    if (!strong[k]) continue;
+    const int J = col[k];
+    const int aj = agg1[J];
+    if (aj < 0) continue;
+    if (snorm[k] > bs || (snorm[k] == bs && J < best)) {
+      bs = snorm[k];
+      best = J;
+      ba = aj;
+    }
+  }
+  agg[I] = ba;   // -1 (isolated) if nothing was found
+}
+
+__global__ void k_count_members(int n, const int* __restrict__ agg, int* __restrict__ cnt) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  if (agg[I] >= 0) atomicAdd(&cnt[agg[I]], 1);
+}
+
+__global__ void k_fill_members(int n, const int* __restrict__ agg, const int* __restrict__ off,
+                               int* __restrict__ cursor, int* __restrict__ members) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  const int a = agg[I];
+  if (a < 0) return;
+  const int p = atomicAdd(&cursor[a], 1);
+  members[off[a] + p] = I;
+}
+
+__global__ void k_sort_segments(int nseg, const int* __restrict__ off, int* __restrict__ key,
+                                int* __restrict__ aux) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nseg) return;
+  const int lo = off[a], hi = off[a + 1];
+  for (int i = lo + 1; i < hi; ++i) {
+    const int k = key[i];
+    const int x = aux ? aux[i] : 0;
+    int j = i - 1;
+    while (j >= lo && key[j] > k) {
+      key[j + 1] = key[j];
+      if (aux) aux[j + 1] = aux[j];
+      --j;
+    }
+    key[j + 1] = k;
+    if (aux) aux[j + 1] = x;
+  }
+}
+
+// Tentative prolongator: per aggregate, QR of the near-null space rows.
+// Q -> Qn[I][r][j] (node-blocked, br x nns), R -> Bc (column-major, ld = nagg*nns)
+__global__ void k_tentative(int nagg, int br, int nns, const int* __restrict__ off,
+                            const int* __restrict__ members, const double* __restrict__ B,
+                            int64_t ldB, double* __restrict__ Qn, double* __restrict__ Bc,
+                            int64_t ldc) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nagg) return;
+  const int lo = off[a], hi = off[a + 1];
+  // copy B rows into Q storage
+  for (int t = lo; t < hi; ++t) {
+    const int I = members[t];
+    for (int r = 0; r < br; ++r)
+      for (int j = 0; j < nns; ++j)
+        Qn[((int64_t)I * br + r) * nns + j] = B[(int64_t)j * ldB + (int64_t)I * br + r];
+  }
+  double R[6][6];
+  for (int i = 0; i < 6; ++i)
+    for (int j = 0; j < 6; ++j) R[i][j] = 0.0;
+  for (int j = 0; j < nns; ++j) {
+    double n0 = 0.0;
+    for (int t = lo; t < hi; ++t)
+      for (int r = 0; r < br; ++r) {
+        const double v = Qn[((int64_t)members[t] * br + r) * nns + j];
+        n0 += v * v;
+      }
+    n0 = sqrt(n0);
+    for (int pass = 0; pass < 2; ++pass) {
+      for (int k = 0; k < j; ++k) {
+        double dot = 0.0;
+        for (int t = lo; t < hi; ++t)
+          for (int r = 0; r < br; ++r) {
+            const double* q = Qn + ((int64_t)members[t] * br + r) * nns;
+            dot += q[k] * q[j];
+          }
+        R[k][j] += dot;
+        for (int t = lo; t < hi; ++t)
+          for (int r = 0; r < br; ++r) {
+            double* q = Qn + ((int64_t)members[t] * br + r) * nns;
+            q[j] -= dot * q[k];
+          }
+      }
+    }
+    double nj = 0.0;
+    for (int t = lo; t < hi; ++t)
+      for (int r = 0; r < br; ++r) {
+        const double v = Qn[((int64_t)members[t] * br + r) * nns + j];
+        nj += v * v;
+      }
+    nj = sqrt(nj);
+    const bool dead = !(nj > 1e-10 * n0) || n0 == 0.0;
+    R[j][j] = dead ? 0.0 : nj;
+    const double sc = dead ? 0.0 : 1.0 / nj;
+    for (int t = lo; t < hi; ++t)
+      for (int r = 0; r < br; ++r) Qn[((int64_t)members[t] * br + r) * nns + j] *= sc;
+    if (dead)
+      for (int k = 0; k < j; ++k) R[k][j] = 0.0;
+  }
+  for (int k = 0; k < nns; ++k)
+    for (int j = 0; j < nns; ++j) Bc[(int64_t)j * ldc + (int64_t)a * nns + k] = R[k][j];
+}
+
+__global__ void k_zero_rows(int n, int stride, const int* __restrict__ agg, double* __restrict__ Qn) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n || agg[I] >= 0) return;
+  for (int e = 0; e < stride; ++e) Qn[(int64_t)I * stride + e] = 0.0;
+}
+
+// insert c into the sorted list u[0..*len) if absent; false on overflow
+__device__ __forceinline__ bool insert_unique(int* u, int& len, int c) {
+  int lo = 0, hi = len;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (u[mid] < c) lo = mid + 1;
+    else hi = mid;
+  }
+  if (lo < len && u[lo] == c) return true;
+  if (len >= CAP) return false;
+  for (int j = len; j > lo; --j) u[j] = u[j - 1];
+  u[lo] = c;
+  ++len;
+  return true;
+}
+
+// P = (I - omega D^-1 A) P_tent: count unique aggregate columns per row
+__global__ void k_P_count(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                          const int* __restrict__ agg, int* __restrict__ cnt, int* __restrict__ err) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  int u[CAP];
+  int len = 0;
+  bool ok = true;
+  if (agg[I] >= 0) ok &= insert_unique(u, len, agg[I]);
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int a = agg[col[k]];
+    if (a >= 0) ok &= insert_unique(u, len, a);
+  }
+  if (!ok) atomicExch(err, 2);
+  cnt[I] = len;
+}
+
+__global__ void k_P_fill(int n, int br, int nns, const int* __restrict__ rp,
+                         const int* __restrict__ col, const double* __restrict__ val,
+                         const int* __restrict__ agg, const double* __restrict__ Qn,
+                         const double* __restrict__ dinv, double omega,
+                         const int* __restrict__ prp, int* __restrict__ pcol,
+                         double* __restrict__ pval) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  int u[CAP];
+  int len = 0;
+  if (agg[I] >= 0) insert_unique(u, len, agg[I]);
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int a = agg[col[k]];
+    if (a >= 0) insert_unique(u, len, a);
+  }
+  const int base = prp[I];
+  const int bs = br * nns;
+  for (int p = 0; p < len; ++p) {
+    pcol[base + p] = u[p];
+    double* dst = pval + (int64_t)(base + p) * bs;
+    for (int e = 0; e < bs; ++e) dst[e] = 0.0;
+  }
+  if (agg[I] >= 0) {
+    const int p = find_col(pcol, base, base + len, agg[I]);
+    if (p < 0) return;   // capacity overflow, reported by k_P_count
+    double* dst = pval + (int64_t)p * bs;
+    for (int e = 0; e < bs; ++e) dst[e] = Qn[(int64_t)I * bs + e];
+  }
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int J = col[k];
+    const int a = agg[J];
+    if (a < 0) continue;
+    const int p = find_col(pcol, base, base + len, a);
+    if (p < 0) continue;
+    double* dst = pval + (int64_t)p * bs;
+    const double* Ablk = val + (int64_t)k * br * br;
+    const double* Q = Qn + (int64_t)J * bs;
+    for (int r = 0; r < br; ++r) {
+      const double w = omega * dinv[(int64_t)I * br + r];
+      for (int j = 0; j < nns; ++j) {
+        double s = 0.0;
+        for (int c = 0; c < br; ++c) s += Ablk[r * br + c] * Q[c * nns + j];
+        dst[r * nns + j] -= w * s;
+      }
+    }
+  }
+}
+
+// transpose: count entries per column
+__global__ void k_T_count(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                          int* __restrict__ cnt) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) atomicAdd(&cnt[col[k]], 1);
+}
+
+__global__ void k_T_fill(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                         const int* __restrict__ trp, int* __restrict__ cursor,
+                         int* __restrict__ tcol, int* __restrict__ src) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int c = col[k];
+    const int p = trp[c] + atomicAdd(&cursor[c], 1);
+    tcol[p] = I;
+    src[p] = k;
+  }
+}
+
+__global__ void k_T_vals(int64_t nnz, int br, int bc, const int* __restrict__ src,
+                         const double* __restrict__ val, double* __restrict__ tval) {
+  const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= nnz) return;
+  const double* s = val + (int64_t)src[p] * br * bc;   // br x bc
+  double* d = tval + p * bc * br;                       // bc x br
+  for (int r = 0; r < br; ++r)
+    for (int c = 0; c < bc; ++c) d[c * br + r] = s[r * bc + c];
+}
+
+// C = X Y, row-wise with sorted unique columns
+__global__ void k_mm_count(int n, const int* __restrict__ xrp, const int* __restrict__ xcol,
+                           const int* __restrict__ yrp, const int* __restrict__ ycol,
+                           int* __restrict__ cnt, int* __restrict__ err) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  int u[CAP];
+  int len = 0;
+  bool ok = true;
+  for (int k = xrp[I]; k < xrp[I + 1]; ++k) {
+    const int K = xcol[k];
+    for (int l = yrp[K]; l < yrp[K + 1]; ++l) ok &= insert_unique(u, len, ycol[l]);
+  }
+  if (!ok) atomicExch(err, 3);
+  cnt[I] = len;
+}
+
+__global__ void k_mm_fill(int n, int xr, int xc, int yc, const int* __restrict__ xrp,
+                          const int* __restrict__ xcol, const double* __restrict__ xval,
+                          const int* __restrict__ yrp, const int* __restrict__ ycol,
+                          const double* __restrict__ yval, const int* __restrict__ crp,
+                          int* __restrict__ ccol, double* __restrict__ cval) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  int u[CAP];
+  int len = 0;
+  for (int k = xrp[I]; k < xrp[I + 1]; ++k) {
+    const int K = xcol[k];
+    for (int l = yrp[K]; l < yrp[K + 1]; ++l) insert_unique(u, len, ycol[l]);
+  }
+  const int base = crp[I];
+  const int bs = xr * yc;
+  for (int p = 0; p < len; ++p) {
+    ccol[base + p] = u[p];
+    for (int e = 0; e < bs; ++e) cval[(int64_t)(base + p) * bs + e] = 0.0;
+  }
+  for (int k = xrp[I]; k < xrp[I + 1]; ++k) {
+    const int K = xcol[k];
+    const double* X = xval + (int64_t)k * xr * xc;
+    for (int l = yrp[K]; l < yrp[K + 1]; ++l) {
+      const int p = find_col(ccol, base, base + len, ycol[l]);
+      if (p < 0) continue;   // capacity overflow, reported by k_mm_count
+      const double* Y = yval + (int64_t)l * xc * yc;
+      double* C = cval + (int64_t)p * bs;
+      for (int r = 0; r < xr; ++r)
+        for (int c = 0; c < yc; ++c) {
+          double s = 0.0;
+          for (int m = 0; m < xc; ++m) s += X[r * xc + m] * Y[m * yc + c];
+          C[r * yc + c] += s;
+        }
+    }
+  }
+}
+
+// zero diagonal entries (dead coarse DoFs) -> 1
+__global__ void k_fix_diag(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
+                           double* __restrict__ val) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  const int k = find_col(col, rp[I], rp[I + 1], I);
+  if (k < 0) return;
+  double* v = val + (int64_t)k * b * b;
+  for (int a = 0; a < b; ++a) {
+    bool zero_row = true;
+    for (int kk = rp[I]; kk < rp[I + 1] && zero_row; ++kk)
+      for (int c = 0; c < b; ++c)
+        if (val[(int64_t)kk * b * b + a * b + c] != 0.0) zero_row = false;
+    if (zero_row) v[a * b + a] = 1.0;
+  }
+}
+
+__global__ void k_densify(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
+                          const double* __restrict__ val, double* __restrict__ D, int ld) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int J = col[k];
+    for (int r = 0; r < b; ++r)
+      for (int c = 0; c < b; ++c)
+        D[(int64_t)(I * b + r) * ld + J * b + c] = val[(int64_t)k * b * b + r * b + c];
+  }
+}
+
+// Gauss-Jordan inverse with partial pivoting, one block (n small)
+__global__ void k_gauss_jordan(int n, double* __restrict__ A, double* __restrict__ Inv,
+                               int* __restrict__ err) {
+  __shared__ int piv;
+  __shared__ double pmax[256];
+  __shared__ int pidx[256];
+  const int t = threadIdx.x;
+  for (int e = t; e < n * n; e += blockDim.x) Inv[e] = (e / n == e % n) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    double best = -1.0;
+    int bi = k;
+    for (int r = k + t; r < n; r += blockDim.x) {
+      const double v = fabs(A[(int64_t)r * n + k]);
+      if (v > best) {
+        best = v;
+        bi = r;
+      }
+    }
+    pmax[t] = best;
+    pidx[t] = bi;
+    __syncthreads();
+    if (t == 0) {
+      double b = -1.0;
+      int bb = k;
+      for (int j = 0; j < (int)blockDim.x; ++j)
+        if (pmax[j] > b || (pmax[j] == b && pidx[j] < bb)) {
+          b = pmax[j];
+          bb = pidx[j];
+        }
+      piv = bb;
+      if (!(b > 0.0)) atomicExch(err, 4);
+    }
+    __syncthreads();
+    const int p = piv;
+    if (p != k) {
+      for (int c = t; c < n; c += blockDim.x) {
+        double x = A[(int64_t)k * n + c];
+        A[(int64_t)k * n + c] = A[(int64_t)p * n + c];
+        A[(int64_t)p * n + c] = x;
+        x = Inv[(int64_t)k * n + c];
+        Inv[(int64_t)k * n + c] = Inv[(int64_t)p * n + c];
+        Inv[(int64_t)p * n + c] = x;
+      }
+    }
+    __syncthreads();
+    const double dk = A[(int64_t)k * n + k];
+    const double inv = dk != 0.0 ? 1.0 / dk : 0.0;
+    __syncthreads();
+    for (int c = t; c < n; c += blockDim.x) {
+      A[(int64_t)k * n + c] *= inv;
+      Inv[(int64_t)k * n + c] *= inv;
+    }
+    __syncthreads();
+    for (int e = t; e < n * n; e += blockDim.x) {
+      const int r = e / n, c = e % n;
+      if (r == k) continue;
+      const double f = A[(int64_t)r * n + k];
+      if (c != k) A[(int64_t)r * n + c] -= f * A[(int64_t)k * n + c];
+      Inv[(int64_t)r * n + c] -= f * Inv[(int64_t)k * n + c];
+    }
+    __syncthreads();
+    for (int r = t; r < n; r += blockDim.x)
+      if (r != k) A[(int64_t)r * n + k] = 0.0;
+    __syncthreads();
+  }
+}
+
+// power-iteration step: y = D^-1 A x
+__global__ void k_dinv_spmv(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ val, const double* __restrict__ dinv,
+                            const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= (int64_t)n * b) return;
+  const int I = (int)(r / b), a = (int)(r % b);
+  double s = 0.0;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const double* v = val + ((int64_t)k * b + a) * b;
+    const double* xx = x + (int64_t)col[k] * b;
+    for (int c = 0; c < b; ++c) s += v[c] * xx[c];
+  }
+  y[r] = dinv[r] * s;
+}
+
+__global__ void k_hash_vec(int64_t n, double* __restrict__ x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] = (double)(hash32((uint32_t)i * 2654435761u + 12345u) & 0xffffff) / 16777216.0 + 0.1;
+}
+
+__global__ void k_scale(int64_t n, double* __restrict__ x, const double* __restrict__ nrm2) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
+  if (i < n) x[i] *= s;
+}
+
+__global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+// --------------------------------------------------------------- V-cycle ---
+template <class T>
+__global__ void k_cheb(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
+                       const T* __restrict__ val, const T* __restrict__ dinv,
+                       const T* __restrict__ rhs, const T* __restrict__ xin, T* __restrict__ xout,
+                       T* __restrict__ d, T cd, T cr, int zero_x) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= (int64_t)n * b) return;
+  T s = 0;
+  if (!zero_x) {
+    const int I = (int)(r / b), a = (int)(r % b);
+    for (int k = rp[I]; k < rp[I + 1]; ++k) {
+      const T* v = val + ((int64_t)k * b + a) * b;
+      const T* xx = xin + (int64_t)col[k] * b;
+      for (int c = 0; c < b; ++c) s += v[c] * xx[c];
+    }
+  }
+  const T res = dinv[r] * (rhs[r] - s);
+  const T dn = cd * (zero_x ? T(0) : d[r]) + cr * res;
+  d[r] = dn;
+  xout[r] = (zero_x ? T(0) : xin[r]) + dn;
+}
+
+template <class T>
+__global__ void k_resid(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
+                        const T* __restrict__ val, const T* __restrict__ rhs,
+                        const T* __restrict__ x, T* __restrict__ r) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (int64_t)n * b) return;
+  const int I = (int)(i / b), a = (int)(i % b);
+  T s = 0;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const T* v = val + ((int64_t)k * b + a) * b;
+    const T* xx = x + (int64_t)col[k] * b;
+    for (int c = 0; c < b; ++c) s += v[c] * xx[c];
+  }
+  r[i] = rhs[i] - s;
+}
+
+template <class T>
+__global__ void k_dense_mv(int n, const T* __restrict__ M, const T* __restrict__ x, T* __restrict__ y) {
+  const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  T s = 0;
+  for (int c = lane; c < n; c += 32) s += M[(int64_t)row * n + c] * x[c];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (lane == 0) y[row] = s;
+}
+
+template <class Tin, class Tout>
+__global__ void k_convert(int64_t n, const Tin* __restrict__ a, Tout* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (Tout)a[i];
+}
+
+template <class T>
+const T* vals(const Bsr& A);
+template <>
+const double* vals<double>(const Bsr& A) { return A.val; }
+template <>
+const float* vals<float>(const Bsr& A) { return A.valf; }
+
+template <class T>
+const T* dinvs(const AmgLevel& L);
+template <>
+const double* dinvs<double>(const AmgLevel& L) { return L.dinv; }
+template <>
+const float* dinvs<float>(const AmgLevel& L) { return L.dinvf; }
+
+template <class T>
+void spmv_t(const Bsr& A, const T* x, T* y, T alpha, T beta, cudaStream_t s);
+template <>
+void spmv_t<double>(const Bsr& A, const double* x, double* y, double a, double b, cudaStream_t s) {
+  bsr_spmv(A, x, y, a, b, s);
+}
+template <>
+void spmv_t<float>(const Bsr& A, const float* x, float* y, float a, float b, cudaStream_t s) {
+  bsr_spmv_f(A, x, y, a, b, s);
+}
+
+template <class T>
+void smooth(const AmgLevel& L, int degree, const T* rhs, T* x, T* t, T* d, bool zero_start,
+            cudaStream_t s) {
+  // Chebyshev iteration for D^-1 A on [lmax/30, 1.1 lmax]
+  const double beta = 1.1 * L.lmax, alpha = L.lmax / 30.0;
+  const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
+  const double sigma = theta / delta;
+  double rho = 1.0 / sigma;
+  const Bsr& A = L.A;
+  const int nb = A.nrows, b = A.br;
+  const unsigned g = grid_for((int64_t)nb * b, 256);
+  T* cur = x;
+  T* nxt = t;
+  // first step: d = r / theta
+  k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
+                              T(0), T(1.0 / theta), zero_start ? 1 : 0);
+  std::swap(cur, nxt);
+  for (int k = 1; k < degree; ++k) {
+    const double rn = 1.0 / (2.0 * sigma - rho);
+    k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
+                                T(rn * rho), T(2.0 * rn / delta), 0);
+    std::swap(cur, nxt);
+    rho = rn;
+  }
+  if (cur != x) PFF_CUDA(cudaMemcpyAsync(x, cur, sizeof(T) * (size_t)nb * b, cudaMemcpyDeviceToDevice, s));
+  PFF_LAUNCH("chebyshev");
+}
+
+template <class T>
+void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
+  if (l == (int)amg.lev.size()) {
+    const T* M = nullptr;
+    if constexpr (sizeof(T) == 8) M = reinterpret_cast<const T*>(amg.cinv);
+    else M = reinterpret_cast<const T*>(amg.cinvf);
+    k_dense_mv<T><<<grid_for(amg.nc, 8), 256, 0, s>>>(amg.nc, M, rhs, x);
+    PFF_LAUNCH("coarse");
+    return;
+  }
+  AmgLevel& L = amg.lev[l];
+  T* t = reinterpret_cast<T*>(L.t);
+  T* d = reinterpret_cast<T*>(L.d);
+  T* r = reinterpret_cast<T*>(L.r);
+  smooth<T>(L, amg.cheb_degree, rhs, x, t, d, true, s);
+  if (L.terminal) {
+    smooth<T>(L, amg.cheb_degree, rhs, x, t, d, false, s);
+    return;
+  }
+  const Bsr& A = L.A;
+  k_resid<T><<<grid_for((int64_t)A.nrows * A.br, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr, A.col,
+                                                                    vals<T>(A), rhs, x, r);
+  const bool last = l + 1 == (int)amg.lev.size();
+  T* cb = last ? reinterpret_cast<T*>(amg.cb) : reinterpret_cast<T*>(amg.lev[l + 1].b);
+  T* cx = last ? reinterpret_cast<T*>(amg.cx) : reinterpret_cast<T*>(amg.lev[l + 1].x);
+  spmv_t<T>(L.R, r, cb, T(1), T(0), s);
+  vcycle_level<T>(amg, l + 1, cb, cx, s);
+  spmv_t<T>(L.P, cx, x, T(1), T(1), s);
+  smooth<T>(L, amg.cheb_degree, rhs, x, t, d, false, s);
+}
+
+struct SetupScratch {
+  int* err = nullptr;
+  int* h_err = nullptr;
+  double* red = nullptr;
+  double* h_red = nullptr;
+};
+
+double estimate_lmax(const Bsr& A, const double* dinv, cudaStream_t s, double* partials,
+                     double* dred, double* hred) {
+  const int64_t n = (int64_t)A.nrows * A.br;
+  double* x = dalloc<double>(n);
+  double* y = dalloc<double>(n);
+  k_hash_vec<<<grid_for(n, 256), 256, 0, s>>>(n, x);
+  double lam = 1.0;
+  for (int it = 0; it < 12; ++it) {
+    dot_dev(x, x, n, dred, partials, s);
+    k_scale<<<grid_for(n, 256), 256, 0, s>>>(n, x, dred);
+    k_dinv_spmv<<<grid_for(n, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr, A.col, A.val, dinv, x, y);
+    dot_dev(y, y, n, dred, partials, s);
+    PFF_CUDA(cudaMemcpyAsync(hred, dred, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PFF_CUDA(cudaStreamSynchronize(s));
+    lam = std::sqrt(*hred);
+    std::swap(x, y);
+  }
+  dfree(x);
+  dfree(y);
+  PFF_LAUNCH("lmax");
+  return lam > 0.0 ? lam : 1.0;
+}
+
+// C = X * Y (BSR)
+void spgemm(const Bsr& X, const Bsr& Y, Bsr& C, int* err, cudaStream_t s) {
+  C.nrows = X.nrows;
+  C.ncols = Y.ncols;
+  C.br = X.br;
+  C.bc = Y.bc;
+  C.rowptr = dalloc<int>(X.nrows + 1);
+  int* cnt = dalloc<int>(X.nrows + 1);
+  const unsigned g = grid_for(X.nrows, 128);
+  k_mm_count<<<g, 128, 0, s>>>(X.nrows, X.rowptr, X.col, Y.rowptr, Y.col, cnt, err);
+  PFF_LAUNCH("mm_count");
+  int total = 0;
+  exclusive_scan_int(cnt, C.rowptr, X.nrows, &total, s);
+  C.nnzb = total;
+  C.col = dalloc<int>(total);
+  C.val = dalloc<double>((size_t)total * C.br * C.bc);
+  k_mm_fill<<<g, 128, 0, s>>>(X.nrows, X.br, X.bc, Y.bc, X.rowptr, X.col, X.val, Y.rowptr, Y.col,
+                              Y.val, C.rowptr, C.col, C.val);
+  PFF_LAUNCH("mm_fill");
+  dfree(cnt);
+}
+
+void transpose(const Bsr& P, Bsr& R, cudaStream_t s) {
+  R.nrows = P.ncols;
+  R.ncols = P.nrows;
+  R.br = P.bc;
+  R.bc = P.br;
+  R.nnzb = P.nnzb;
+  R.rowptr = dalloc<int>(R.nrows + 1);
+  int* cnt = dalloc<int>(R.nrows + 1);
+  int* cursor = dalloc<int>(R.nrows + 1);
+  PFF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (R.nrows + 1), s));
+  PFF_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (R.nrows + 1), s));
+  k_T_count<<<grid_for(P.nrows, 256), 256, 0, s>>>(P.nrows, P.rowptr, P.col, cnt);
+  int total = 0;
+  exclusive_scan_int(cnt, R.rowptr, R.nrows, &total, s);
+  R.col = dalloc<int>(total);
+  int* src = dalloc<int>(total);
+  k_T_fill<<<grid_for(P.nrows, 256), 256, 0, s>>>(P.nrows, P.rowptr, P.col, R.rowptr, cursor,
+                                                  R.col, src);
+  k_sort_segments<<<grid_for(R.nrows, 128), 128, 0, s>>>(R.nrows, R.rowptr, R.col, src);
+  R.val = dalloc<double>((size_t)total * R.br * R.bc);
+  k_T_vals<<<grid_for(total, 256), 256, 0, s>>>(total, P.br, P.bc, src, P.val, R.val);
+  PFF_LAUNCH("transpose");
+  PFF_CUDA(cudaStreamSynchronize(s));
+  dfree(cnt);
+  dfree(cursor);
+  dfree(src);
+}
+
+void copy_bsr(const Bsr& A, Bsr& C, cudaStream_t s) {
+  C.nrows = A.nrows;
+  C.ncols = A.ncols;
+  C.br = A.br;
+  C.bc = A.bc;
+  C.nnzb = A.nnzb;
+  C.rowptr = dalloc<int>(A.nrows + 1);
+  C.col = dalloc<int>(A.nnzb);
+  C.val = dalloc<double>((size_t)A.nnzb * A.br * A.bc);
+  PFF_CUDA(cudaMemcpyAsync(C.rowptr, A.rowptr, sizeof(int) * (A.nrows + 1), cudaMemcpyDeviceToDevice, s));
+  PFF_CUDA(cudaMemcpyAsync(C.col, A.col, sizeof(int) * A.nnzb, cudaMemcpyDeviceToDevice, s));
+  PFF_CUDA(cudaMemcpyAsync(C.val, A.val, sizeof(double) * A.nnzb * A.br * A.bc,
+                           cudaMemcpyDeviceToDevice, s));
+}
+
+void make_float(Bsr& A, cudaStream_t s) {
+  const int64_t nv = A.nnzb * A.br * A.bc;
+  A.valf = dalloc<float>(nv);
+  k_to_float<<<grid_for(nv, 256), 256, 0, s>>>(nv, A.val, A.valf);
+  PFF_LAUNCH("to_float");
+}
+
+void check_err(SetupScratch& sc, cudaStream_t s, const char* where) {
+  PFF_CUDA(cudaMemcpyAsync(sc.h_err, sc.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PFF_CUDA(cudaStreamSynchronize(s));
+  if (*sc.h_err) fail(PFF_ERR_CAPACITY, std::string("AMG setup failed in ") + where + " (code " +
+                                           std::to_string(*sc.h_err) + ")");
+}
+
+}  // namespace
+
+void Amg::release() {
+  for (auto& L : lev) {
+    L.A.release();
+    L.P.release();
+    L.R.release();
+    dfree(L.dinv);
+    dfree(L.dinvf);
+    dfree(L.x);
+    dfree(L.b);
+    dfree(L.r);
+    dfree(L.d);
+    dfree(L.t);
+  }
+  lev.clear();
+  dfree(cinv);
+  dfree(cinvf);
+  dfree(cx);
+  dfree(cb);
+  cinv = nullptr;
+  cinvf = nullptr;
+  cx = cb = nullptr;
+  built = 0;
+}
+
+void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgParams& prm,
+               cudaStream_t s) {
+  amg.release();
+  amg.mixed = prm.mixed;
+  amg.cheb_degree = prm.cheb_degree;
+  SetupScratch sc;
+  sc.err = dalloc<int>(4);
+  PFF_CUDA(cudaMallocHost(&sc.h_err, sizeof(int) * 4));
+  PFF_CUDA(cudaMallocHost(&sc.h_red, sizeof(double) * 4));
+  sc.red = dalloc<double>(4);
+  double* partials = dalloc<double>(RED_PARTIALS);
+  PFF_CUDA(cudaMemsetAsync(sc.err, 0, sizeof(int) * 4, s));
+
+  Bsr A;
+  copy_bsr(Ain, A, s);
+  int nb = A.nrows, br = A.br;
+  double* B = dalloc<double>((size_t)nb * br * nns);
+  PFF_CUDA(cudaMemcpyAsync(B, Bin, sizeof(double) * (size_t)nb * br * nns, cudaMemcpyDeviceToDevice, s));
+
+  for (int level = 0;; ++level) {
+    const int n = nb * br;
+    const bool too_big = n > 8 * prm.coarse_max;
+    if (n <= prm.coarse_max || (level >= prm.max_levels && !too_big)) {
+      // coarsest level: dense inverse
+      amg.nc = n;
+      double* Dm = dalloc<double>((size_t)n * n);
+      amg.cinv = dalloc<double>((size_t)n * n);
+      PFF_CUDA(cudaMemsetAsync(Dm, 0, sizeof(double) * (size_t)n * n, s));
+      k_densify<<<grid_for(nb, 128), 128, 0, s>>>(nb, br, A.rowptr, A.col, A.val, Dm, n);
+      k_gauss_jordan<<<1, 256, 0, s>>>(n, Dm, amg.cinv, sc.err);
+      PFF_LAUNCH("coarse inverse");
+      if (amg.mixed) {
+        amg.cinvf = dalloc<float>((size_t)n * n);
+        k_to_float<<<grid_for((int64_t)n * n, 256), 256, 0, s>>>((int64_t)n * n, amg.cinv, amg.cinvf);
+      }
+      amg.cx = dalloc<double>(n);
+      amg.cb = dalloc<double>(n);
+      check_err(sc, s, "coarse inverse");
+      dfree(Dm);
+      A.release();
+      break;
+    }
+    AmgLevel L;
+    L.A = A;   // takes ownership
+    L.n = n;
+    L.dinv = dalloc<double>(n);
+    double* dnorm = dalloc<double>(nb);
+    k_diag<<<grid_for(nb, 256), 256, 0, s>>>(nb, br, A.rowptr, A.col, A.val, dnorm, L.dinv, sc.err);
+    // strength
+    uint8_t* s0 = dalloc<uint8_t>(A.nnzb);
+    uint8_t* strong = dalloc<uint8_t>(A.nnzb);
+    double* snorm = dalloc<double>(A.nnzb);
+    k_strength<<<grid_for(nb, 256), 256, 0, s>>>(nb, br, A.rowptr, A.col, A.val, dnorm,
+                                                 prm.theta * prm.theta, s0, snorm);
+    k_symmetrize<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, s0, strong);
+    PFF_LAUNCH("strength");
+    // MIS(2)
+    int* state = dalloc<int>(nb);
+    uint8_t* iso = dalloc<uint8_t>(nb);
+    unsigned long long* M1 = dalloc<unsigned long long>(nb);
+    unsigned long long* M2 = dalloc<unsigned long long>(nb);
+    int* und = dalloc<int>(1);
+    int* h_und = sc.h_err + 1;
+    k_mis_init<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, strong, state, iso);
+    int rounds = 0;
+    for (;; ++rounds) {
+      PFF_CUDA(cudaMemsetAsync(und, 0, sizeof(int), s));
+      k_mis_max1<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, strong, state, M1);
+      k_mis_max2<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, strong, M1, M2);
+      k_mis_decide<<<grid_for(nb, 256), 256, 0, s>>>(nb, state, M2, und);
+      PFF_LAUNCH("mis");
+      PFF_CUDA(cudaMemcpyAsync(h_und, und, sizeof(int), cudaMemcpyDeviceToHost, s));
+      PFF_CUDA(cudaStreamSynchronize(s));
+      if (*h_und == 0) break;
+      if (rounds > 200) fail(PFF_ERR_CAPACITY, "AMG MIS(2) did not terminate");
+    }
+    // aggregates
+    int* flag = dalloc<int>(nb + 1);
+    int* rootid = dalloc<int>(nb + 1);
+    k_root_flags<<<grid_for(nb, 256), 256, 0, s>>>(nb, state, flag);
+    int nagg = 0;
+    exclusive_scan_int(flag, rootid, nb, &nagg, s);
+    int* agg1 = dalloc<int>(nb);
+    int* agg = dalloc<int>(nb);
+    k_agg_pass1<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, strong, snorm, state, iso,
+                                                  rootid, agg1);
+    k_agg_pass2<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, strong, snorm, agg1, agg);
+    PFF_LAUNCH("aggregate");
+    if (nagg == 0 || (int64_t)nagg * nns > (int64_t)(0.9 * n) || level >= prm.max_levels) {
+      // every row is isolated (identity / decoupled rows): smoothing is all there is
+      L.terminal = true;
+      L.lmax = estimate_lmax(L.A, L.dinv, s, partials, sc.red, sc.h_red);
+      L.x = dalloc<double>(n);
+      L.b = dalloc<double>(n);
+      L.r = dalloc<double>(n);
+      L.d = dalloc<double>(n);
+      L.t = dalloc<double>(n);
+      if (amg.mixed) {
+        make_float(L.A, s);
+        L.dinvf = dalloc<float>(n);
+        k_to_float<<<grid_for(n, 256), 256, 0, s>>>(n, L.dinv, L.dinvf);
+      }
+      PFF_CUDA(cudaStreamSynchronize(s));
+      dfree(dnorm);
+      dfree(s0);
+      dfree(strong);
+      dfree(snorm);
+      dfree(state);
+      dfree(iso);
+      dfree(M1);
+      dfree(M2);
+      dfree(und);
+      dfree(flag);
+      dfree(rootid);
+      dfree(agg1);
+      dfree(agg);
+      amg.lev.push_back(L);
+      amg.nc = 0;
+      break;
+    }
+    int* cnt = dalloc<int>(nagg + 1);
+    int* off = dalloc<int>(nagg + 1);
+    int* cursor = dalloc<int>(nagg + 1);
+    int* members = dalloc<int>(nb);
+    PFF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (nagg + 1), s));
+    PFF_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (nagg + 1), s));
+    k_count_members<<<grid_for(nb, 256), 256, 0, s>>>(nb, agg, cnt);
+    int nmem = 0;
+    exclusive_scan_int(cnt, off, nagg, &nmem, s);
+    k_fill_members<<<grid_for(nb, 256), 256, 0, s>>>(nb, agg, off, cursor, members);
+    k_sort_segments<<<grid_for(nagg, 128), 128, 0, s>>>(nagg, off, members, nullptr);
+    // tentative prolongator + coarse near-null space
+    double* Qn = dalloc<double>((size_t)nb * br * nns);
+    double* Bc = dalloc<double>((size_t)nagg * nns * nns);
+    k_zero_rows<<<grid_for(nb, 256), 256, 0, s>>>(nb, br * nns, agg, Qn);
+    k_tentative<<<grid_for(nagg, 64), 64, 0, s>>>(nagg, br, nns, off, members, B, (int64_t)nb * br,
+                                                  Qn, Bc, (int64_t)nagg * nns);
+    PFF_LAUNCH("tentative");
+    // smoothed prolongator
+    L.lmax = estimate_lmax(L.A, L.dinv, s, partials, sc.red, sc.h_red);
+    const double omega = 4.0 / (3.0 * L.lmax);
+    Bsr& P = L.P;
+    P.nrows = nb;
+    P.ncols = nagg;
+    P.br = br;
+    P.bc = nns;
+    P.rowptr = dalloc<int>(nb + 1);
+    int* pc = dalloc<int>(nb + 1);
+    k_P_count<<<grid_for(nb, 128), 128, 0, s>>>(nb, A.rowptr, A.col, agg, pc, sc.err);
+    int pnnz = 0;
+    exclusive_scan_int(pc, P.rowptr, nb, &pnnz, s);
+    P.nnzb = pnnz;
+    P.col = dalloc<int>(pnnz);
+    P.val = dalloc<double>((size_t)pnnz * br * nns);
+    k_P_fill<<<grid_for(nb, 128), 128, 0, s>>>(nb, br, nns, A.rowptr, A.col, A.val, agg, Qn, L.dinv,
+                                               omega, P.rowptr, P.col, P.val);
+    PFF_LAUNCH("P");
+    check_err(sc, s, "prolongator");
+    transpose(P, L.R, s);
+    // Galerkin product
+    Bsr AP, Ac;
+    spgemm(L.A, P, AP, sc.err, s);
+    spgemm(L.R, AP, Ac, sc.err, s);
+    check_err(sc, s, "Galerkin product");
+    k_fix_diag<<<grid_for(Ac.nrows, 128), 128, 0, s>>>(Ac.nrows, Ac.br, Ac.rowptr, Ac.col, Ac.val);
+    PFF_LAUNCH("fix_diag");
+    AP.release();
+    // work vectors and FP32 copies
+    L.x = dalloc<double>(n);
+    L.b = dalloc<double>(n);
+    L.r = dalloc<double>(n);
+    L.d = dalloc<double>(n);
+    L.t = dalloc<double>(n);
+    if (amg.mixed) {
+      make_float(L.A, s);
+      make_float(L.P, s);
+      make_float(L.R, s);
+      L.dinvf = dalloc<float>(n);
+      k_to_float<<<grid_for(n, 256), 256, 0, s>>>(n, L.dinv, L.dinvf);
+    }
+    PFF_CUDA(cudaStreamSynchronize(s));
+    dfree(dnorm);
+    dfree(s0);
+    dfree(strong);
+    dfree(snorm);
+    dfree(state);
+    dfree(iso);
+    dfree(M1);
+    dfree(M2);
+    dfree(und);
+    dfree(flag);
+    dfree(rootid);
+    dfree(agg1);
+    dfree(agg);
+    dfree(cnt);
+    dfree(off);
+    dfree(cursor);
+    dfree(members);
+    dfree(Qn);
+    dfree(pc);
+    dfree(B);
+    amg.lev.push_back(L);
+    // next level
+    A = Ac;
+    B = Bc;
+    nb = Ac.nrows;
+    br = Ac.br;
+  }
+  dfree(B);
+  dfree(partials);
+  dfree(sc.err);
+  dfree(sc.red);
+  cudaFreeHost(sc.h_err);
+  cudaFreeHost(sc.h_red);
+  amg.built = 1;
+}
+
+void amg_vcycle(Amg& amg, const double* r, double* z, cudaStream_t s) {
+  if (amg.lev.empty()) {
+    // whole problem is the coarse level
+    k_dense_mv<double><<<grid_for(amg.nc, 8), 256, 0, s>>>(amg.nc, amg.cinv, r, z);
+    PFF_LAUNCH("coarse only");
+    return;
+  }
+  AmgLevel& L0 = amg.lev[0];
+  const int64_t n = L0.n;
+  if (amg.mixed) {
+    float* b = reinterpret_cast<float*>(L0.b);
+    float* x = reinterpret_cast<float*>(L0.x);
+    k_convert<double, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, b);
+    vcycle_level<float>(amg, 0, b, x, s);
+    k_convert<float, double><<<grid_for(n, 256), 256, 0, s>>>(n, x, z);
+  } else {
+    PFF_CUDA(cudaMemcpyAsync(L0.b, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    vcycle_level<double>(amg, 0, L0.b, L0.x, s);
+    PFF_CUDA(cudaMemcpyAsync(z, L0.x, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+  }
+  PFF_LAUNCH("vcycle");
+}
+
+}  // namespace pff

@@ -1,0 +1,566 @@
+// extern "C" entry points of include/pff.h: argument checks, ownership of the
+// device state, error translation.  All numerical work is in the kernels.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+
+#include "pff_internal.h"
+
+namespace pff {
+
+struct Failure {
+  int code;
+  std::string msg;
+};
+
+namespace {
+thread_local std::string g_msg;
+}
+
+void set_error(int code, const std::string& msg) {
+  (void)code;
+  g_msg = msg;
+}
+
+void fail(int code, const std::string& msg) { throw Failure{code, msg}; }
+
+void check_cuda(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return;
+  cudaGetLastError();
+  const int code = e == cudaErrorMemoryAllocation ? PFF_ERR_OOM : PFF_ERR_CUDA;
+  throw Failure{code, std::string(what) + ": " + cudaGetErrorString(e)};
+}
+
+void* dmalloc(size_t bytes) {
+  void* p = nullptr;
+  const cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    throw Failure{PFF_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
+                                   cudaGetErrorString(e)};
+  }
+  return p;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+}  // namespace pff
+
+using pff::fail;
+
+#define API_BEGIN try {
+#define API_END                                      \
+  }                                                  \
+  catch (const pff::Failure& f) {                    \
+    pff::set_error(f.code, f.msg);                   \
+    return f.code;                                   \
+  }                                                  \
+  catch (const std::bad_alloc&) {                    \
+    pff::set_error(PFF_ERR_OOM, "host allocation failed"); \
+    return PFF_ERR_OOM;                              \
+  }                                                  \
+  catch (const std::exception& e) {                  \
+    pff::set_error(PFF_ERR_INVALID_ARG, e.what());   \
+    return PFF_ERR_INVALID_ARG;                      \
+  }                                                  \
+  return PFF_OK;
+
+namespace {
+
+void need(bool ok, const char* msg) {
+  if (!ok) fail(PFF_ERR_INVALID_ARG, msg);
+}
+
+void sync(pff_problem* P) { PFF_CUDA(cudaStreamSynchronize(P->stream)); }
+
+void upload(pff_problem* P, double* dst, const double* src, size_t n) {
+  PFF_CUDA(cudaMemcpyAsync(dst, src, sizeof(double) * n, cudaMemcpyHostToDevice, P->stream));
+}
+
+void refresh_phi_tilde(pff_problem* P) {
+  pff::launch_phi_tilde(P->mesh(), P->n_nodes, P->steps_done, P->phi_old, P->phi_prev, P->phit,
+                        P->stream);
+  P->uu_assembled = false;
+  P->phi_assembled = false;
+  P->amg_u_valid = false;
+  P->in_step = false;
+}
+
+void release(pff_problem* P) {
+  using pff::dfree;
+  for (int a = 0; a < 3; ++a) dfree(P->X[a]);
+  double* dbl[] = {P->u, P->phi, P->phi_old, P->phi_prev, P->phit, P->mass, P->S, P->Sinv,
+                   P->indicator, P->d_scalars, P->partials, P->Kuu, P->Kpu, P->Kpp, P->F,
+                   P->Ft, P->dU, P->dUA, P->ut, P->phit_trial, P->Ftrial, P->Bu, P->Bp,
+                   P->V, P->Z, P->w, P->h, P->tmp};
+  for (double* p : dbl) dfree(p);
+  dfree(P->active);
+  dfree(P->active_prev);
+  dfree(P->raw_prev);
+  dfree(P->locked);
+  dfree(P->toggles);
+  dfree(P->counters);
+  if (P->h_counters) cudaFreeHost(P->h_counters);
+  if (P->h_scalars) cudaFreeHost(P->h_scalars);
+  if (P->h_host) cudaFreeHost(P->h_host);
+  P->Auu.release();
+  P->App.release();
+  P->amg_u.release();
+  P->amg_p.release();
+}
+
+// crack rule of Section 4 (see pff_set_crack in include/pff.h)
+std::vector<double> crack_field(const pff_problem* P, double l0) {
+  const int d = P->dim;
+  std::vector<double> phi((size_t)P->n_nodes, 1.0);
+  const auto& X = P->hX;
+  const int nx = P->nc[0], ny = P->nc[1], nz = d == 3 ? P->nc[2] : 1;
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        bool cut;
+        if (d == 2) {
+          cut = X[0][i] < l0 && X[0][i + 1] > -l0 && X[1][j] <= 0.0 && X[1][j + 1] >= 0.0;
+        } else {
+          const double px = std::min(std::max(0.0, X[0][i]), X[0][i + 1]);
+          const double py = std::min(std::max(0.0, X[1][j]), X[1][j + 1]);
+          cut = X[2][k] <= 0.0 && X[2][k + 1] >= 0.0 && px * px + py * py < l0 * l0;
+        }
+        if (!cut) continue;
+        for (int c = 0; c < (1 << d); ++c) {
+          const int64_t ii = i + (c & 1), jj = j + ((c >> 1) & 1), kk = k + ((c >> 2) & 1);
+          phi[(size_t)(ii + P->nn[0] * (jj + (int64_t)P->nn[1] * kk))] = 0.0;
+        }
+      }
+  return phi;
+}
+
+// cells of one axis whose closed interval contains x, with averaging weights
+std::vector<std::pair<int, double>> columns(const std::vector<double>& X, double x) {
+  std::vector<std::pair<int, double>> hits;
+  const int n = (int)X.size() - 1;
+  if (!(x >= X[0] && x <= X[n])) fail(PFF_ERR_INVALID_ARG, "COD point outside the domain");
+  const int p = (int)(std::upper_bound(X.begin(), X.end(), x) - X.begin());
+  for (int i = std::max(0, p - 2); i < std::min(n, p + 1); ++i)
+    if (X[i] <= x && x <= X[i + 1]) hits.push_back({i, 0.0});
+  for (auto& h : hits) h.second = 1.0 / hits.size();
+  return hits;
+}
+
+}  // namespace
+
+extern "C" {
+
+void pff_default_options(pff_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = PFF_PREC_FP64;
+  o->c = 1.0;
+  o->tol_newton = 1e-10;
+  o->tol_step = 1e-9;
+  o->tol_linear = 1e-8;
+  o->max_newton = 50;
+  o->max_halvings = 10;
+  o->cycle_lock = 3;
+  o->krylov_restart = 40;
+  o->max_krylov = 600;
+  o->cheb_degree = 2;
+  o->amg_theta = 0.08;
+  o->amg_coarse_max = 320;
+  o->apply_variant = PFF_APPLY_AUTO;
+  o->precond = PFF_PC_AMG;
+}
+
+const char* pff_last_error(void) { return pff::g_msg.c_str(); }
+
+int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_coords,
+                    pff_problem** out) {
+  API_BEGIN
+  need(out != nullptr, "out is NULL");
+  *out = nullptr;
+  need(dim == 2 || dim == 3, "dim must be 2 or 3");
+  need(n_cells && axis_coords, "n_cells / axis_coords is NULL");
+  auto* P = new pff_problem();
+  try {
+    P->dim = dim;
+    int64_t nn = 1, nc = 1;
+    for (int a = 0; a < dim; ++a) {
+      need(n_cells[a] >= 1 && n_cells[a] < (1 << 24), "n_cells out of range");
+      need(axis_coords[a] != nullptr, "axis coordinate array is NULL");
+      P->nc[a] = n_cells[a];
+      P->nn[a] = n_cells[a] + 1;
+      P->hX[a].assign(axis_coords[a], axis_coords[a] + n_cells[a] + 1);
+      for (int i = 0; i < n_cells[a]; ++i)
+        need(std::isfinite(P->hX[a][i]) && P->hX[a][i + 1] > P->hX[a][i],
+             "axis coordinates must be finite and strictly increasing");
+      nn *= P->nn[a];
+      nc *= P->nc[a];
+    }
+    need(nn < (int64_t)1 << 31, "too many nodes");
+    P->n_nodes = nn;
+    P->n_cells = nc;
+    P->n_dofs = (int64_t)(dim + 1) * nn;
+    const int64_t n = nn, N = P->n_dofs;
+    for (int a = 0; a < dim; ++a) {
+      P->X[a] = pff::dalloc<double>(P->nn[a]);
+      PFF_CUDA(cudaMemcpy(P->X[a], P->hX[a].data(), sizeof(double) * P->nn[a], cudaMemcpyHostToDevice));
+    }
+    using pff::dalloc;
+    P->u = dalloc<double>(n * dim);
+    P->ut = dalloc<double>(n * dim);
+    P->phi = dalloc<double>(n);
+    P->phi_old = dalloc<double>(n);
+    P->phi_prev = dalloc<double>(n);
+    P->phit = dalloc<double>(n);
+    P->phit_trial = dalloc<double>(n);
+    P->mass = dalloc<double>(n);
+    P->S = dalloc<double>(N);
+    P->Sinv = dalloc<double>(N);
+    P->indicator = dalloc<double>(n);
+    P->active = dalloc<uint8_t>(n);
+    P->active_prev = dalloc<uint8_t>(n);
+    P->raw_prev = dalloc<uint8_t>(n);
+    P->locked = dalloc<uint8_t>(n);
+    P->toggles = dalloc<int>(n);
+    P->counters = dalloc<int>(8);
+    P->d_scalars = dalloc<double>(16);
+    P->partials = dalloc<double>(65536);
+    PFF_CUDA(cudaMallocHost(&P->h_counters, sizeof(int) * 8));
+    PFF_CUDA(cudaMallocHost(&P->h_scalars, sizeof(double) * 16));
+    const int NS = pff::n_slots(dim);
+    P->Kuu = dalloc<double>((size_t)NS * dim * dim * n);
+    P->Kpu = dalloc<double>((size_t)NS * dim * n);
+    P->Kpp = dalloc<double>((size_t)NS * n);
+    P->F = dalloc<double>(N);
+    P->Ft = dalloc<double>(N);
+    P->dU = dalloc<double>(N);
+    P->dUA = dalloc<double>(N);
+    P->Ftrial = dalloc<double>(N);
+    P->tmp = dalloc<double>(N);
+    PFF_CUDA(cudaMemset(P->u, 0, sizeof(double) * n * dim));
+    PFF_CUDA(cudaMemset(P->active, 0, n));
+    PFF_CUDA(cudaMemset(P->raw_prev, 0, n));
+    PFF_CUDA(cudaMemset(P->locked, 0, n));
+    PFF_CUDA(cudaMemset(P->toggles, 0, sizeof(int) * n));
+    std::vector<double> ones((size_t)n, 1.0);
+    PFF_CUDA(cudaMemcpy(P->phi, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    PFF_CUDA(cudaMemcpy(P->phi_old, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    PFF_CUDA(cudaMemcpy(P->phi_prev, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    P->Bp = dalloc<double>(n);
+    PFF_CUDA(cudaMemcpy(P->Bp, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    const auto m = P->mesh();
+    pff::launch_lumped_mass(m, n, P->mass, P->stream);
+    P->Bu = dalloc<double>((size_t)n * dim * (dim == 2 ? 3 : 6));
+    pff::launch_rigid_modes(m, n, P->Bu, P->stream);
+    pff::build_stencil_bsr_structure(m, n, dim, P->Auu, P->stream);
+    pff::build_stencil_bsr_structure(m, n, 1, P->App, P->stream);
+    const double E = 1.0, nu = 0.2;
+    P->mat.mu = E / (2.0 * (1.0 + nu));
+    P->mat.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+    refresh_phi_tilde(P);
+    sync(P);
+  } catch (...) {
+    release(P);
+    delete P;
+    throw;
+  }
+  *out = P;
+  API_END
+}
+
+int pff_set_material(pff_problem* P, double E, double nu, double Gc, double kappa, double eps) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  need(E > 0 && std::isfinite(E), "E must be > 0");
+  need(nu >= 0 && nu < 0.5, "nu must be in [0, 0.5)");
+  need(Gc > 0 && std::isfinite(Gc), "Gc must be > 0");
+  need(kappa >= 0 && kappa < 1, "kappa must be in [0, 1)");
+  need(eps > 0 && std::isfinite(eps), "eps must be > 0");
+  P->mat.E = E;
+  P->mat.nu = nu;
+  P->mat.Gc = Gc;
+  P->mat.kappa = kappa;
+  P->mat.eps = eps;
+  P->mat.mu = E / (2.0 * (1.0 + nu));
+  P->mat.lam = E * nu / ((1.0 + nu) * (1.0 - 2.0 * nu));
+  P->uu_assembled = false;
+  P->phi_assembled = false;
+  P->amg_u_valid = false;
+  P->in_step = false;
+  API_END
+}
+
+int pff_set_pressure(pff_problem* P, double p) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  need(std::isfinite(p), "pressure must be finite");
+  pff::begin_loading_step(P, p);
+  API_END
+}
+
+int pff_set_crack(pff_problem* P, double l0) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  need(l0 > 0 && std::isfinite(l0), "l0 must be > 0");
+  const auto phi = crack_field(P, l0);
+  const size_t n = (size_t)P->n_nodes;
+  upload(P, P->phi, phi.data(), n);
+  upload(P, P->phi_old, phi.data(), n);
+  upload(P, P->phi_prev, phi.data(), n);
+  PFF_CUDA(cudaMemsetAsync(P->u, 0, sizeof(double) * n * P->dim, P->stream));
+  P->steps_done = 0;
+  refresh_phi_tilde(P);
+  sync(P);
+  API_END
+}
+
+int pff_set_state(pff_problem* P, const double* u, const double* phi, const double* phi_old,
+                  const double* phi_prev, int steps_done) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  need(steps_done >= 0, "steps_done must be >= 0");
+  const size_t n = (size_t)P->n_nodes;
+  if (u) upload(P, P->u, u, n * P->dim);
+  if (phi) upload(P, P->phi, phi, n);
+  if (phi_old) upload(P, P->phi_old, phi_old, n);
+  if (phi_prev) upload(P, P->phi_prev, phi_prev, n);
+  P->steps_done = steps_done;
+  refresh_phi_tilde(P);
+  sync(P);
+  API_END
+}
+
+int pff_newton_step(pff_problem* P, const pff_options* opts, pff_step_report* rep) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  pff_options o;
+  pff_default_options(&o);
+  if (opts) o = *opts;
+  if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
+    P->apply_variant = o.apply_variant;
+  const int rc = pff::newton_iteration(P, o, rep);
+  if (rc != PFF_OK) {
+    pff::set_error(rc, "Newton iteration failed");
+    return rc;
+  }
+  API_END
+}
+
+int pff_end_loading_step(pff_problem* P) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  pff::end_loading_step(P);
+  API_END
+}
+
+int pff_solve_loading_steps(pff_problem* P, int n_steps, const double* p_schedule,
+                            const pff_options* opts, pff_step_report* reports) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  need(n_steps >= 0 && (n_steps == 0 || p_schedule != nullptr), "bad schedule");
+  pff_options o;
+  pff_default_options(&o);
+  if (opts) o = *opts;
+  if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
+    P->apply_variant = o.apply_variant;
+  int rc_all = PFF_OK;
+  for (int st = 0; st < n_steps; ++st) {
+    const auto t0 = std::chrono::steady_clock::now();
+    pff::begin_loading_step(P, p_schedule[st]);
+    pff_step_report r{};
+    int rc = PFF_OK;
+    while (true) {
+      rc = pff::newton_iteration(P, o, &r);
+      if (rc != PFF_OK || r.converged) break;
+    }
+    pff::end_loading_step(P);
+    r.time_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    r.status = rc;
+    if (reports) reports[st] = r;
+    if (rc != PFF_OK) {
+      rc_all = rc;
+      pff::set_error(rc, "loading step " + std::to_string(st) + " failed");
+      return rc_all;
+    }
+  }
+  API_END
+}
+
+int pff_eval_tcv_cod(pff_problem* P, int n_pts, const double* pts, double* tcv, double* cod) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  need(n_pts >= 0 && (n_pts == 0 || pts != nullptr), "bad COD points");
+  const auto m = P->mesh();
+  if (tcv) {
+    pff::tcv_dev(m, P->n_cells, P->u, P->phi, P->d_scalars, P->partials, P->stream);
+    PFF_CUDA(cudaMemcpyAsync(P->h_scalars, P->d_scalars, sizeof(double), cudaMemcpyDeviceToHost,
+                             P->stream));
+    sync(P);
+    *tcv = P->h_scalars[0];
+  }
+  if (cod && n_pts > 0) {
+    const int d = P->dim;
+    std::vector<pff::CodColumn> cols;
+    for (int k = 0; k < n_pts; ++k) {
+      const auto cx = columns(P->hX[0], pts[k * (d - 1)]);
+      std::vector<std::pair<int, double>> cy = {{0, 1.0}};
+      if (d == 3) cy = columns(P->hX[1], pts[k * 2 + 1]);
+      for (auto& a : cx)
+        for (auto& b : cy) {
+          pff::CodColumn c{};
+          c.col[0] = a.first;
+          c.xi[0] = (pts[k * (d - 1)] - P->hX[0][a.first]) / (P->hX[0][a.first + 1] - P->hX[0][a.first]);
+          if (d == 3) {
+            c.col[1] = b.first;
+            c.xi[1] = (pts[k * 2 + 1] - P->hX[1][b.first]) / (P->hX[1][b.first + 1] - P->hX[1][b.first]);
+          }
+          c.w = a.second * b.second;
+          c.point = k;
+          cols.push_back(c);
+        }
+    }
+    const int nc = (int)cols.size();
+    auto* dcols = pff::dalloc<pff::CodColumn>(nc);
+    double* dout = pff::dalloc<double>(nc);
+    PFF_CUDA(cudaMemcpyAsync(dcols, cols.data(), sizeof(pff::CodColumn) * nc, cudaMemcpyHostToDevice,
+                             P->stream));
+    pff::cod_dev(m, dcols, nc, P->u, P->phi, dout, n_pts, P->stream);
+    std::vector<double> hout(nc);
+    PFF_CUDA(cudaMemcpyAsync(hout.data(), dout, sizeof(double) * nc, cudaMemcpyDeviceToHost, P->stream));
+    sync(P);
+    pff::dfree(dcols);
+    pff::dfree(dout);
+    for (int k = 0; k < n_pts; ++k) cod[k] = 0.0;
+    for (int c = 0; c < nc; ++c) cod[cols[c].point] += hout[c];
+  }
+  API_END
+}
+
+int pff_get_solution(pff_problem* P, double* u, double* phi, uint8_t* active) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  const size_t n = (size_t)P->n_nodes;
+  if (u) PFF_CUDA(cudaMemcpyAsync(u, P->u, sizeof(double) * n * P->dim, cudaMemcpyDeviceToHost, P->stream));
+  if (phi) PFF_CUDA(cudaMemcpyAsync(phi, P->phi, sizeof(double) * n, cudaMemcpyDeviceToHost, P->stream));
+  if (active) PFF_CUDA(cudaMemcpyAsync(active, P->active, n, cudaMemcpyDeviceToHost, P->stream));
+  sync(P);
+  API_END
+}
+
+int pff_set_stream(pff_problem* P, void* stream) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  sync(P);
+  P->stream = static_cast<cudaStream_t>(stream);
+  API_END
+}
+
+int pff_get_sizes(const pff_problem* P, int* dim, int64_t* n_nodes, int64_t* n_dofs) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  if (dim) *dim = P->dim;
+  if (n_nodes) *n_nodes = P->n_nodes;
+  if (n_dofs) *n_dofs = P->n_dofs;
+  API_END
+}
+
+void pff_destroy(pff_problem* P) {
+  if (!P) return;
+  cudaStreamSynchronize(P->stream);
+  release(P);
+  delete P;
+}
+
+int pff_residual_dev(pff_problem* P, double* F_dev) {
+  API_BEGIN
+  need(P != nullptr && F_dev != nullptr, "NULL argument");
+  pff::compute_residual(P, P->u, P->phi, F_dev);
+  API_END
+}
+
+int pff_active_set_dev(pff_problem* P, double c, uint8_t* active_dev, double* indicator_dev) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  need(c > 0 && std::isfinite(c), "c must be > 0");
+  pff::compute_residual(P, P->u, P->phi, P->F);
+  pff::compute_active_set(P, c, 1 << 30, false);
+  if (active_dev)
+    PFF_CUDA(cudaMemcpyAsync(active_dev, P->active, P->n_nodes, cudaMemcpyDeviceToDevice, P->stream));
+  if (indicator_dev)
+    PFF_CUDA(cudaMemcpyAsync(indicator_dev, P->indicator, sizeof(double) * P->n_nodes,
+                             cudaMemcpyDeviceToDevice, P->stream));
+  P->phi_assembled = false;
+  API_END
+}
+
+int pff_assemble(pff_problem* P) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  pff::compute_residual(P, P->u, P->phi, P->F);
+  pff::assemble_all(P);
+  API_END
+}
+
+int pff_apply_jacobian_dev(pff_problem* P, int variant, const double* x_dev, double* y_dev) {
+  API_BEGIN
+  need(P != nullptr && x_dev && y_dev, "NULL argument");
+  need(variant == PFF_APPLY_ASSEMBLED || variant == PFF_APPLY_MATFREE, "bad variant");
+  pff::apply_jacobian(P, variant, x_dev, y_dev, nullptr);
+  API_END
+}
+
+int pff_precond_setup(pff_problem* P, const pff_options* opts) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  need(P->phi_assembled, "call pff_assemble first");
+  pff_options o;
+  pff_default_options(&o);
+  if (opts) o = *opts;
+  P->amg_u_valid = false;
+  pff::precond_setup(P, o);
+  sync(P);
+  API_END
+}
+
+int pff_precond_apply_dev(pff_problem* P, const double* r_dev, double* z_dev) {
+  API_BEGIN
+  need(P != nullptr && r_dev && z_dev, "NULL argument");
+  need(P->amg_u.built && P->amg_p.built, "call pff_precond_setup first");
+  const int64_t nu = (int64_t)P->dim * P->n_nodes;
+  pff::amg_vcycle(P->amg_u, r_dev, z_dev, P->stream);
+  pff::amg_vcycle(P->amg_p, r_dev + nu, z_dev + nu, P->stream);
+  API_END
+}
+
+int pff_linear_solve_dev(pff_problem* P, const pff_options* opts, const double* b_dev,
+                         double* x_dev, int* iters) {
+  API_BEGIN
+  need(P != nullptr && b_dev && x_dev, "NULL argument");
+  need(P->phi_assembled, "call pff_assemble first");
+  pff_options o;
+  pff_default_options(&o);
+  if (opts) o = *opts;
+  if (o.precond == PFF_PC_AMG) need(P->amg_u.built && P->amg_p.built, "call pff_precond_setup first");
+  if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
+    P->apply_variant = o.apply_variant;
+  const int64_t N = P->n_dofs;
+  pff::ensure_krylov(P, std::max(2, o.krylov_restart));
+  // scaled right-hand side Sinv .* b into scratch, solution into x
+  double* bs = P->Ftrial;
+  pff::scale_into(P->Sinv, b_dev, bs, N, P->stream);
+  int its = 0;
+  const int rc = pff::fgmres(P, o, bs, x_dev, &its);
+  if (iters) *iters = its;
+  sync(P);
+  if (rc != PFF_OK) {
+    pff::set_error(rc, "FGMRES did not converge");
+    return rc;
+  }
+  API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,1124 @@
+// Element-batched Q1 kernels for Formulation 1 (Section 2) and the Jacobian
+// blocks of Section 3.1 on tensor-product meshes.
+//
+// Every kernel is node-centric: one thread owns one mesh node and gathers the
+// contributions of its 2^d adjacent cells, so results are written once, without
+// atomics, and are bitwise reproducible.  Cells are axis-aligned boxes, so the
+// reference-to-physical map is diagonal (d/dx_l = (1/h_l) d/dxi_l); the
+// quadrature is the tensor 2^d-point Gauss rule.  Quadrature-point values use
+// the interpolated nodal phi, phi~ (then squared).
+//
+// Stencil layout: the Jacobian rows of node i couple to the 3^d neighbours
+// (i_x + o_x, i_y + o_y[, i_z + o_z]), o in {-1,0,1}; slot s = (o_x+1) +
+// 3(o_y+1) + 9(o_z+1) (increasing neighbour index).  Values are stored slot-
+// major so that consecutive threads read consecutive addresses:
+//   Kuu[((s*d + m)*d + n)*N + i]   (M_uu, d x d block per slot)
+//   Kpu[(s*d + n)*N + i]           (M_phi_u)
+//   Kpp[s*N + i]                   (M_phi_phi)
+#include "pff_internal.h"
+
+namespace pff {
+
+namespace {
+
+constexpr int BLK = 128;
+
+__device__ __forceinline__ double gauss_pt(int i) {
+  return i ? 0.78867513459481288225 : 0.21132486540518711775;   // (1 +- 1/sqrt 3) / 2
+}
+
+// Q1 shape value of local node a at Gauss point q of [0,1]^D
+template <int D>
+__device__ __forceinline__ double shp(int a, int q) {
+  double r = 1.0;
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    const double x = gauss_pt((q >> l) & 1);
+    r *= ((a >> l) & 1) ? x : 1.0 - x;
+  }
+  return r;
+}
+
+// reference derivative d N_a / d xi_l at Gauss point q
+template <int D>
+__device__ __forceinline__ double dshp(int a, int q, int l) {
+  double r = ((a >> l) & 1) ? 1.0 : -1.0;
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    if (k == l) continue;
+    const double x = gauss_pt((q >> k) & 1);
+    r *= ((a >> k) & 1) ? x : 1.0 - x;
+  }
+  return r;
+}
+
+template <int D>
+__device__ __forceinline__ void node_index(int64_t i, const MeshDev& m, int* idx) {
+  idx[0] = (int)(i % m.nn[0]);
+  const int64_t r = i / m.nn[0];
+  if (D == 2) {
+    idx[1] = (int)r;
+  } else {
+    idx[1] = (int)(r % m.nn[1]);
+    idx[2] = (int)(r / m.nn[1]);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ bool is_boundary(const int* idx, const MeshDev& m) {
+  bool b = false;
+#pragma unroll
+  for (int l = 0; l < D; ++l) b |= (idx[l] == 0) | (idx[l] == m.nn[l] - 1);
+  return b;
+}
+
+template <int D>
+__device__ __forceinline__ int64_t node_of(const int* idx, const MeshDev& m) {
+  int64_t r = idx[0] + (int64_t)m.nn[0] * idx[1];
+  if (D == 3) r += (int64_t)m.nn[0] * m.nn[1] * idx[2];
+  return r;
+}
+
+// Cell c adjacent to node idx: offset bit l of c = cell index - node index + 1.
+// Returns false if the cell lies outside the mesh.  ci receives the cell index,
+// h the edge lengths, and the node's local index inside the cell is (~c) & (2^D-1).
+template <int D>
+__device__ __forceinline__ bool adjacent_cell(const int* idx, int c, const MeshDev& m, int* ci,
+                                              double* h) {
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    ci[l] = idx[l] - 1 + ((c >> l) & 1);
+    if (ci[l] < 0 || ci[l] >= m.nc[l]) return false;
+  }
+#pragma unroll
+  for (int l = 0; l < D; ++l) h[l] = m.X[l][ci[l] + 1] - m.X[l][ci[l]];
+  return true;
+}
+
+template <int D>
+__device__ __forceinline__ int64_t cell_node(const int* ci, int b, const MeshDev& m) {
+  int64_t r = ci[0] + (b & 1) + (int64_t)m.nn[0] * (ci[1] + ((b >> 1) & 1));
+  if (D == 3) r += (int64_t)m.nn[0] * m.nn[1] * (ci[2] + ((b >> 2) & 1));
+  return r;
+}
+
+template <int D>
+__device__ __forceinline__ bool node_on_boundary(const int* ci, int b, const MeshDev& m) {
+  bool r = false;
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    const int k = ci[l] + ((b >> l) & 1);
+    r |= (k == 0) | (k == m.nn[l] - 1);
+  }
+  return r;
+}
+
+// stencil slot of trial node b of a cell at offset c relative to the row node
+template <int D>
+__device__ __forceinline__ int slot_of(int c, int b) {
+  int s = 0, mul = 1;
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    const int o = ((c >> l) & 1) + ((b >> l) & 1);   // offset + 1 in {0,1,2}
+    s += o * mul;
+    mul *= 3;
+  }
+  return s;
+}
+
+// ------------------------------------------------------------- residual ---
+// F = -r(U), r = left-hand sides of Eq. (E22ATW) / (E33ATW) tested with chi_i.
+template <int D>
+__global__ void __launch_bounds__(BLK) k_residual(MeshDev m, Material mat, int64_t n,
+                                                  const double* __restrict__ u,
+                                                  const double* __restrict__ phi,
+                                                  const double* __restrict__ phit,
+                                                  double* __restrict__ F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NA = 1 << D;
+  const double wq = D == 2 ? 0.25 : 0.125;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  double ru[D];
+#pragma unroll
+  for (int a = 0; a < D; ++a) ru[a] = 0.0;
+  double rp = 0.0;
+  const double k1 = 1.0 - mat.kappa;
+#pragma unroll 1
+  for (int c = 0; c < NA; ++c) {
+    int ci[3];
+    double h[3];
+    if (!adjacent_cell<D>(idx, c, m, ci, h)) continue;
+    const int ai = (~c) & (NA - 1);
+    double ih[D], vol = 1.0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      ih[l] = 1.0 / h[l];
+      vol *= h[l];
+    }
+    double ue[NA][D], pe[NA], te[NA];
+#pragma unroll
+    for (int b = 0; b < NA; ++b) {
+      const int64_t nb = cell_node<D>(ci, b, m);
+#pragma unroll
+      for (int a = 0; a < D; ++a) ue[b][a] = u[nb * D + a];
+      pe[b] = phi[nb];
+      te[b] = phit[nb];
+    }
+    const double JxW = wq * vol;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      double G[D][D], gp[D], ph = 0.0, pt = 0.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        gp[a] = 0.0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) G[a][l] = 0.0;
+      }
+#pragma unroll
+      for (int b = 0; b < NA; ++b) {
+        const double Nb = shp<D>(b, q);
+        ph += Nb * pe[b];
+        pt += Nb * te[b];
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          const double dN = dshp<D>(b, q, l) * ih[l];
+          gp[l] += dN * pe[b];
+#pragma unroll
+          for (int a = 0; a < D; ++a) G[a][l] += ue[b][a] * dN;
+        }
+      }
+      double div = 0.0;
+#pragma unroll
+      for (int l = 0; l < D; ++l) div += G[l][l];
+      double sig[D][D], sige = 0.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          const double e = 0.5 * (G[a][l] + G[l][a]);
+          sig[a][l] = 2.0 * mat.mu * e + (a == l ? mat.lam * div : 0.0);
+          sige += sig[a][l] * e;
+        }
+      const double g = k1 * pt * pt + mat.kappa;
+      const double Na = shp<D>(ai, q);
+      double dNa[D];
+#pragma unroll
+      for (int l = 0; l < D; ++l) dNa[l] = dshp<D>(ai, q, l) * ih[l];
+      const double pp = ph * ph * mat.p;
+#pragma unroll
+      for (int a = 0; a < D; ++a) {
+        double t = 0.0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) t += sig[a][l] * dNa[l];
+        ru[a] += JxW * (g * t + pp * dNa[a]);
+      }
+      double gdot = 0.0;
+#pragma unroll
+      for (int l = 0; l < D; ++l) gdot += gp[l] * dNa[l];
+      rp += JxW * ((k1 * ph * sige + 2.0 * ph * mat.p * div - mat.Gc / mat.eps * (1.0 - ph)) * Na +
+                   mat.Gc * mat.eps * gdot);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) F[i * D + a] = -ru[a];
+  F[(int64_t)D * n + i] = -rp;
+}
+
+// ---------------------------------------------------------- phi~, mass, S ---
+__global__ void k_phi_tilde(int64_t n, int first, const double* __restrict__ phi_old,
+                            const double* __restrict__ phi_prev, double* __restrict__ phit) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  if (first) {
+    phit[i] = phi_old[i];
+  } else {
+    const double v = 2.0 * phi_old[i] - phi_prev[i];
+    phit[i] = fmin(fmax(v, 0.0), 1.0);
+  }
+}
+
+// mass[i] = (1, chi_i); optionally S_phi[i] = G_c (chi_i, chi_i)/eps + G_c eps |grad chi_i|^2
+template <int D>
+__global__ void k_mass_and_sphi(MeshDev m, Material mat, int64_t n, double* __restrict__ mass,
+                                double* __restrict__ Sphi) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NA = 1 << D;
+  const double wq = D == 2 ? 0.25 : 0.125;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  double ms = 0.0, mm = 0.0, kk = 0.0;
+  for (int c = 0; c < NA; ++c) {
+    int ci[3];
+    double h[3];
+    if (!adjacent_cell<D>(idx, c, m, ci, h)) continue;
+    const int ai = (~c) & (NA - 1);
+    double vol = 1.0;
+    for (int l = 0; l < D; ++l) vol *= h[l];
+    const double JxW = wq * vol;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const double Na = shp<D>(ai, q);
+      ms += JxW * Na;
+      mm += JxW * Na * Na;
+      double g2 = 0.0;
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        const double d = dshp<D>(ai, q, l) / h[l];
+        g2 += d * d;
+      }
+      kk += JxW * g2;
+    }
+  }
+  if (mass) mass[i] = ms;
+  if (Sphi) Sphi[i] = mat.Gc * (mm / mat.eps + mat.eps * kk);
+}
+
+template <int D>
+__global__ void k_scaling_u(int64_t n, const double* __restrict__ Kuu, double* __restrict__ S,
+                            double* __restrict__ Sinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int center = D == 2 ? 4 : 13;
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    const double v = Kuu[((int64_t)(center * D + a) * D + a) * n + i];
+    S[i * D + a] = v;
+    Sinv[i * D + a] = 1.0 / v;
+  }
+}
+
+__global__ void k_invert(int64_t n, const double* __restrict__ S, double* __restrict__ Sinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) Sinv[i] = 1.0 / S[i];
+}
+
+// --------------------------------------------------------------- assembly ---
+// (M_uu)_ij = (g(phi~) sigma(chi_j), e(chi_i)); Dirichlet rows -> identity,
+// Dirichlet columns -> 0.
+template <int D>
+__global__ void __launch_bounds__(BLK) k_assemble_uu(MeshDev m, Material mat, int64_t n,
+                                                     const double* __restrict__ phit,
+                                                     double* __restrict__ Kuu) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NA = 1 << D;
+  constexpr int NS = D == 2 ? 9 : 27;
+  constexpr int center = D == 2 ? 4 : 13;
+  const double wq = D == 2 ? 0.25 : 0.125;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  for (int s = 0; s < NS * D * D; ++s) Kuu[(int64_t)s * n + i] = 0.0;
+  if (is_boundary<D>(idx, m)) {
+    for (int a = 0; a < D; ++a) Kuu[((int64_t)(center * D + a) * D + a) * n + i] = 1.0;
+    return;
+  }
+  const double k1 = 1.0 - mat.kappa;
+#pragma unroll 1
+  for (int c = 0; c < NA; ++c) {
+    int ci[3];
+    double h[3];
+    if (!adjacent_cell<D>(idx, c, m, ci, h)) continue;
+    const int ai = (~c) & (NA - 1);
+    double ih[D], vol = 1.0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      ih[l] = 1.0 / h[l];
+      vol *= h[l];
+    }
+    double te[NA];
+#pragma unroll
+    for (int b = 0; b < NA; ++b) te[b] = phit[cell_node<D>(ci, b, m)];
+    double Ke[NA][D][D];
+#pragma unroll
+    for (int b = 0; b < NA; ++b)
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int e = 0; e < D; ++e) Ke[b][a][e] = 0.0;
+    const double JxW = wq * vol;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      double pt = 0.0;
+#pragma unroll
+      for (int b = 0; b < NA; ++b) pt += shp<D>(b, q) * te[b];
+      const double wg = JxW * (k1 * pt * pt + mat.kappa);
+      double dNa[D];
+#pragma unroll
+      for (int l = 0; l < D; ++l) dNa[l] = dshp<D>(ai, q, l) * ih[l];
+#pragma unroll
+      for (int b = 0; b < NA; ++b) {
+        double dNb[D], dd = 0.0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          dNb[l] = dshp<D>(b, q, l) * ih[l];
+          dd += dNa[l] * dNb[l];
+        }
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int e = 0; e < D; ++e)
+            Ke[b][a][e] += wg * (mat.mu * ((a == e ? dd : 0.0) + dNa[e] * dNb[a]) +
+                                 mat.lam * dNa[a] * dNb[e]);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < NA; ++b) {
+      if (node_on_boundary<D>(ci, b, m)) continue;
+      const int s = slot_of<D>(c, b);
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int e = 0; e < D; ++e) Kuu[((int64_t)(s * D + a) * D + e) * n + i] += Ke[b][a][e];
+    }
+  }
+}
+
+// (M_phi_u)_ij = 2(1-kappa)(phi sigma(chi_j^u):e(u), chi_i) + 2p(phi div chi_j^u, chi_i)
+// (M_phi_phi)_ij = ((1-kappa) sigma(u):e(u) + 2p div u + G_c/eps) (chi_j, chi_i)
+//                 + G_c eps (grad chi_j, grad chi_i)
+// Dirichlet displacement columns of M_phi_u are zero (eliminated DoFs).
+template <int D>
+__global__ void __launch_bounds__(BLK) k_assemble_phi(MeshDev m, Material mat, int64_t n,
+                                                      const double* __restrict__ u,
+                                                      const double* __restrict__ phi,
+                                                      double* __restrict__ Kpu,
+                                                      double* __restrict__ Kpp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NA = 1 << D;
+  constexpr int NS = D == 2 ? 9 : 27;
+  const double wq = D == 2 ? 0.25 : 0.125;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  for (int s = 0; s < NS * D; ++s) Kpu[(int64_t)s * n + i] = 0.0;
+  for (int s = 0; s < NS; ++s) Kpp[(int64_t)s * n + i] = 0.0;
+  const double k1 = 1.0 - mat.kappa;
+#pragma unroll 1
+  for (int c = 0; c < NA; ++c) {
+    int ci[3];
+    double h[3];
+    if (!adjacent_cell<D>(idx, c, m, ci, h)) continue;
+    const int ai = (~c) & (NA - 1);
+    double ih[D], vol = 1.0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      ih[l] = 1.0 / h[l];
+      vol *= h[l];
+    }
+    double ue[NA][D], pe[NA];
+#pragma unroll
+    for (int b = 0; b < NA; ++b) {
+      const int64_t nb = cell_node<D>(ci, b, m);
+#pragma unroll
+      for (int a = 0; a < D; ++a) ue[b][a] = u[nb * D + a];
+      pe[b] = phi[nb];
+    }
+    double Kpu_e[NA][D], Kpp_e[NA];
+#pragma unroll
+    for (int b = 0; b < NA; ++b) {
+      Kpp_e[b] = 0.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a) Kpu_e[b][a] = 0.0;
+    }
+    const double JxW = wq * vol;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      double G[D][D], ph = 0.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int l = 0; l < D; ++l) G[a][l] = 0.0;
+#pragma unroll
+      for (int b = 0; b < NA; ++b) {
+        ph += shp<D>(b, q) * pe[b];
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          const double dN = dshp<D>(b, q, l) * ih[l];
+#pragma unroll
+          for (int a = 0; a < D; ++a) G[a][l] += ue[b][a] * dN;
+        }
+      }
+      double div = 0.0;
+#pragma unroll
+      for (int l = 0; l < D; ++l) div += G[l][l];
+      double sig[D][D], sige = 0.0;
+#pragma unroll
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          const double e = 0.5 * (G[a][l] + G[l][a]);
+          sig[a][l] = 2.0 * mat.mu * e + (a == l ? mat.lam * div : 0.0);
+          sige += sig[a][l] * e;
+        }
+      const double c0 = k1 * sige + 2.0 * mat.p * div + mat.Gc / mat.eps;
+      const double Na = shp<D>(ai, q);
+      double dNa[D];
+#pragma unroll
+      for (int l = 0; l < D; ++l) dNa[l] = dshp<D>(ai, q, l) * ih[l];
+      const double wa = JxW * Na;
+      const double cs = 2.0 * k1 * ph, cp = 2.0 * mat.p * ph;
+#pragma unroll
+      for (int b = 0; b < NA; ++b) {
+        const double Nb = shp<D>(b, q);
+        double dNb[D], dd = 0.0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          dNb[l] = dshp<D>(b, q, l) * ih[l];
+          dd += dNa[l] * dNb[l];
+        }
+#pragma unroll
+        for (int e = 0; e < D; ++e) {
+          double t = 0.0;
+#pragma unroll
+          for (int l = 0; l < D; ++l) t += sig[e][l] * dNb[l];
+          Kpu_e[b][e] += wa * (cs * t + cp * dNb[e]);
+        }
+        Kpp_e[b] += JxW * (c0 * Na * Nb + mat.Gc * mat.eps * dd);
+      }
+    }
+#pragma unroll
+    for (int b = 0; b < NA; ++b) {
+      const int s = slot_of<D>(c, b);
+      Kpp[(int64_t)s * n + i] += Kpp_e[b];
+      if (node_on_boundary<D>(ci, b, m)) continue;
+#pragma unroll
+      for (int e = 0; e < D; ++e) Kpu[(int64_t)(s * D + e) * n + i] += Kpu_e[b][e];
+    }
+  }
+}
+
+// neighbour node of slot s, or -1 outside the mesh
+template <int D>
+__device__ __forceinline__ int64_t neighbour(const int* idx, int s, const MeshDev& m) {
+  int o[3];
+  o[0] = s % 3 - 1;
+  o[1] = (s / 3) % 3 - 1;
+  o[2] = s / 9 - 1;
+  int j[3];
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    j[l] = idx[l] + o[l];
+    if (j[l] < 0 || j[l] >= m.nn[l]) return -1;
+  }
+  return node_of<D>(j, m);
+}
+
+// Reduced right-hand side and active-set masking of the phase-field rows.
+template <int D>
+__global__ void k_reduce_phi(MeshDev m, int64_t n, const uint8_t* __restrict__ active,
+                             const double* __restrict__ phi, const double* __restrict__ phi_old,
+                             const double* __restrict__ F, double* __restrict__ Ft,
+                             double* __restrict__ dUA, double* __restrict__ Kpu,
+                             double* __restrict__ Kpp) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NS = D == 2 ? 9 : 27;
+  constexpr int center = D == 2 ? 4 : 13;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  const bool bnd = is_boundary<D>(idx, m);
+#pragma unroll
+  for (int a = 0; a < D; ++a) {
+    Ft[i * D + a] = bnd ? 0.0 : F[i * D + a];
+    dUA[i * D + a] = 0.0;
+  }
+  const int64_t ip = (int64_t)D * n + i;
+  if (active[i]) {
+    dUA[ip] = phi_old[i] - phi[i];
+    Ft[ip] = 0.0;
+    for (int s = 0; s < NS; ++s) Kpp[(int64_t)s * n + i] = (s == center) ? 1.0 : 0.0;
+    for (int s = 0; s < NS * D; ++s) Kpu[(int64_t)s * n + i] = 0.0;
+    return;
+  }
+  dUA[ip] = 0.0;
+  double f = F[ip];
+  for (int s = 0; s < NS; ++s) {
+    const int64_t j = neighbour<D>(idx, s, m);
+    if (j < 0 || !active[j]) continue;
+    f -= Kpp[(int64_t)s * n + i] * (phi_old[j] - phi[j]);
+    Kpp[(int64_t)s * n + i] = 0.0;
+  }
+  Ft[ip] = f;
+}
+
+// y = Sinv .* (G~ x) from the assembled (reduced) stencils.
+template <int D>
+__global__ void __launch_bounds__(256) k_apply_assembled(MeshDev m, int64_t n,
+                                                         const double* __restrict__ Kuu,
+                                                         const double* __restrict__ Kpu,
+                                                         const double* __restrict__ Kpp,
+                                                         const double* __restrict__ x,
+                                                         double* __restrict__ y,
+                                                         const double* __restrict__ Sinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NS = D == 2 ? 9 : 27;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  double yu[D], yp = 0.0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) yu[a] = 0.0;
+  const double* xp = x + (int64_t)D * n;
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int64_t j = neighbour<D>(idx, s, m);
+    if (j < 0) continue;
+    double xu[D];
+#pragma unroll
+    for (int e = 0; e < D; ++e) xu[e] = x[j * D + e];
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int e = 0; e < D; ++e) yu[a] += Kuu[((int64_t)(s * D + a) * D + e) * n + i] * xu[e];
+#pragma unroll
+    for (int e = 0; e < D; ++e) yp += Kpu[(int64_t)(s * D + e) * n + i] * xu[e];
+    yp += Kpp[(int64_t)s * n + i] * xp[j];
+  }
+  if (Sinv) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) yu[a] *= Sinv[i * D + a];
+    yp *= Sinv[(int64_t)D * n + i];
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) y[i * D + a] = yu[a];
+  y[(int64_t)D * n + i] = yp;
+}
+
+// y = Sinv .* (G~ x), matrix-free: the Section 3.1 blocks applied cell by cell
+// at the quadrature points; Dirichlet / active rows are identity rows and the
+// corresponding columns of x are treated as zero.
+template <int D>
+__global__ void __launch_bounds__(BLK) k_apply_matfree(MeshDev m, Material mat, int64_t n,
+                                                       const double* __restrict__ u,
+                                                       const double* __restrict__ phi,
+                                                       const double* __restrict__ phit,
+                                                       const uint8_t* __restrict__ active,
+                                                       const double* __restrict__ x,
+                                                       double* __restrict__ y,
+                                                       const double* __restrict__ Sinv) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NA = 1 << D;
+  const double wq = D == 2 ? 0.25 : 0.125;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  const bool bnd = is_boundary<D>(idx, m);
+  const bool act = active[i] != 0;
+  const double* xp = x + (int64_t)D * n;
+  double yu[D], yp = 0.0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) yu[a] = 0.0;
+  const double k1 = 1.0 - mat.kappa;
+  if (!(bnd && act)) {
+#pragma unroll 1
+    for (int c = 0; c < NA; ++c) {
+      int ci[3];
+      double h[3];
+      if (!adjacent_cell<D>(idx, c, m, ci, h)) continue;
+      const int ai = (~c) & (NA - 1);
+      double ih[D], vol = 1.0;
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        ih[l] = 1.0 / h[l];
+        vol *= h[l];
+      }
+      double ue[NA][D], xe[NA][D], pe[NA], te[NA], xpe[NA];
+#pragma unroll
+      for (int b = 0; b < NA; ++b) {
+        const int64_t nb = cell_node<D>(ci, b, m);
+        const bool bb = node_on_boundary<D>(ci, b, m);
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          ue[b][a] = u[nb * D + a];
+          xe[b][a] = bb ? 0.0 : x[nb * D + a];
+        }
+        pe[b] = phi[nb];
+        te[b] = phit[nb];
+        xpe[b] = active[nb] ? 0.0 : xp[nb];
+      }
+      const double JxW = wq * vol;
+#pragma unroll
+      for (int q = 0; q < NA; ++q) {
+        double G[D][D], Gx[D][D], gx[D], ph = 0.0, pt = 0.0, xq = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+          gx[a] = 0.0;
+#pragma unroll
+          for (int l = 0; l < D; ++l) G[a][l] = Gx[a][l] = 0.0;
+        }
+#pragma unroll
+        for (int b = 0; b < NA; ++b) {
+          const double Nb = shp<D>(b, q);
+          ph += Nb * pe[b];
+          pt += Nb * te[b];
+          xq += Nb * xpe[b];
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            const double dN = dshp<D>(b, q, l) * ih[l];
+            gx[l] += dN * xpe[b];
+#pragma unroll
+            for (int a = 0; a < D; ++a) {
+              G[a][l] += ue[b][a] * dN;
+              Gx[a][l] += xe[b][a] * dN;
+            }
+          }
+        }
+        double div = 0.0, divx = 0.0;
+#pragma unroll
+        for (int l = 0; l < D; ++l) {
+          div += G[l][l];
+          divx += Gx[l][l];
+        }
+        double sigx[D][D], sige = 0.0, sigex = 0.0;
+#pragma unroll
+        for (int a = 0; a < D; ++a)
+#pragma unroll
+          for (int l = 0; l < D; ++l) {
+            const double e = 0.5 * (G[a][l] + G[l][a]);
+            const double ex = 0.5 * (Gx[a][l] + Gx[l][a]);
+            const double s = 2.0 * mat.mu * e + (a == l ? mat.lam * div : 0.0);
+            sigx[a][l] = 2.0 * mat.mu * ex + (a == l ? mat.lam * divx : 0.0);
+            sige += s * e;
+            sigex += s * ex;
+          }
+        const double Na = shp<D>(ai, q);
+        double dNa[D];
+#pragma unroll
+        for (int l = 0; l < D; ++l) dNa[l] = dshp<D>(ai, q, l) * ih[l];
+        if (!bnd) {
+          const double wg = JxW * (k1 * pt * pt + mat.kappa);
+#pragma unroll
+          for (int a = 0; a < D; ++a) {
+            double t = 0.0;
+#pragma unroll
+            for (int l = 0; l < D; ++l) t += sigx[a][l] * dNa[l];
+            yu[a] += wg * t;
+          }
+        }
+        if (!act) {
+          const double c0 = k1 * sige + 2.0 * mat.p * div + mat.Gc / mat.eps;
+          double gdot = 0.0;
+#pragma unroll
+          for (int l = 0; l < D; ++l) gdot += gx[l] * dNa[l];
+          yp += JxW * (Na * (2.0 * k1 * ph * sigex + 2.0 * mat.p * ph * divx + c0 * xq) +
+                       mat.Gc * mat.eps * gdot);
+        }
+      }
+    }
+  }
+  if (bnd) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) yu[a] = x[i * D + a];
+  }
+  if (act) yp = xp[i];
+  if (Sinv) {
+#pragma unroll
+    for (int a = 0; a < D; ++a) yu[a] *= Sinv[i * D + a];
+    yp *= Sinv[(int64_t)D * n + i];
+  }
+#pragma unroll
+  for (int a = 0; a < D; ++a) y[i * D + a] = yu[a];
+  y[(int64_t)D * n + i] = yp;
+}
+
+// ------------------------------------------------------------- active set ---
+__global__ void k_active_set(int64_t n, int dim, const double* __restrict__ F,
+                             const double* __restrict__ mass, const double* __restrict__ phi,
+                             const double* __restrict__ phi_old, double c, int have_prev,
+                             int lock_after, uint8_t* __restrict__ raw_prev,
+                             int* __restrict__ toggles, uint8_t* __restrict__ locked,
+                             uint8_t* __restrict__ active, double* __restrict__ indicator,
+                             int* __restrict__ counters) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  bool A = false, changed = false;
+  if (i < n) {
+    const double ind = F[(int64_t)dim * n + i] / mass[i] + c * (phi[i] - phi_old[i]);
+    const bool raw = ind > 0.0;
+    bool lk = false;
+    if (have_prev) {
+      const int tg = toggles[i] + (raw != (raw_prev[i] != 0));
+      toggles[i] = tg;
+      lk = locked[i] || tg >= lock_after;
+      locked[i] = lk;
+      A = raw || lk;
+      changed = A != (active[i] != 0);
+    } else {
+      toggles[i] = 0;
+      locked[i] = 0;
+      A = raw;
+    }
+    raw_prev[i] = raw;
+    active[i] = A;
+    if (indicator) indicator[i] = ind;
+  }
+  const unsigned na = __ballot_sync(0xffffffffu, A);
+  const unsigned nc = __ballot_sync(0xffffffffu, changed);
+  if ((threadIdx.x & 31) == 0) {
+    if (na) atomicAdd(&counters[0], __popc(na));
+    if (nc) atomicAdd(&counters[1], __popc(nc));
+  }
+}
+
+// rho_i = F_i / S_i on free rows (not Dirichlet, not active), 0 elsewhere
+template <int D>
+__global__ void k_scaled_reduced(MeshDev m, int64_t n, const double* __restrict__ F,
+                                 const double* __restrict__ Sinv,
+                                 const uint8_t* __restrict__ active, double* __restrict__ rho) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  const bool bnd = is_boundary<D>(idx, m);
+#pragma unroll
+  for (int a = 0; a < D; ++a) rho[i * D + a] = bnd ? 0.0 : F[i * D + a] * Sinv[i * D + a];
+  const int64_t ip = (int64_t)D * n + i;
+  rho[ip] = active[i] ? 0.0 : F[ip] * Sinv[ip];
+}
+
+// ------------------------------------------------------------ BSR helpers ---
+template <int D>
+__global__ void k_stencil_count(MeshDev m, int64_t n, int* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NS = D == 2 ? 9 : 27;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  int k = 0;
+  for (int s = 0; s < NS; ++s) k += neighbour<D>(idx, s, m) >= 0;
+  cnt[i] = k;
+}
+
+template <int D>
+__global__ void k_stencil_cols(MeshDev m, int64_t n, const int* __restrict__ rowptr,
+                               int* __restrict__ col) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NS = D == 2 ? 9 : 27;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  int k = rowptr[i];
+  for (int s = 0; s < NS; ++s) {
+    const int64_t j = neighbour<D>(idx, s, m);
+    if (j >= 0) col[k++] = (int)j;
+  }
+}
+
+template <int D>
+__global__ void k_stencil_vals(MeshDev m, int64_t n, int b, const double* __restrict__ K,
+                               const int* __restrict__ rowptr, double* __restrict__ val) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NS = D == 2 ? 9 : 27;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  int64_t k = rowptr[i];
+  const int bb = b * b;
+  for (int s = 0; s < NS; ++s) {
+    if (neighbour<D>(idx, s, m) < 0) continue;
+    for (int e = 0; e < bb; ++e) val[k * bb + e] = K[((int64_t)s * bb + e) * n + i];
+    ++k;
+  }
+}
+
+template <int D>
+__global__ void k_rigid_modes(MeshDev m, int64_t n, double* __restrict__ B) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  double x[3] = {0, 0, 0};
+  for (int l = 0; l < D; ++l) x[l] = m.X[l][idx[l]];
+  const int64_t ld = (int64_t)n * D;
+  constexpr int NNS = D == 2 ? 3 : 6;
+  double v[NNS][D];
+  for (int k = 0; k < NNS; ++k)
+    for (int a = 0; a < D; ++a) v[k][a] = 0.0;
+  for (int a = 0; a < D; ++a) v[a][a] = 1.0;
+  if (D == 2) {
+    v[2][0] = -x[1];
+    v[2][1] = x[0];
+  } else {
+    v[3][0] = -x[1];
+    v[3][1] = x[0];
+    v[4][1] = -x[2];
+    v[4][2] = x[1];
+    v[5][0] = x[2];
+    v[5][2] = -x[0];
+  }
+  for (int k = 0; k < NNS; ++k)
+    for (int a = 0; a < D; ++a) B[k * ld + i * D + a] = v[k][a];
+}
+
+// -------------------------------------------------------------- functionals --
+template <int D>
+__global__ void k_tcv(MeshDev m, int64_t ncell, const double* __restrict__ u,
+                      const double* __restrict__ phi, double* __restrict__ partials) {
+  constexpr int NA = 1 << D;
+  const double wq = D == 2 ? 0.25 : 0.125;
+  double acc = 0.0;
+  for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < ncell;
+       c += (int64_t)gridDim.x * blockDim.x) {
+    int ci[3];
+    ci[0] = (int)(c % m.nc[0]);
+    const int64_t r = c / m.nc[0];
+    if (D == 2) {
+      ci[1] = (int)r;
+    } else {
+      ci[1] = (int)(r % m.nc[1]);
+      ci[2] = (int)(r / m.nc[1]);
+    }
+    double h[D], vol = 1.0;
+    for (int l = 0; l < D; ++l) {
+      h[l] = m.X[l][ci[l] + 1] - m.X[l][ci[l]];
+      vol *= h[l];
+    }
+    double ue[NA][D], pe[NA];
+#pragma unroll
+    for (int b = 0; b < NA; ++b) {
+      const int64_t nb = cell_node<D>(ci, b, m);
+      for (int a = 0; a < D; ++a) ue[b][a] = u[nb * D + a];
+      pe[b] = phi[nb];
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      double uq[D], gp[D];
+      for (int a = 0; a < D; ++a) uq[a] = gp[a] = 0.0;
+#pragma unroll
+      for (int b = 0; b < NA; ++b) {
+        const double Nb = shp<D>(b, q);
+        for (int a = 0; a < D; ++a) {
+          uq[a] += Nb * ue[b][a];
+          gp[a] += dshp<D>(b, q, a) / h[a] * pe[b];
+        }
+      }
+      double dot = 0.0;
+      for (int a = 0; a < D; ++a) dot += uq[a] * gp[a];
+      s += dot;
+    }
+    acc += wq * vol * s;
+  }
+  // block reduction (fixed order)
+  __shared__ double sh[256];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void k_sum_partials(const double* __restrict__ partials, int np, double* __restrict__ out) {
+  __shared__ double sh[256];
+  double a = 0.0;
+  for (int k = threadIdx.x; k < np; k += blockDim.x) a += partials[k];
+  sh[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = sh[0];
+}
+
+// COD: block per (column, point) entry; threads walk the cells along the last axis
+template <int D>
+__global__ void k_cod(MeshDev m, const CodColumn* __restrict__ cols, const double* __restrict__ u,
+                      const double* __restrict__ phi, double* __restrict__ out) {
+  const CodColumn cc = cols[blockIdx.x];
+  constexpr int NA = 1 << D;
+  constexpr int L = D - 1;   // integration axis
+  double acc = 0.0;
+  for (int j = threadIdx.x; j < m.nc[L]; j += blockDim.x) {
+    int ci[3];
+    double loc[3], h[3];
+    for (int a = 0; a < L; ++a) {
+      ci[a] = cc.col[a];
+      loc[a] = cc.xi[a];
+    }
+    ci[L] = j;
+    for (int l = 0; l < D; ++l) h[l] = m.X[l][ci[l] + 1] - m.X[l][ci[l]];
+    double ue[NA][D], pe[NA];
+    for (int b = 0; b < NA; ++b) {
+      const int64_t nb = cell_node<D>(ci, b, m);
+      for (int a = 0; a < D; ++a) ue[b][a] = u[nb * D + a];
+      pe[b] = phi[nb];
+    }
+    for (int g = 0; g < 2; ++g) {
+      loc[L] = gauss_pt(g);
+      double uq[D], gp[D];
+      for (int a = 0; a < D; ++a) uq[a] = gp[a] = 0.0;
+      for (int b = 0; b < NA; ++b) {
+        double f[D];
+        for (int l = 0; l < D; ++l) f[l] = ((b >> l) & 1) ? loc[l] : 1.0 - loc[l];
+        double Nb = 1.0;
+        for (int l = 0; l < D; ++l) Nb *= f[l];
+        for (int a = 0; a < D; ++a) uq[a] += Nb * ue[b][a];
+        for (int l = 0; l < D; ++l) {
+          double d = ((b >> l) & 1) ? 1.0 : -1.0;
+          for (int k = 0; k < D; ++k)
+            if (k != l) d *= f[k];
+          gp[l] += d / h[l] * pe[b];
+        }
+      }
+      double dot = 0.0;
+      for (int a = 0; a < D; ++a) dot += uq[a] * gp[a];
+      acc += 0.5 * h[L] * dot;
+    }
+  }
+  __shared__ double sh[128];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o) sh[threadIdx.x] += sh[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = cc.w * sh[0];
+}
+
+}  // namespace
+
+// ----------------------------------------------------------------- launchers --
+#define DISPATCH(dim, ...) \
+  do {                     \
+    if ((dim) == 2) {      \
+      constexpr int D = 2; \
+      __VA_ARGS__;         \
+    } else {               \
+      constexpr int D = 3; \
+      __VA_ARGS__;         \
+    }                      \
+  } while (0)
+
+void launch_phi_tilde(const MeshDev& m, int64_t n, int steps_done, const double* phi_old,
+                      const double* phi_prev, double* phit, cudaStream_t s) {
+  k_phi_tilde<<<grid_for(n, 256), 256, 0, s>>>(n, steps_done == 0, phi_old, phi_prev, phit);
+  PFF_LAUNCH("phi_tilde");
+}
+
+void launch_lumped_mass(const MeshDev& m, int64_t n, double* mass, cudaStream_t s) {
+  Material dummy{1, 0, 1, 0, 1, 0, 0, 0};
+  DISPATCH(m.dim, (k_mass_and_sphi<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, dummy, n, mass, nullptr)));
+  PFF_LAUNCH("lumped_mass");
+}
+
+void launch_residual(const MeshDev& m, const Material& mat, int64_t n, const double* u,
+                     const double* phi, const double* phit, double* F, cudaStream_t s) {
+  DISPATCH(m.dim, (k_residual<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, u, phi, phit, F)));
+  PFF_LAUNCH("residual");
+}
+
+void launch_assemble_uu(const MeshDev& m, const Material& mat, int64_t n, const double* phit,
+                        double* Kuu, cudaStream_t s) {
+  DISPATCH(m.dim, (k_assemble_uu<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, phit, Kuu)));
+  PFF_LAUNCH("assemble_uu");
+}
+
+void launch_assemble_phi(const MeshDev& m, const Material& mat, int64_t n, const double* u,
+                         const double* phi, double* Kpu, double* Kpp, cudaStream_t s) {
+  DISPATCH(m.dim,
+           (k_assemble_phi<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, u, phi, Kpu, Kpp)));
+  PFF_LAUNCH("assemble_phi");
+}
+
+void launch_scaling(const MeshDev& m, const Material& mat, int64_t n, const double* Kuu,
+                    double* S, double* Sinv, cudaStream_t s) {
+  const int d = m.dim;
+  DISPATCH(d, (k_scaling_u<D><<<grid_for(n, 256), 256, 0, s>>>(n, Kuu, S, Sinv)));
+  DISPATCH(d, (k_mass_and_sphi<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, nullptr,
+                                                                    S + (int64_t)d * n)));
+  k_invert<<<grid_for(n, 256), 256, 0, s>>>(n, S + (int64_t)d * n, Sinv + (int64_t)d * n);
+  PFF_LAUNCH("scaling");
+}
+
+void launch_reduce_phi(const MeshDev& m, int64_t n, const uint8_t* active, const double* phi,
+                       const double* phi_old, const double* F, double* Ft, double* dUA,
+                       double* Kpu, double* Kpp, cudaStream_t s) {
+  DISPATCH(m.dim, (k_reduce_phi<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, active, phi, phi_old, F,
+                                                                     Ft, dUA, Kpu, Kpp)));
+  PFF_LAUNCH("reduce_phi");
+}
+
+void launch_apply_assembled(const MeshDev& m, int64_t n, const double* Kuu, const double* Kpu,
+                            const double* Kpp, const double* x, double* y, const double* Sinv,
+                            cudaStream_t s) {
+  DISPATCH(m.dim, (k_apply_assembled<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, Kuu, Kpu, Kpp, x, y,
+                                                                         Sinv)));
+  PFF_LAUNCH("apply_assembled");
+}
+
+void launch_apply_matfree(const MeshDev& m, const Material& mat, int64_t n, const double* u,
+                          const double* phi, const double* phit, const uint8_t* active,
+                          const double* x, double* y, const double* Sinv, cudaStream_t s) {
+  DISPATCH(m.dim, (k_apply_matfree<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, u, phi, phit,
+                                                                       active, x, y, Sinv)));
+  PFF_LAUNCH("apply_matfree");
+}
+
+void launch_active_set(int64_t n, int dim, const double* F, const double* mass, const double* phi,
+                       const double* phi_old, double c, int have_prev, int lock_after,
+                       uint8_t* raw_prev, int* toggles, uint8_t* locked, uint8_t* active,
+                       uint8_t* /*active_prev*/, double* indicator, int* counters,
+                       cudaStream_t s) {
+  PFF_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int), s));
+  k_active_set<<<grid_for(n, 256), 256, 0, s>>>(n, dim, F, mass, phi, phi_old, c, have_prev,
+                                                lock_after, raw_prev, toggles, locked, active,
+                                                indicator, counters);
+  PFF_LAUNCH("active_set");
+}
+
+void launch_scaled_reduced(const MeshDev& m, int64_t n, const double* F, const double* Sinv,
+                           const uint8_t* active, double* rho, cudaStream_t s) {
+  DISPATCH(m.dim, (k_scaled_reduced<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, F, Sinv, active, rho)));
+  PFF_LAUNCH("scaled_reduced");
+}
+
+void build_stencil_bsr_structure(const MeshDev& m, int64_t n, int b, Bsr& A, cudaStream_t s) {
+  A.nrows = A.ncols = (int)n;
+  A.br = A.bc = b;
+  A.rowptr = dalloc<int>(n + 1);
+  int* cnt = dalloc<int>(n + 1);
+  DISPATCH(m.dim, (k_stencil_count<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, cnt)));
+  PFF_LAUNCH("stencil_count");
+  int total = 0;
+  exclusive_scan_int(cnt, A.rowptr, (int)n, &total, s);
+  A.nnzb = total;
+  A.col = dalloc<int>(total);
+  A.val = dalloc<double>((size_t)total * b * b);
+  DISPATCH(m.dim, (k_stencil_cols<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, A.rowptr, A.col)));
+  PFF_LAUNCH("stencil_cols");
+  PFF_CUDA(cudaStreamSynchronize(s));
+  dfree(cnt);
+}
+
+void launch_stencil_to_bsr(const MeshDev& m, int64_t n, int b, const double* K, const Bsr& A,
+                           cudaStream_t s) {
+  DISPATCH(m.dim, (k_stencil_vals<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, b, K, A.rowptr, A.val)));
+  PFF_LAUNCH("stencil_vals");
+}
+
+void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s) {
+  DISPATCH(m.dim, (k_rigid_modes<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, B)));
+  PFF_LAUNCH("rigid_modes");
+}
+
+void tcv_dev(const MeshDev& m, int64_t n_cells, const double* u, const double* phi, double* out,
+             double* partials, cudaStream_t s) {
+  const int nb = (int)std::min<int64_t>(RED_PARTIALS, (n_cells + 255) / 256);
+  DISPATCH(m.dim, (k_tcv<D><<<nb, 256, 0, s>>>(m, n_cells, u, phi, partials)));
+  k_sum_partials<<<1, 256, 0, s>>>(partials, nb, out);
+  PFF_LAUNCH("tcv");
+}
+
+void cod_dev(const MeshDev& m, const CodColumn* cols, int ncols, const double* u, const double* phi,
+             double* out, int /*npts*/, cudaStream_t s) {
+  if (ncols == 0) return;
+  DISPATCH(m.dim, (k_cod<D><<<ncols, 128, 0, s>>>(m, cols, u, phi, out)));
+  PFF_LAUNCH("cod");
+}
+
+}  // namespace pff

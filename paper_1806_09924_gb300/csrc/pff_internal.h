@@ -1,0 +1,276 @@
+// Internal declarations of the GB300 phase-field fracture library.
+//
+// Layers (bottom to top):
+//   fe_kernels.cu  -- Q1 element-batched kernels: residual of Formulation 1,
+//                     stencil assembly of the Section 3.1 Jacobian blocks,
+//                     matrix-free and assembled Jacobian applies, active set,
+//                     phi~ extrapolation, lumped mass, scaling, TCV / COD.
+//   linalg.cu      -- deterministic reductions, scans, vector kernels, BSR SpMV,
+//                     Chebyshev smoothing, dense coarse solve.
+//   amg.cu         -- smoothed-aggregation AMG hierarchy built on the device
+//                     and the V-cycle.
+//   solver.cu      -- FGMRES with the block-diagonal preconditioner and the
+//                     semi-smooth Newton / primal-dual active-set driver.
+//   capi.cu        -- the extern "C" entry points of include/pff.h.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pff.h"
+
+namespace pff {
+
+// ------------------------------------------------------------------ errors --
+struct Error {
+  int code;
+  std::string msg;
+};
+
+void set_error(int code, const std::string& msg);
+[[noreturn]] void fail(int code, const std::string& msg);
+void check_cuda(cudaError_t e, const char* what);
+#define PFF_CUDA(x) ::pff::check_cuda((x), #x)
+#define PFF_LAUNCH(what) ::pff::check_cuda(cudaGetLastError(), what)
+
+// ------------------------------------------------------------ device memory --
+void* dmalloc(size_t bytes);
+void dfree(void* p);
+template <class T>
+T* dalloc(size_t n) {
+  return static_cast<T*>(dmalloc(n * sizeof(T) + 16));
+}
+
+// grid size for n threads of block b, capped
+inline unsigned grid_for(int64_t n, int block, int64_t cap = 1 << 30) {
+  int64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+// ------------------------------------------------------------------- mesh ---
+struct MeshDev {
+  int dim;
+  int nn[3];      // nodes per axis
+  int nc[3];      // cells per axis
+  const double* X[3];  // device axis coordinates
+};
+
+// ------------------------------------------------------------ BSR matrices --
+struct Bsr {
+  int nrows = 0, ncols = 0;   // block rows / cols
+  int br = 1, bc = 1;         // block size
+  int64_t nnzb = 0;
+  int* rowptr = nullptr;      // nrows + 1
+  int* col = nullptr;         // nnzb, sorted within a row
+  double* val = nullptr;      // nnzb * br * bc, block row-major
+  float* valf = nullptr;      // FP32 copy (mixed precision)
+  void release();
+};
+
+// ------------------------------------------------------------------- AMG ---
+struct AmgLevel {
+  Bsr A, P, R;
+  double* dinv = nullptr;     // inverse scalar diagonal (n scalar rows)
+  float* dinvf = nullptr;
+  double lmax = 1.0;          // estimate of the largest eigenvalue of D^-1 A
+  int n = 0;                  // scalar rows
+  bool terminal = false;      // no coarser level (every row isolated): smoothing only
+  // V-cycle work vectors (stored as doubles; FP32 cycles reinterpret them)
+  double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
+};
+
+struct Amg {
+  std::vector<AmgLevel> lev;
+  int nc = 0;                 // coarsest size (scalar)
+  double* cinv = nullptr;     // dense inverse of the coarsest operator (nc x nc)
+  float* cinvf = nullptr;
+  double *cx = nullptr, *cb = nullptr;
+  bool mixed = false;
+  int cheb_degree = 2;
+  int built = 0;
+  void release();
+};
+
+struct AmgParams {
+  double theta = 0.08;
+  int coarse_max = 320;
+  int cheb_degree = 2;
+  bool mixed = false;
+  int max_levels = 20;
+};
+
+// Build a hierarchy for the block matrix A (FP64 values, block size br) with
+// near-null space B (n scalar rows x nns columns, column-major).  A is copied.
+void amg_build(Amg& amg, const Bsr& A, const double* B, int nns, const AmgParams& prm,
+               cudaStream_t s);
+// z = V-cycle(r) (FP64 in / out; the cycle runs in FP32 when amg.mixed).
+void amg_vcycle(Amg& amg, const double* r, double* z, cudaStream_t s);
+
+// ---------------------------------------------------------------- linalg ---
+// Deterministic two-pass reductions: the result lands in a device double.
+void dot_dev(const double* x, const double* y, int64_t n, double* out, double* partials,
+             cudaStream_t s);
+void nrm_inf_dev(const double* x, int64_t n, double* out, double* partials, cudaStream_t s);
+// Fused: out[k] = <V_k, w> for k < nv (V stored as nv vectors of stride ld).
+void multidot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* out,
+                  double* partials, cudaStream_t s);
+// w -= sum_k h[k] V_k   (h on device)
+void multi_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n,
+                    double sign, cudaStream_t s);
+void exclusive_scan_int(const int* in, int* out, int n, int* total_host, cudaStream_t s);
+
+enum { RED_PARTIALS = 1024 };   // partial buffer length needed by the reductions
+
+// BSR SpMV y = alpha A x + beta y (FP64 or FP32 values / vectors)
+void bsr_spmv(const Bsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
+void bsr_spmv_f(const Bsr& A, const float* x, float* y, float alpha, float beta, cudaStream_t s);
+
+// ------------------------------------------------------------ FE kernels ---
+struct Material {
+  double E, nu, Gc, kappa, eps, p, mu, lam;
+};
+
+// stencil slot count and layout helpers
+inline int n_slots(int dim) { return dim == 2 ? 9 : 27; }
+
+void launch_phi_tilde(const MeshDev& m, int64_t n, int steps_done, const double* phi_old,
+                      const double* phi_prev, double* phit, cudaStream_t s);
+void launch_lumped_mass(const MeshDev& m, int64_t n, double* mass, cudaStream_t s);
+void launch_residual(const MeshDev& m, const Material& mat, int64_t n, const double* u,
+                     const double* phi, const double* phit, double* F, cudaStream_t s);
+void launch_assemble_uu(const MeshDev& m, const Material& mat, int64_t n, const double* phit,
+                        double* Kuu, cudaStream_t s);
+void launch_assemble_phi(const MeshDev& m, const Material& mat, int64_t n, const double* u,
+                         const double* phi, double* Kpu, double* Kpp, cudaStream_t s);
+// scaling S (u: diag M_uu, Dirichlet 1; phi: diag G_c(M/eps + eps K)) and its inverse
+void launch_scaling(const MeshDev& m, const Material& mat, int64_t n, const double* Kuu,
+                    double* S, double* Sinv, cudaStream_t s);
+// reduced rhs: Ft = F with Dirichlet rows 0, active phi rows 0 and the active
+// columns (dphiA = phi_old - phi on the active set) moved to the rhs; masks the
+// phi rows / cols of Kpu, Kpp for the active set; writes dUA.
+void launch_reduce_phi(const MeshDev& m, int64_t n, const uint8_t* active, const double* phi,
+                       const double* phi_old, const double* F, double* Ft, double* dUA,
+                       double* Kpu, double* Kpp, cudaStream_t s);
+// y = Sinv .* (G~ x) with the assembled stencils (Sinv may be null)
+void launch_apply_assembled(const MeshDev& m, int64_t n, const double* Kuu, const double* Kpu,
+                            const double* Kpp, const double* x, double* y, const double* Sinv,
+                            cudaStream_t s);
+// y = Sinv .* (G~ x) matrix-free (Sinv may be null)
+void launch_apply_matfree(const MeshDev& m, const Material& mat, int64_t n, const double* u,
+                          const double* phi, const double* phit, const uint8_t* active,
+                          const double* x, double* y, const double* Sinv, cudaStream_t s);
+// Active set (step 2 of the Section 3 algorithm) with cycle locking.
+// counters[0] = |A|, counters[1] = changes vs. previous A (if have_prev)
+void launch_active_set(int64_t n, int dim, const double* F, const double* mass, const double* phi,
+                       const double* phi_old, double c, int have_prev, int lock_after,
+                       uint8_t* raw_prev, int* toggles, uint8_t* locked, uint8_t* active,
+                       uint8_t* active_prev, double* indicator, int* counters, cudaStream_t s);
+// rho = Sinv .* F on free rows (not Dirichlet, not active), 0 elsewhere
+void launch_scaled_reduced(const MeshDev& m, int64_t n, const double* F, const double* Sinv,
+                           const uint8_t* active, double* rho, cudaStream_t s);
+// stencil -> BSR value copy (structure precomputed)
+void launch_stencil_to_bsr(const MeshDev& m, int64_t n, int b, const double* K, const Bsr& A,
+                           cudaStream_t s);
+void build_stencil_bsr_structure(const MeshDev& m, int64_t n, int b, Bsr& A, cudaStream_t s);
+// rigid-body (u) near-null space, column-major n*dim x nns
+void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s);
+// TCV partial sums (deterministic) and COD line integrals
+void tcv_dev(const MeshDev& m, int64_t n_cells, const double* u, const double* phi, double* out,
+             double* partials, cudaStream_t s);
+struct CodColumn {
+  int col[2];       // cell index along x (and y in 3d)
+  double xi[2];     // local coordinate in that cell
+  double w;         // averaging weight
+  int point;        // output slot
+};
+void cod_dev(const MeshDev& m, const CodColumn* cols, int ncols, const double* u,
+             const double* phi, double* out, int npts, cudaStream_t s);
+
+}  // namespace pff
+
+// -------------------------------------------------------------- the handle --
+struct pff_problem {
+  int dim = 2;
+  int nn[3] = {1, 1, 1}, nc[3] = {1, 1, 1};
+  int64_t n_nodes = 0, n_cells = 0, n_dofs = 0;
+  std::vector<double> hX[3];
+  double* X[3] = {nullptr, nullptr, nullptr};
+  pff::Material mat{1.0, 0.2, 1.0, 1e-10, 0.0625, 0.0, 0.0, 0.0};
+  cudaStream_t stream = nullptr;
+
+  // state (device)
+  double *u = nullptr, *phi = nullptr, *phi_old = nullptr, *phi_prev = nullptr, *phit = nullptr;
+  int steps_done = 0;
+  double *mass = nullptr, *S = nullptr, *Sinv = nullptr;
+  uint8_t *active = nullptr, *active_prev = nullptr, *raw_prev = nullptr, *locked = nullptr;
+  int* toggles = nullptr;
+  double* indicator = nullptr;
+  int* counters = nullptr;      // device ints
+  int* h_counters = nullptr;    // pinned host mirror
+  double* h_scalars = nullptr;  // pinned host doubles
+  double* d_scalars = nullptr;  // device doubles
+  double* partials = nullptr;
+
+  // assembled stencils
+  double *Kuu = nullptr, *Kpu = nullptr, *Kpp = nullptr;
+  bool uu_assembled = false, phi_assembled = false;
+
+  // work vectors (n_dofs)
+  double *F = nullptr, *Ft = nullptr, *dU = nullptr, *dUA = nullptr;
+  double *ut = nullptr, *phit_trial = nullptr, *Ftrial = nullptr;
+
+  // preconditioner
+  pff::Bsr Auu, App;
+  double* Bu = nullptr;   // rigid-body modes
+  double* Bp = nullptr;   // constants
+  pff::Amg amg_u, amg_p;
+  bool amg_u_valid = false;
+  int precision = PFF_PREC_FP64;
+
+  // Krylov workspace
+  int krylov_m = 0;
+  double *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *tmp = nullptr;
+  double* h_host = nullptr;
+
+  // Newton step state
+  bool in_step = false;
+  bool have_prev = false;
+  bool last_small = false;
+  int k = 0;
+  double rho0 = 0.0;
+  int apply_variant = PFF_APPLY_ASSEMBLED;
+  bool apply_tuned = false;
+  pff_step_report cur{};
+
+  pff::MeshDev mesh() const {
+    pff::MeshDev m;
+    m.dim = dim;
+    for (int a = 0; a < 3; ++a) {
+      m.nn[a] = nn[a];
+      m.nc[a] = nc[a];
+      m.X[a] = X[a];
+    }
+    return m;
+  }
+};
+
+namespace pff {
+// solver.cu
+void begin_loading_step(pff_problem* P, double p);
+int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep);
+void end_loading_step(pff_problem* P);
+void compute_residual(pff_problem* P, const double* u, const double* phi, double* F);
+void compute_active_set(pff_problem* P, double c, int lock_after, bool track);
+void assemble_all(pff_problem* P);
+void precond_setup(pff_problem* P, const pff_options& o);
+void precond_apply(pff_problem* P, const double* r, double* z);
+int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int* iters);
+void apply_jacobian(pff_problem* P, int variant, const double* x, double* y, const double* Sinv);
+void ensure_krylov(pff_problem* P, int m);
+void scale_into(const double* s, const double* x, double* y, int64_t n, cudaStream_t st);
+}  // namespace pff

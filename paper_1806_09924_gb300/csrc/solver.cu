@@ -1,0 +1,439 @@
+// FGMRES with the block-diagonal preconditioner of Section 3.1 and the combined
+// semi-smooth Newton / primal-dual active-set loop of Section 3 (the algorithm
+// the paper prints in LaTeX comments), orchestrated from the host; every vector
+// operation runs in the kernels of fe_kernels.cu, linalg.cu and amg.cu.
+//
+// Newton iteration k of a loading step:
+//   1. F = -r(U^k)                                 (residual kernel)
+//   2. A_k = {i : F_phi,i/m_i + c(phi_i - phi_old,i) > 0}, plus indices locked
+//      after `cycle_lock` membership changes      (active-set kernel)
+//   3. stop if k > 0, A_k = A_{k-1}, the scaled reduced residual fell by
+//      tol_newton and the previous step was below tol_step
+//   4. assemble M_phi_u, M_phi_phi (M_uu once per loading step), eliminate the
+//      Dirichlet / active rows and columns (active entries get
+//      delta phi = phi_old - phi, moved to the right-hand side)
+//   5. FGMRES on the Jacobi-scaled reduced system S^-1 G~ dU = S^-1 F~ with the
+//      right preconditioner diag(V-cycle(M_uu), V-cycle(M_phi_phi)) S
+//   6. line search on ||S^-1 F~||_2 (halving), update.
+// S = diag(M_uu(phi~)) (+ diag G_c(M/eps + eps K) for phi) is fixed during a
+// loading step, so the reduced residual norms of different iterates compare.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+
+#include "pff_internal.h"
+
+namespace pff {
+
+namespace {
+
+__global__ void k_update(int64_t n, int dim, const double* __restrict__ u,
+                         const double* __restrict__ phi, const double* __restrict__ phi_old,
+                         const uint8_t* __restrict__ active, const double* __restrict__ dU,
+                         double omega, double* __restrict__ uo, double* __restrict__ po) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int a = 0; a < dim; ++a) uo[i * dim + a] = u[i * dim + a] + omega * dU[i * dim + a];
+  const double dp = dU[(int64_t)dim * n + i];
+  po[i] = (omega == 1.0 && active[i]) ? phi_old[i] : phi[i] + omega * dp;
+}
+
+__global__ void k_add(int64_t n, const double* __restrict__ a, double* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] += a[i];
+}
+
+__global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                      double* __restrict__ c) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] = a[i] * b[i];
+}
+
+// w /= sqrt(*nrm2) (into dst)
+__global__ void k_normalize(int64_t n, const double* __restrict__ w, const double* __restrict__ nrm2,
+                            double* __restrict__ dst) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const double nn = *nrm2;
+  const double s = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+  if (i < n) dst[i] = w[i] * s;
+}
+
+__global__ void k_sub(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                      double* __restrict__ c) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) c[i] = a[i] - b[i];
+}
+
+// lam_i = |F_phi,i / m_i|
+__global__ void k_lambda(int64_t n, int dim, const double* __restrict__ F,
+                         const double* __restrict__ mass, double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fabs(F[(int64_t)dim * n + i] / mass[i]);
+}
+
+__global__ void k_count_ties(int64_t n, const double* __restrict__ ind, const double* __restrict__ lam_inf,
+                             double c, int* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool tie = i < n && fabs(ind[i]) < 1e-14 * (*lam_inf + c);
+  const unsigned b = __ballot_sync(0xffffffffu, tie);
+  if ((threadIdx.x & 31) == 0 && b) atomicAdd(cnt, __popc(b));
+}
+
+void sync(pff_problem* P) { PFF_CUDA(cudaStreamSynchronize(P->stream)); }
+
+double fetch(pff_problem* P, const double* d) {
+  PFF_CUDA(cudaMemcpyAsync(P->h_scalars, d, sizeof(double), cudaMemcpyDeviceToHost, P->stream));
+  sync(P);
+  return P->h_scalars[0];
+}
+
+}  // namespace
+
+void scale_into(const double* s, const double* x, double* y, int64_t n, cudaStream_t st) {
+  k_mul<<<grid_for(n, 256), 256, 0, st>>>(n, s, x, y);
+  PFF_LAUNCH("scale");
+}
+
+void ensure_krylov(pff_problem* P, int m) {
+  if (P->krylov_m >= m) return;
+  dfree(P->V);
+  dfree(P->Z);
+  dfree(P->w);
+  dfree(P->h);
+  dfree(P->tmp);
+  if (P->h_host) cudaFreeHost(P->h_host);
+  const int64_t N = P->n_dofs;
+  P->V = dalloc<double>((size_t)(m + 1) * N);
+  P->Z = dalloc<double>((size_t)m * N);
+  P->w = dalloc<double>(N);
+  P->tmp = dalloc<double>(N);
+  P->h = dalloc<double>(4 * (m + 2));
+  PFF_CUDA(cudaMallocHost(&P->h_host, sizeof(double) * 4 * (m + 2)));
+  P->krylov_m = m;
+}
+
+void compute_residual(pff_problem* P, const double* u, const double* phi, double* F) {
+  launch_residual(P->mesh(), P->mat, P->n_nodes, u, phi, P->phit, F, P->stream);
+}
+
+void compute_active_set(pff_problem* P, double c, int lock_after, bool track) {
+  launch_active_set(P->n_nodes, P->dim, P->F, P->mass, P->phi, P->phi_old, c, track ? 1 : 0,
+                    lock_after, P->raw_prev, P->toggles, P->locked, P->active, nullptr,
+                    P->indicator, P->counters, P->stream);
+}
+
+void assemble_all(pff_problem* P) {
+  const auto m = P->mesh();
+  if (!P->uu_assembled) {
+    launch_assemble_uu(m, P->mat, P->n_nodes, P->phit, P->Kuu, P->stream);
+    launch_scaling(m, P->mat, P->n_nodes, P->Kuu, P->S, P->Sinv, P->stream);
+    P->uu_assembled = true;
+  }
+  launch_assemble_phi(m, P->mat, P->n_nodes, P->u, P->phi, P->Kpu, P->Kpp, P->stream);
+  launch_reduce_phi(m, P->n_nodes, P->active, P->phi, P->phi_old, P->F, P->Ft, P->dUA, P->Kpu,
+                    P->Kpp, P->stream);
+  P->phi_assembled = true;
+}
+
+void apply_jacobian(pff_problem* P, int variant, const double* x, double* y, const double* Sinv) {
+  if (variant == PFF_APPLY_MATFREE) {
+    launch_apply_matfree(P->mesh(), P->mat, P->n_nodes, P->u, P->phi, P->phit, P->active, x, y,
+                         Sinv, P->stream);
+  } else {
+    if (!P->phi_assembled) fail(PFF_ERR_INVALID_ARG, "assembled apply requested before assembly");
+    launch_apply_assembled(P->mesh(), P->n_nodes, P->Kuu, P->Kpu, P->Kpp, x, y, Sinv, P->stream);
+  }
+}
+
+void precond_setup(pff_problem* P, const pff_options& o) {
+  P->precision = o.precision;
+  if (o.precond == PFF_PC_JACOBI) return;
+  AmgParams ap;
+  ap.theta = o.amg_theta;
+  ap.coarse_max = o.amg_coarse_max;
+  ap.cheb_degree = o.cheb_degree;
+  ap.mixed = o.precision == PFF_PREC_MIXED;
+  const auto m = P->mesh();
+  if (!P->amg_u_valid || P->amg_u.mixed != ap.mixed) {
+    launch_stencil_to_bsr(m, P->n_nodes, P->dim, P->Kuu, P->Auu, P->stream);
+    amg_build(P->amg_u, P->Auu, P->Bu, P->dim == 2 ? 3 : 6, ap, P->stream);
+    P->amg_u_valid = true;
+  }
+  launch_stencil_to_bsr(m, P->n_nodes, 1, P->Kpp, P->App, P->stream);
+  amg_build(P->amg_p, P->App, P->Bp, 1, ap, P->stream);
+}
+
+// z = diag(V_u, V_phi) (S .* r) -- the right preconditioner of the scaled system
+void precond_apply(pff_problem* P, const double* r, double* z) {
+  const int64_t N = P->n_dofs, nu = (int64_t)P->dim * P->n_nodes;
+  k_mul<<<grid_for(N, 256), 256, 0, P->stream>>>(N, P->S, r, P->tmp);
+  PFF_LAUNCH("precond scale");
+  amg_vcycle(P->amg_u, P->tmp, z, P->stream);
+  amg_vcycle(P->amg_p, P->tmp + nu, z + nu, P->stream);
+}
+
+static void precond(pff_problem* P, const pff_options& o, const double* r, double* z) {
+  if (o.precond == PFF_PC_JACOBI) {
+    PFF_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * P->n_dofs, cudaMemcpyDeviceToDevice, P->stream));
+  } else {
+    precond_apply(P, r, z);
+  }
+}
+
+// Restarted flexible GMRES (right preconditioned, CGS2 orthogonalization) for
+// (S^-1 G~) x = b; b is already scaled.  Returns PFF_OK or PFF_ERR_NOT_CONVERGED.
+int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int* iters) {
+  const int m = std::max(2, o.krylov_restart);
+  ensure_krylov(P, m);
+  const int64_t N = P->n_dofs;
+  cudaStream_t s = P->stream;
+  double* V = P->V;
+  double* Z = P->Z;
+  double* w = P->w;
+  double* dh = P->h;            // [0, m+1): pass 1, [m+2, ...): pass 2, [2(m+2)]: ||w||^2
+  double* hh = P->h_host;
+  const unsigned g = grid_for(N, 256);
+  PFF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
+  dot_dev(b, b, N, P->d_scalars, P->partials, s);
+  const double beta0 = std::sqrt(fetch(P, P->d_scalars));
+  *iters = 0;
+  if (!(beta0 > 0.0)) return std::isfinite(beta0) ? PFF_OK : PFF_ERR_NAN;
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), y(m);
+  int total = 0;
+  const double target = o.tol_linear * beta0;
+  // r = b
+  PFF_CUDA(cudaMemcpyAsync(w, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  double beta = beta0;
+  while (true) {
+    k_normalize<<<g, 256, 0, s>>>(N, w, P->d_scalars, V);   // d_scalars holds ||r||^2
+    PFF_LAUNCH("normalize");
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int j = 0;
+    double resid = beta;
+    for (; j < m; ++j) {
+      double* vj = V + (int64_t)j * N;
+      double* zj = Z + (int64_t)j * N;
+      precond(P, o, vj, zj);
+      apply_jacobian(P, P->apply_variant, zj, w, P->Sinv);
+      // CGS2
+      multidot_dev(V, N, j + 1, w, N, dh, P->partials, s);
+      multi_axpy_dev(V, N, j + 1, dh, w, N, -1.0, s);
+      multidot_dev(V, N, j + 1, w, N, dh + (m + 2), P->partials, s);
+      multi_axpy_dev(V, N, j + 1, dh + (m + 2), w, N, -1.0, s);
+      dot_dev(w, w, N, dh + 2 * (m + 2), P->partials, s);
+      PFF_CUDA(cudaMemcpyAsync(hh, dh, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, s));
+      sync(P);
+      const double hn = std::sqrt(hh[2 * (m + 2)]);
+      if (!std::isfinite(hn)) return PFF_ERR_NAN;
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[(m + 2) + i];
+      H[(size_t)(j + 1) * m + j] = hn;
+      // V_{j+1} = w / hn  (norm squared already on device)
+      k_normalize<<<g, 256, 0, s>>>(N, w, dh + 2 * (m + 2), V + (int64_t)(j + 1) * N);
+      PFF_LAUNCH("normalize");
+      for (int i = 0; i < j; ++i) {
+        const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = cs[i] * a + sn[i] * bb;
+        H[(size_t)(i + 1) * m + j] = -sn[i] * a + cs[i] * bb;
+      }
+      const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+      const double r = std::hypot(a, bb);
+      cs[j] = r > 0 ? a / r : 1.0;
+      sn[j] = r > 0 ? bb / r : 0.0;
+      H[(size_t)j * m + j] = r;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      resid = std::fabs(gv[j + 1]);
+      ++total;
+      if (resid <= target || total >= o.max_krylov || hn == 0.0) {
+        ++j;
+        break;
+      }
+    }
+    // y = H^-1 g, x += Z y
+    for (int i = j - 1; i >= 0; --i) {
+      double t = gv[i];
+      for (int k = i + 1; k < j; ++k) t -= H[(size_t)i * m + k] * y[k];
+      y[i] = H[(size_t)i * m + i] != 0.0 ? t / H[(size_t)i * m + i] : 0.0;
+    }
+    for (int i = 0; i < j; ++i) hh[i] = y[i];
+    PFF_CUDA(cudaMemcpyAsync(dh, hh, sizeof(double) * j, cudaMemcpyHostToDevice, s));
+    multi_axpy_dev(Z, N, j, dh, x, N, 1.0, s);
+    *iters = total;
+    if (resid <= target) {
+      sync(P);
+      return PFF_OK;
+    }
+    if (total >= o.max_krylov) {
+      sync(P);
+      return PFF_ERR_NOT_CONVERGED;
+    }
+    // explicit restart residual r = b - A x
+    apply_jacobian(P, P->apply_variant, x, w, P->Sinv);
+    k_sub<<<g, 256, 0, s>>>(N, b, w, w);
+    dot_dev(w, w, N, P->d_scalars, P->partials, s);
+    beta = std::sqrt(fetch(P, P->d_scalars));
+    if (beta <= target) return PFF_OK;
+  }
+}
+
+void begin_loading_step(pff_problem* P, double p) {
+  P->mat.p = p;
+  launch_phi_tilde(P->mesh(), P->n_nodes, P->steps_done, P->phi_old, P->phi_prev, P->phit,
+                   P->stream);
+  P->uu_assembled = false;
+  P->phi_assembled = false;
+  P->amg_u_valid = false;
+  // M_uu and S depend on phi~ only
+  launch_assemble_uu(P->mesh(), P->mat, P->n_nodes, P->phit, P->Kuu, P->stream);
+  launch_scaling(P->mesh(), P->mat, P->n_nodes, P->Kuu, P->S, P->Sinv, P->stream);
+  P->uu_assembled = true;
+  P->in_step = true;
+  P->k = 0;
+  P->have_prev = false;
+  P->last_small = false;
+  P->rho0 = 0.0;
+  P->cur = pff_step_report{};
+  sync(P);
+}
+
+static double scaled_norms(pff_problem* P, const double* F, double* l2) {
+  launch_scaled_reduced(P->mesh(), P->n_nodes, F, P->Sinv, P->active, P->tmp, P->stream);
+  nrm_inf_dev(P->tmp, P->n_dofs, P->d_scalars, P->partials, P->stream);
+  dot_dev(P->tmp, P->tmp, P->n_dofs, P->d_scalars + 1, P->partials, P->stream);
+  PFF_CUDA(cudaMemcpyAsync(P->h_scalars, P->d_scalars, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                           P->stream));
+  sync(P);
+  if (l2) *l2 = std::sqrt(P->h_scalars[1]);
+  return P->h_scalars[0];
+}
+
+static int count_ties(pff_problem* P, double c) {
+  const int64_t n = P->n_nodes;
+  k_lambda<<<grid_for(n, 256), 256, 0, P->stream>>>(n, P->dim, P->F, P->mass, P->tmp);
+  nrm_inf_dev(P->tmp, n, P->d_scalars, P->partials, P->stream);
+  PFF_CUDA(cudaMemsetAsync(P->counters + 2, 0, sizeof(int), P->stream));
+  k_count_ties<<<grid_for(n, 256), 256, 0, P->stream>>>(n, P->indicator, P->d_scalars, c,
+                                                        P->counters + 2);
+  PFF_CUDA(cudaMemcpyAsync(P->h_counters + 2, P->counters + 2, sizeof(int), cudaMemcpyDeviceToHost,
+                           P->stream));
+  sync(P);
+  return P->h_counters[2];
+}
+
+int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep) {
+  if (!P->in_step) fail(PFF_ERR_INVALID_ARG, "no loading step in progress (call pff_set_pressure)");
+  cudaStream_t s = P->stream;
+  const int64_t n = P->n_nodes;
+  const int dim = P->dim;
+  const int64_t N = P->n_dofs;
+  pff_step_report& R = P->cur;
+  // 1-2. residual and active set
+  compute_residual(P, P->u, P->phi, P->F);
+  compute_active_set(P, o.c, o.cycle_lock, P->have_prev);
+  PFF_CUDA(cudaMemcpyAsync(P->h_counters, P->counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  double rho_l2 = 0.0;
+  const double rho_inf = scaled_norms(P, P->F, &rho_l2);
+  const int n_active = P->h_counters[0];
+  const int n_changed = P->have_prev ? P->h_counters[1] : n_active;
+  if (!std::isfinite(rho_inf)) {
+    R.status = PFF_ERR_NAN;
+    if (rep) *rep = R;
+    return PFF_ERR_NAN;
+  }
+  if (P->k == 0) R.rho0 = P->rho0 = rho_inf;
+  R.rho = rho_inf;
+  R.active = n_active;
+  R.changed = n_changed;
+  // 3. stopping test
+  const bool done = (P->have_prev && n_changed == 0 && rho_inf <= o.tol_newton * P->rho0 &&
+                     P->last_small) ||
+                    P->rho0 == 0.0;
+  if (done) {
+    R.converged = 1;
+    R.newton_its = P->k;
+    R.ties = count_ties(P, o.c);
+    PFF_CUDA(cudaMemcpyAsync(P->h_counters, P->counters, sizeof(int), cudaMemcpyDeviceToHost, s));
+    R.status = PFF_OK;
+    if (rep) *rep = R;
+    return PFF_OK;
+  }
+  if (P->k >= o.max_newton) {
+    R.converged = 0;
+    R.newton_its = P->k;
+    R.status = PFF_ERR_NOT_CONVERGED;
+    if (rep) *rep = R;
+    return PFF_ERR_NOT_CONVERGED;
+  }
+  // 4. reduced Jacobian and right-hand side
+  assemble_all(P);
+  precond_setup(P, o);
+  // 5. linear solve on the scaled system
+  k_mul<<<grid_for(N, 256), 256, 0, s>>>(N, P->Sinv, P->Ft, P->tmp);
+  PFF_LAUNCH("scale rhs");
+  PFF_CUDA(cudaMemcpyAsync(P->Ftrial, P->tmp, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  int its = 0;
+  const int lrc = fgmres(P, o, P->Ftrial, P->dU, &its);
+  R.krylov_its += its;
+  R.krylov_its_max = std::max(R.krylov_its_max, its);
+  if (lrc == PFF_ERR_NAN) {
+    R.status = lrc;
+    if (rep) *rep = R;
+    return lrc;
+  }
+  k_add<<<grid_for(N, 256), 256, 0, s>>>(N, P->dUA, P->dU);
+  // step size test on the full step
+  k_update<<<grid_for(n, 256), 256, 0, s>>>(n, dim, P->u, P->phi, P->phi_old, P->active, P->dU, 1.0,
+                                            P->ut, P->phit_trial);
+  nrm_inf_dev(P->dU, (int64_t)dim * n, P->d_scalars, P->partials, s);
+  nrm_inf_dev(P->ut, (int64_t)dim * n, P->d_scalars + 1, P->partials, s);
+  nrm_inf_dev(P->dU + (int64_t)dim * n, n, P->d_scalars + 2, P->partials, s);
+  nrm_inf_dev(P->phit_trial, n, P->d_scalars + 3, P->partials, s);
+  PFF_CUDA(cudaMemcpyAsync(P->h_scalars, P->d_scalars, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+  sync(P);
+  const double* hs = P->h_scalars;
+  const bool small = hs[0] <= o.tol_step * hs[1] && hs[2] <= o.tol_step * hs[3];
+  // 6. line search
+  double omega = 1.0;
+  if (!small) {
+    for (int t = 0; t <= o.max_halvings; ++t) {
+      if (t > 0)
+        k_update<<<grid_for(n, 256), 256, 0, s>>>(n, dim, P->u, P->phi, P->phi_old, P->active,
+                                                  P->dU, omega, P->ut, P->phit_trial);
+      compute_residual(P, P->ut, P->phit_trial, P->Ftrial);
+      double l2 = 0.0;
+      scaled_norms(P, P->Ftrial, &l2);
+      if (l2 < rho_l2) break;
+      if (t == o.max_halvings) {
+        omega = 1.0;
+        R.linesearch_fails += 1;
+        k_update<<<grid_for(n, 256), 256, 0, s>>>(n, dim, P->u, P->phi, P->phi_old, P->active,
+                                                  P->dU, omega, P->ut, P->phit_trial);
+        break;
+      }
+      omega *= 0.5;
+    }
+  }
+  std::swap(P->u, P->ut);
+  std::swap(P->phi, P->phit_trial);
+  P->last_small = small;
+  P->have_prev = true;
+  P->k += 1;
+  R.newton_its = P->k;
+  R.status = lrc;
+  if (rep) *rep = R;
+  sync(P);
+  return PFF_OK;
+}
+
+void end_loading_step(pff_problem* P) {
+  std::swap(P->phi_prev, P->phi_old);
+  PFF_CUDA(cudaMemcpyAsync(P->phi_old, P->phi, sizeof(double) * P->n_nodes, cudaMemcpyDeviceToDevice,
+                           P->stream));
+  P->steps_done += 1;
+  P->in_step = false;
+  sync(P);
+}
+
+}  // namespace pff

@@ -1,0 +1,70 @@
+"""CPU checks of the C ABI: the library builds, loads, exports every entry point
+declared in include/pff.h, and its structs have the layout the binding assumes.
+No compute call is made (there may be no GPU)."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+HEADER = os.path.join(ROOT, "include", "pff.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1806_09924_gb300 import build as B
+    if not os.path.exists(B.LIB):
+        B.build()
+    import paper_1806_09924_gb300 as pff
+    return pff.load_library()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(pff_[a-z_0-9]+)\s*\(", text)))
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = declared_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+
+
+def test_binding_declares_every_symbol():
+    import paper_1806_09924_gb300 as pff
+    assert set(declared_functions()) == set(pff._SIGS)
+
+
+def test_struct_layout_matches_header(tmp_path):
+    import paper_1806_09924_gb300 as pff
+    src = tmp_path / "sz.c"
+    src.write_text('#include "pff.h"\n#include <stdio.h>\n#include <stddef.h>\n'
+                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(pff_options), sizeof(pff_step_report),'
+                   ' offsetof(pff_options, precond), offsetof(pff_step_report, time_ms));return 0;}\n')
+    exe = tmp_path / "sz"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
+    so, sr, off_pc, off_t = map(int, out)
+    assert so == ctypes.sizeof(pff.PffOptions)
+    assert sr == ctypes.sizeof(pff.PffStepReport)
+    assert off_pc == pff.PffOptions.precond.offset
+    assert off_t == pff.PffStepReport.time_ms.offset
+
+
+def test_defaults_and_argument_errors_without_gpu(lib):
+    import paper_1806_09924_gb300 as pff
+    o = pff.options()
+    assert o.tol_linear == 1e-8 and o.c == 1.0 and o.precision == pff.PFF_PREC_FP64
+    assert o.krylov_restart == 40 and o.max_newton == 50
+    h = ctypes.c_void_p()
+    nc = (ctypes.c_int32 * 3)(4, 4, 4)
+    # invalid dimension is rejected before any device work
+    rc = lib.pff_create_mesh(5, nc, None, ctypes.byref(h))
+    assert rc == pff.PFF_ERR_INVALID_ARG
+    assert b"dim" in lib.pff_last_error()
+    assert lib.pff_set_pressure(None, 1e-3) == pff.PFF_ERR_INVALID_ARG
+    assert lib.pff_newton_step(None, None, None) == pff.PFF_ERR_INVALID_ARG

@@ -1,0 +1,272 @@
+"""GPU parity: the CUDA path (through the C ABI) against the CPU oracle.
+
+Bars (FP64 path): residual and reduced-Jacobian apply relative L2 <= 1e-12;
+functionals and lumped quantities 1e-12; converged u, phi relative L2 <= 1e-8
+with identical active sets away from round-off ties; TCV / COD <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import fe, functionals as fn, model, pdas
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+pff = pytest.importorskip("paper_1806_09924_gb300")
+
+RTOL_OP = 1e-12
+RTOL_SOL = 1e-8
+RTOL_FUNC = 1e-6
+
+
+def rel(a, b):
+    a = np.asarray(a, dtype=np.float64).ravel()
+    b = np.asarray(b, dtype=np.float64).ravel()
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def random_coords(rng, n, lo=-1.0, hi=1.0):
+    x = np.sort(rng.uniform(lo, hi, n - 1))
+    c = np.concatenate([[lo], x, [hi]])
+    if np.min(np.diff(c)) < 1e-3 * (hi - lo) / n:
+        return np.linspace(lo, hi, n + 1)
+    return c
+
+
+def make_case(dim, shape, seed, p=3e-2):
+    rng = np.random.default_rng(seed)
+    coords = [random_coords(rng, n) for n in shape[:dim]]
+    mesh = fe.Mesh(coords)
+    n = mesh.n_nodes
+    w = W.Workload("case", dim, coords, E=1.3, nu=0.27, Gc=0.9, kappa=1e-6, eps=0.3)
+    u, phi, phi_old, _ = W.random_state(w, seed, u_scale=0.05)
+    phi_prev = rng.random(n)
+    prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=p)
+    phit = np.clip(2 * phi_old - phi_prev, 0.0, 1.0)
+    P = pff.Problem(coords)
+    P.set_material(w.E, w.nu, w.Gc, w.kappa, w.eps)
+    P.set_state(u, phi, phi_old, phi_prev, steps_done=1)
+    P.set_pressure(p)
+    return P, mesh, prm, (u, phi, phi_old, phi_prev, phit)
+
+
+CASES = [(2, (37, 23), 11), (2, (8, 5), 12), (2, (1, 1), 13), (3, (9, 7, 5), 14), (3, (2, 3, 2), 15)]
+
+
+@pytest.mark.parametrize("dim,shape,seed", CASES)
+def test_residual_parity(dim, shape, seed):
+    P, mesh, prm, (u, phi, phi_old, phi_prev, phit) = make_case(dim, shape, seed)
+    F = torch.empty(P.n_dofs, dtype=torch.float64, device="cuda")
+    P.residual_dev(F)
+    torch.cuda.synchronize()
+    r_u, r_phi = model.gradient(mesh, prm, u, phi, phit)
+    F_ref = -np.concatenate([r_u.ravel(), r_phi])
+    assert rel(F.cpu().numpy(), F_ref) <= RTOL_OP
+    P.close()
+
+
+def oracle_reduced_apply(mesh, prm, state, active, x):
+    u, phi, _, _, phit = state
+    d, n = mesh.d, mesh.n_nodes
+    J = model.jacobian(mesh, prm, u, phi, phit)
+    fixed = np.concatenate([np.repeat(mesh.boundary_nodes(), d), active.astype(bool)])
+    xm = np.where(fixed, 0.0, x)
+    y = J @ xm
+    y[fixed] = x[fixed]
+    return y
+
+
+@pytest.mark.parametrize("dim,shape,seed", CASES)
+def test_active_set_and_jacobian_apply_parity(dim, shape, seed):
+    P, mesh, prm, state = make_case(dim, shape, seed)
+    u, phi, phi_old, phi_prev, phit = state
+    n = mesh.n_nodes
+    act = torch.empty(n, dtype=torch.uint8, device="cuda")
+    ind = torch.empty(n, dtype=torch.float64, device="cuda")
+    P.active_set_dev(1.0, act, ind)
+    r_u, r_phi = model.gradient(mesh, prm, u, phi, phit)
+    ind_ref = pdas.active_indicator(-r_phi, model.lumped_mass(mesh), phi, phi_old, 1.0)
+    assert rel(ind.cpu().numpy(), ind_ref) <= RTOL_OP
+    a = act.cpu().numpy().astype(bool)
+    clear = np.abs(ind_ref) > 1e-12 * np.max(np.abs(ind_ref))
+    assert np.array_equal(a[clear], (ind_ref > 0)[clear])
+    P.assemble()
+    rng = np.random.default_rng(seed + 100)
+    x = rng.standard_normal(P.n_dofs)
+    y_ref = oracle_reduced_apply(mesh, prm, state, a, x)
+    xd = torch.tensor(x, device="cuda")
+    for variant in (pff.PFF_APPLY_ASSEMBLED, pff.PFF_APPLY_MATFREE):
+        y = torch.empty_like(xd)
+        P.apply_jacobian_dev(variant, xd, y)
+        torch.cuda.synchronize()
+        assert rel(y.cpu().numpy(), y_ref) <= RTOL_OP, variant
+    P.close()
+
+
+@pytest.mark.parametrize("dim,shape,seed", [(2, (37, 23), 21), (3, (9, 7, 5), 22)])
+def test_tcv_cod_parity(dim, shape, seed):
+    P, mesh, prm, (u, phi, *_rest) = make_case(dim, shape, seed)
+    rng = np.random.default_rng(seed)
+    if dim == 2:
+        pts = np.concatenate([rng.uniform(-1, 1, 6), [mesh.coords[0][3], -1.0, 1.0]])
+    else:
+        pts = np.concatenate([rng.uniform(-1, 1, (4, 2)),
+                              [[mesh.coords[0][2], mesh.coords[1][4]], [0.1, mesh.coords[1][1]]]]).ravel()
+    tcv, cod = P.eval_tcv_cod(pts)
+    assert rel(tcv, fn.tcv(mesh, u, phi)) <= RTOL_OP
+    assert rel(cod, fn.cod(mesh, u, phi, pts)) <= 1e-12
+    P.close()
+
+
+def _oracle_solution(w, pressures, opts=None):
+    mesh = fe.Mesh(w.coords)
+    prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=pressures[0])
+    st = pdas.State.initial(mesh, prm, w.phi0())
+    reps = pdas.solve_loading_steps(st, pressures, opts or pdas.Options())
+    return mesh, st, reps
+
+
+def _gpu_solution(w, pressures, **kw):
+    P = pff.problem_from_workload(w)
+    reps = P.solve_loading_steps(pressures, pff.options(**kw))
+    u, phi, act = P.get_solution()
+    return P, u, phi, act.astype(bool), reps
+
+
+def _assert_solution_parity(mesh, st, u, phi, act, tie_rel=1e-11):
+    assert rel(u, st.u) <= RTOL_SOL
+    assert rel(phi, st.phi) <= RTOL_SOL
+    ind = st.indicator
+    clear = np.abs(ind) > tie_rel * (np.max(np.abs(ind)) + 1.0)
+    mism = np.count_nonzero(act[clear] != st.active[clear])
+    assert mism == 0, f"{mism} active-set mismatches away from ties"
+    return int(np.count_nonzero(act != st.active))
+
+
+@pytest.mark.parametrize("n_cells,precision", [(32, 0), (64, 0), (64, 1)])
+def test_newton_solution_parity_2d(n_cells, precision):
+    w = W.scaled_workload(W.config(0), n_cells)
+    mesh, st, oreps = _oracle_solution(w, w.pressures)
+    P, u, phi, act, reps = _gpu_solution(w, w.pressures, precision=precision)
+    assert reps[0]["converged"] == 1 and oreps[0].converged
+    _assert_solution_parity(mesh, st, u, phi, act)
+    pts = fn.cod_points(w.l0, 64)
+    tcv, cod = P.eval_tcv_cod(pts)
+    assert rel(tcv, fn.tcv(mesh, st.u, st.phi)) <= RTOL_FUNC
+    assert rel(cod, fn.cod(mesh, st.u, st.phi, pts)) <= RTOL_FUNC
+    P.close()
+
+
+def test_newton_solution_parity_sneddon_128():
+    """The 128x128 Sneddon configuration (Table 1 refinement 4 size), FP64 and mixed."""
+    w = W.config(0)
+    mesh, st, oreps = _oracle_solution(w, w.pressures)
+    pts = fn.cod_points(w.l0, 64)
+    tcv_ref = fn.tcv(mesh, st.u, st.phi)
+    cod_ref = fn.cod(mesh, st.u, st.phi, pts)
+    for precision in (0, 1):
+        P, u, phi, act, reps = _gpu_solution(w, w.pressures, precision=precision)
+        assert reps[0]["converged"] == 1
+        _assert_solution_parity(mesh, st, u, phi, act)
+        tcv, cod = P.eval_tcv_cod(pts)
+        assert rel(tcv, tcv_ref) <= RTOL_FUNC
+        assert rel(cod, cod_ref) <= RTOL_FUNC
+        P.close()
+
+
+def test_two_loading_steps_parity():
+    w = W.scaled_workload(W.config(0), 48)
+    pressures = [5e-4, 1e-3]
+    mesh, st, oreps = _oracle_solution(w, pressures)
+    P, u, phi, act, reps = _gpu_solution(w, pressures)
+    assert all(r["converged"] == 1 for r in reps)
+    _assert_solution_parity(mesh, st, u, phi, act)
+    P.close()
+
+
+def test_newton_solution_parity_3d():
+    w = W.scaled_workload(W.config(2), 12)
+    mesh, st, oreps = _oracle_solution(w, [1e-3])
+    P, u, phi, act, reps = _gpu_solution(w, [1e-3], precision=1)
+    assert reps[0]["converged"] == 1
+    _assert_solution_parity(mesh, st, u, phi, act)
+    tcv, _ = P.eval_tcv_cod([])
+    assert rel(tcv, fn.tcv(mesh, st.u, st.phi)) <= RTOL_FUNC
+    P.close()
+
+
+def test_preconditioner_is_a_convergent_linear_map():
+    rng = np.random.default_rng(31)
+    coords = [random_coords(rng, 40), random_coords(rng, 33)]
+    mesh = fe.Mesh(coords)
+    n, d = mesh.n_nodes, 2
+    phi_old = 1.0 - 0.1 * rng.random(n)
+    u = 1e-3 * rng.standard_normal((n, d))
+    u[mesh.boundary_nodes()] = 0.0
+    P = pff.Problem(coords)
+    P.set_material(1.0, 0.2, 1.0, 1e-10, 0.2)
+    P.set_state(u, phi_old * 0.99, phi_old, phi_old, steps_done=1)
+    P.set_pressure(1e-3)
+    act = torch.empty(n, dtype=torch.uint8, device="cuda")
+    P.active_set_dev(1.0, act, None)
+    P.assemble()
+    P.precond_setup(pff.options())
+    N = P.n_dofs
+    r1 = torch.tensor(rng.standard_normal(N), device="cuda")
+    r2 = torch.tensor(rng.standard_normal(N), device="cuda")
+    z1, z2, z3 = (torch.empty_like(r1) for _ in range(3))
+    P.precond_apply_dev(r1, z1)
+    P.precond_apply_dev(r2, z2)
+    P.precond_apply_dev(2.0 * r1 - 3.0 * r2, z3)
+    torch.cuda.synchronize()
+    assert rel(z3.cpu().numpy(), (2.0 * z1 - 3.0 * z2).cpu().numpy()) <= 1e-12
+    # the stationary iteration x <- x + V(b - A x) contracts on each diagonal block
+    a = act.cpu().numpy().astype(bool)
+    fixed = np.concatenate([np.repeat(mesh.boundary_nodes(), d), a])
+    for blk, is_u in ((slice(0, d * n), True), (slice(d * n, N), False)):
+        b = np.zeros(N)
+        b[blk] = rng.standard_normal(b[blk].shape)
+        b[fixed] = 0.0
+        bd = torch.tensor(b, device="cuda")
+        x = torch.zeros_like(bd)
+        Ax = torch.empty_like(bd)
+        z = torch.empty_like(bd)
+        norms = []
+        for _ in range(6):
+            P.apply_jacobian_dev(pff.PFF_APPLY_ASSEMBLED, x, Ax)
+            res = bd - Ax
+            if is_u:
+                res[d * n:] = 0.0
+            norms.append(float(torch.linalg.norm(res[blk])))
+            P.precond_apply_dev(res, z)
+            x = x + z
+        assert norms[-1] < 0.05 * norms[0], norms
+    P.close()
+
+
+def test_linear_solve_matches_direct_solve():
+    P, mesh, prm, state = make_case(2, (30, 26), 41, p=1e-3)
+    act = torch.empty(mesh.n_nodes, dtype=torch.uint8, device="cuda")
+    P.active_set_dev(1.0, act, None)
+    P.assemble()
+    opts = pff.options(tol_linear=1e-12)
+    P.precond_setup(opts)
+    a = act.cpu().numpy().astype(bool)
+    d, n = 2, mesh.n_nodes
+    fixed = np.concatenate([np.repeat(mesh.boundary_nodes(), d), a])
+    rng = np.random.default_rng(3)
+    b = rng.standard_normal(P.n_dofs)
+    b[fixed] = 0.0
+    x = torch.zeros(P.n_dofs, dtype=torch.float64, device="cuda")
+    its = P.linear_solve_dev(torch.tensor(b, device="cuda"), x, opts)
+    u, phi, _, _, phit = state
+    J = model.jacobian(mesh, prm, u, phi, phit)
+    free = np.flatnonzero(~fixed)
+    import scipy.sparse.linalg as spla
+    xr = np.zeros(P.n_dofs)
+    xr[free] = spla.spsolve(J[free][:, free].tocsc(), b[free])
+    assert its > 0
+    assert rel(x.cpu().numpy(), xr) <= 1e-8
+    P.close()
