@@ -6,8 +6,10 @@ phi <= phi_old (Section 2):
 
   repeat for k = 0, 1, ...
     1. residual F = -r(U^k)                                   (model.gradient)
-    2. active set A_k = {i : F_phi,i / m_i + c (phi_i - phi_old,i) > 0}
-       with the lumped phase-field mass m (the paper's "B"), c > 0; indices
+    2. active set A_k = {i : F_phi,i / m_i + c (phi_i - phi_old,i) > tau}
+       with the lumped phase-field mass m (the paper's "B"), c > 0 and the
+       printed threshold read as round-off size, tau = 64 u G_c / eps
+       (u = 2^-53), so that exact ties resolve alike on every machine; indices
        that change membership ``cycle_lock`` times in this loading step are
        locked active (Section 3: alternating active-set indices are detected
        and constrained to avoid cycles)
@@ -25,8 +27,9 @@ phi <= phi_old (Section 2):
 
 After a converged loading step phi_prev <- phi_old, phi_old <- phi.  The
 extrapolation phi~ (Section 2, "linear extrapolation in time") is read as
-phi~ = phi_old in the first loading step and clamp(2 phi_old - phi_prev, 0, 1)
-afterwards.
+phi~ = phi_old in the first two loading steps (the initial crack field is not a
+computed time level) and clamp(2 phi_old - phi_prev, 0, 1) afterwards.
+Parity unpinned: the paper prints no value that fixes phi~ or the cycle rule.
 """
 from __future__ import annotations
 
@@ -50,6 +53,7 @@ class Options:
     max_halvings: int = 10
     cycle_lock: int = 3
     full_jacobian: bool = False
+    active_tol_ulps: float = 64.0   # tau = active_tol_ulps * 2^-53 * G_c / eps
 
 
 @dataclass
@@ -86,7 +90,14 @@ class State:
                    phi0.astype(np.float64).copy())
 
     def phi_tilde(self) -> np.ndarray:
-        if self.steps_done == 0 or self.phi_prev is None:
+        """Linear extrapolation in time of Section 2 (parity unpinned against the paper).
+
+        Extrapolation needs two computed time levels: the initial crack field is
+        a description of the crack, not a solution, so the first two loading
+        steps use phi~ = phi_old; from step 3 on phi~ = clamp(2 phi_old -
+        phi_prev, 0, 1) (uniform steps).
+        """
+        if self.steps_done <= 1 or self.phi_prev is None:
             return self.phi_old.copy()
         return np.clip(2.0 * self.phi_old - self.phi_prev, 0.0, 1.0)
 
@@ -124,6 +135,11 @@ def _solve_reduced(J, rhs, free, nu_dofs, full_jacobian):
     return x
 
 
+def active_threshold(prm: Params, opts: Options) -> float:
+    """tau of step 2: the threshold of the printed active-set rule, read as round-off size."""
+    return opts.active_tol_ulps * 2.0 ** -53 * prm.Gc / prm.eps
+
+
 def active_indicator(F_phi, m, phi, phi_old, c):
     """lambda_i + c (phi_i - phi_old,i) with lambda = F_phi / m (step 2)."""
     return F_phi / m + c * (phi - phi_old)
@@ -149,7 +165,7 @@ def loading_step(st: State, p: float, opts: Options = Options()) -> StepReport:
         r_u, r_phi = gradient(mesh, prm, u, phi, phit)
         F = -np.concatenate([r_u.ravel(), r_phi])
         ind = active_indicator(F[nu_dofs:], m, phi, phi_old, opts.c)
-        raw = ind > 0.0
+        raw = ind > active_threshold(prm, opts)
         if raw_prev is not None:
             toggles += raw != raw_prev
             locked |= toggles >= opts.cycle_lock

@@ -156,10 +156,13 @@ def test_two_loading_steps_irreversible_and_extrapolated():
     phi1 = st.phi.copy()
     np.testing.assert_array_equal(st.phi_old, phi1)
     np.testing.assert_array_equal(st.phi_prev, phi0)
-    expect_tilde = np.clip(2 * phi1 - phi0, 0.0, 1.0)
-    np.testing.assert_array_equal(st.phi_tilde(), expect_tilde)
+    # the initial crack field is not a computed time level: no extrapolation yet
+    np.testing.assert_array_equal(st.phi_tilde(), phi1)
     r2 = pdas.loading_step(st, 1e-3)
-    assert r1.converged and r2.converged
-    assert np.all(st.phi <= phi1 + 1e-15)                    # irreversibility phi <= phi_old
-    # more pressure -> wider opening at the centre
-    assert r2.newton_its >= 1
+    phi2 = st.phi.copy()
+    np.testing.assert_array_equal(st.phi_tilde(), np.clip(2 * phi2 - phi1, 0.0, 1.0))
+    r3 = pdas.loading_step(st, 1.5e-3)
+    assert r1.converged and r2.converged and r3.converged
+    assert np.all(phi2 <= phi1 + 1e-15) and np.all(st.phi <= phi2 + 1e-15)   # phi <= phi_old
+    # the opening grows with the pressure and stays bounded (no kappa-only region is loaded)
+    assert np.max(np.abs(st.u)) < 10 * 1.5e-3
