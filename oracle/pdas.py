@@ -7,9 +7,12 @@ phi <= phi_old (Section 2):
   repeat for k = 0, 1, ...
     1. residual F = -r(U^k)                                   (model.gradient)
     2. active set A_k = {i : F_phi,i / m_i + c (phi_i - phi_old,i) > tau}
-       with the lumped phase-field mass m (the paper's "B"), c > 0 and the
-       printed threshold read as round-off size, tau = 64 u G_c / eps
-       (u = 2^-53), so that exact ties resolve alike on every machine; indices
+       with the lumped phase-field mass m (the paper's "B").  The paper gives
+       neither c nor the threshold of its printed rule; both are read in units
+       of the crack-energy stiffness G_c/eps, which makes the two terms of the
+       indicator commensurate: c = c_rel G_c/eps, tau = tol_active G_c/eps
+       (tol_active = 1e-12: indicators below it are numerically zero, e.g. far
+       from the crack where phi differs from 1 by ~1e-13); indices
        that change membership ``cycle_lock`` times in this loading step are
        locked active (Section 3: alternating active-set indices are detected
        and constrained to avoid cycles)
@@ -23,7 +26,9 @@ phi <= phi_old (Section 2):
     6. line search: omega = 1, halved while the scaled reduced residual does
        not decrease (at most ``max_halvings`` times)
   until the active set is unchanged, the scaled reduced residual has dropped
-  by ``tol_newton`` and the last Newton step was below ``tol_step``.
+  by ``tol_newton`` (or below the round-off floor ``atol_newton``; a loading
+  step that starts near its solution cannot drop by 1e-10) and the last
+  Newton step was below ``tol_step``.
 
 After a converged loading step phi_prev <- phi_old, phi_old <- phi.  The
 extrapolation phi~ (Section 2, "linear extrapolation in time") is read as
@@ -46,14 +51,15 @@ from .model import Params, gradient, jacobian, lumped_mass, scaling
 
 @dataclass
 class Options:
-    c: float = 1.0               # active-set constant c of step 2
+    c: float = 0.1               # active-set constant of step 2, in units of G_c / eps
     tol_newton: float = 1e-10    # scaled reduced residual, relative to iteration 0
+    atol_newton: float = 1e-14   # ... or absolute (round-off floor of the scaled residual)
     tol_step: float = 1e-9       # last Newton step, relative to the iterate (per block, inf-norm)
     max_newton: int = 50
     max_halvings: int = 10
     cycle_lock: int = 3
     full_jacobian: bool = False
-    active_tol_ulps: float = 64.0   # tau = active_tol_ulps * 2^-53 * G_c / eps
+    tol_active: float = 1e-12    # threshold tau of step 2, in units of G_c / eps
 
 
 @dataclass
@@ -136,8 +142,13 @@ def _solve_reduced(J, rhs, free, nu_dofs, full_jacobian):
 
 
 def active_threshold(prm: Params, opts: Options) -> float:
-    """tau of step 2: the threshold of the printed active-set rule, read as round-off size."""
-    return opts.active_tol_ulps * 2.0 ** -53 * prm.Gc / prm.eps
+    """tau of step 2: the threshold of the printed active-set rule, tol_active G_c / eps."""
+    return opts.tol_active * prm.Gc / prm.eps
+
+
+def active_constant(prm: Params, opts: Options) -> float:
+    """c of step 2: c_rel G_c / eps."""
+    return opts.c * prm.Gc / prm.eps
 
 
 def active_indicator(F_phi, m, phi, phi_old, c):
@@ -164,7 +175,7 @@ def loading_step(st: State, p: float, opts: Options = Options()) -> StepReport:
     for k in range(opts.max_newton + 1):
         r_u, r_phi = gradient(mesh, prm, u, phi, phit)
         F = -np.concatenate([r_u.ravel(), r_phi])
-        ind = active_indicator(F[nu_dofs:], m, phi, phi_old, opts.c)
+        ind = active_indicator(F[nu_dofs:], m, phi, phi_old, active_constant(prm, opts))
         raw = ind > active_threshold(prm, opts)
         if raw_prev is not None:
             toggles += raw != raw_prev
@@ -178,7 +189,8 @@ def loading_step(st: State, p: float, opts: Options = Options()) -> StepReport:
         rep.history.append(rho_inf)
         rep.changed = int(np.count_nonzero(A != A_prev)) if A_prev is not None else int(A.sum())
         done = (A_prev is not None and np.array_equal(A, A_prev)
-                and rho_inf <= opts.tol_newton * rep.rho0 and last_small) or rep.rho0 == 0.0
+                and rho_inf <= max(opts.tol_newton * rep.rho0, opts.atol_newton)
+                and last_small) or rep.rho0 == 0.0
         if done or k == opts.max_newton:
             rep.converged = bool(done)
             rep.newton_its = k
@@ -214,8 +226,7 @@ def loading_step(st: State, p: float, opts: Options = Options()) -> StepReport:
         raw_prev, A_prev = raw, A
     rep.active = int(A.sum())
     rep.locked = int(locked.sum())
-    lam_inf = float(np.max(np.abs(F[nu_dofs:] / m))) if n else 0.0
-    rep.ties = int(np.count_nonzero(np.abs(ind) < 1e-14 * (lam_inf + opts.c)))
+    rep.ties = int(np.count_nonzero(np.abs(ind) <= active_threshold(prm, opts)))
     st.u, st.phi = u, phi
     st.phi_prev, st.phi_old = st.phi_old, phi.copy()
     st.steps_done += 1

@@ -123,7 +123,7 @@ def test_staggered_projected_gauss_seidel_reaches_same_point():
 
 def test_path_options_reach_same_point(solved32):
     w, mesh, prm, st, rep = solved32
-    for opts in (pdas.Options(full_jacobian=True), pdas.Options(c=10.0)):
+    for opts in (pdas.Options(full_jacobian=True), pdas.Options(c=0.02)):
         st2 = pdas.State.initial(mesh, prm, w.phi0())
         rep2 = pdas.loading_step(st2, w.pressures[0], opts)
         assert rep2.converged
