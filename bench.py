@@ -1,0 +1,371 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 pressurized phase-field fracture solver.
+
+One benchmark step = the whole hot path on the 2d graded Sneddon workload
+(1024 x 1024 Q1 cells, graded from h_min = 2e-4 on [-10, 10]^2, 3,151,875
+DoFs): five loading steps with the pressure ramped to 1e-3, each solved to
+convergence by the Newton / active-set method with FGMRES + AMG on the device,
+followed by TCV and the COD at 64 points.
+
+value  = DoF/s = (loading steps solved x DoFs) / device time, inputs resident
+         in HBM (the state is reset from device buffers each step).
+e2e    = the same through the C ABI with host buffers: the initial state is
+         copied host -> device and the solution device -> host every step.
+cpu_baseline / --impl reference = the CPU oracle (oracle/) on a bounded sample
+         of the same workload recipe, on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+Multi-GPU runs (torchrun) are independent replicas: each rank solves its own
+copy of the workload; value sums the ranks' work over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Newton-Krylov solves/s & DoF/s at <=1e-8 rel err; p50/p99 latency; HBM GB/s"
+UNIT = "DoF/s"
+WORKLOAD_INDEX = 1          # the 2d graded 1024^2 Sneddon configuration
+SAMPLE_CELLS = 128          # oracle sample: same recipe at 128^2 cells
+SAMPLE_STEPS = 2            # loading steps of the sample timed by the CPU baseline
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------ CPU oracle ----
+ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle import fe, model, pdas
+w = W.scaled_workload(W.config({idx}), {cells})
+mesh = fe.Mesh(w.coords)
+prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressures[0])
+st = pdas.State.initial(mesh, prm, w.phi0())
+times = []
+for k in range({nsteps}):
+    p = w.pressures[k % len(w.pressures)]
+    if k % len(w.pressures) == 0 and k > 0:
+        st = pdas.State.initial(mesh, prm, w.phi0())
+    t = time.perf_counter()
+    rep = pdas.loading_step(st, p)
+    times.append(time.perf_counter() - t)
+print(json.dumps({{"times": times, "n_dofs": w.n_dofs, "name": w.name}}))
+"""
+
+
+def run_oracle(nsteps: int, cells: int = SAMPLE_CELLS):
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        env[k] = "1"
+    code = ORACLE_SNIPPET.format(root=ROOT, idx=WORKLOAD_INDEX, cells=cells, nsteps=nsteps)
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
+                         check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline():
+    r = run_oracle(SAMPLE_STEPS)
+    total = sum(r["times"])
+    return {"value": SAMPLE_STEPS * r["n_dofs"] / total, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{SAMPLE_STEPS} loading steps (p = 2e-4, 4e-4) of the same recipe at "
+                      f"{SAMPLE_CELLS}^2 cells ({r['n_dofs']} DoFs), {total:.1f} s single-threaded"}
+
+
+def reference_arm(args, rank, world):
+    if rank != 0:
+        return 0
+    r = run_oracle(args.warmup + args.steps)
+    times = r["times"][args.warmup:]
+    total = sum(times)
+    value = len(times) * r["n_dofs"] / total
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": r["name"], "loading_steps_per_step": 1,
+                                            "n_dofs": r["n_dofs"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
+                             "sample": f"one loading step per bench step at {SAMPLE_CELLS}^2 cells "
+                                       f"({r['n_dofs']} DoFs) of the graded 1024^2 recipe"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ clocks ----
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "-i", self.gpu_id,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["active", "hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names[1:], parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# -------------------------------------------------------------- GPU arm ----
+def _kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1806_09924_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic_for(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it is current."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    e = d.get(kernel)
+    if not e or e.get("source_hash") != _kernel_hash():
+        return None
+    return e.get("dram_bytes_per_launch_full_size")
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import numpy as np
+    import torch
+    import paper_1806_09924_gb300 as pff
+    import workloads as W
+    from oracle import functionals as fn
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    w = W.config(WORKLOAD_INDEX)
+    prec = pff.PFF_PREC_MIXED if args.precision == "mixed" else pff.PFF_PREC_FP64
+    opts = pff.options(precision=prec)
+    stream = torch.cuda.Stream()
+    P = pff.problem_from_workload(w)
+    P.set_stream(stream)
+    n, d = P.n_nodes, w.dim
+    phi0_h = w.phi0()
+    u0_h = np.zeros((n, d))
+    dev = torch.device("cuda", local_rank)
+    u0 = torch.zeros(n * d, dtype=torch.float64, device=dev)
+    phi0 = torch.tensor(phi0_h, device=dev)
+    pts = fn.cod_points(w.l0, 64)
+    pressures = list(w.pressures)
+
+    def step_device():
+        P.set_state_dev(u0, phi0, phi0, phi0, 0)
+        reps = P.solve_loading_steps(pressures, opts)
+        tcv, cod = P.eval_tcv_cod(pts)
+        return reps, tcv, cod
+
+    def step_e2e():
+        P.set_state(u0_h, phi0_h, phi0_h, phi0_h, 0)
+        reps = P.solve_loading_steps(pressures, opts)
+        tcv, cod = P.eval_tcv_cod(pts)
+        u, phi, act = P.get_solution()
+        return reps, tcv, cod
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            reps, tcv, cod = step_device()
+        # timed region: resident inputs
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        gpu_id = str(local_rank)
+        try:
+            gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+        except Exception:
+            pass
+        sampler = ClockSampler(gpu_id)
+        sampler.start()
+        pff.profile_enable(True)
+        launches0 = pff.launch_count()
+        ev0 = torch.cuda.Event(enable_timing=True)
+        ev1 = torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        all_reps = []
+        for _ in range(args.steps):
+            reps, tcv, cod = step_device()
+            all_reps.append(reps)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        launches = pff.launch_count() - launches0
+        prof = pff.profile_report()
+        pff.profile_enable(False)
+        clocks = sampler.stop()
+        ms = ev0.elapsed_time(ev1)
+        if dist:
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+            dist.barrier()
+        # e2e through host buffers
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            step_e2e()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_ms = max(e0.elapsed_time(e1), 1e3 * (time.perf_counter() - t0))
+        if dist:
+            t = torch.tensor([e2e_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms = float(t.item())
+        # accuracy of this precision against the FP64 GPU path (untimed)
+        err = None
+        if prec == pff.PFF_PREC_MIXED and rank == 0:
+            u_m, phi_m, _ = P.get_solution()
+            Q = pff.problem_from_workload(w)
+            Q.solve_loading_steps(pressures, pff.options(precision=pff.PFF_PREC_FP64))
+            u_f, phi_f, _ = Q.get_solution()
+            Q.close()
+            err = {"u": float(np.linalg.norm(u_m - u_f) / np.linalg.norm(u_f)),
+                   "phi": float(np.linalg.norm(phi_m - phi_f) / np.linalg.norm(phi_f))}
+    P.close()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    solves = args.steps * len(pressures)
+    dofs = solves * w.n_dofs * world
+    value = dofs / (ms / 1e3)
+    h2d = n * (d + 3) * 8
+    d2h = n * (d * 8 + 8 + 1) + 8 * (len(pts) + 1)
+    # dominant instrumented kernel and its roofline
+    peak, peak_kind = _peaks()
+    top = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+    roof = None
+    if top:
+        name, st = top
+        per_launch_bytes = st["bytes"] / max(st["count"], 1)
+        avg_ms = st["ms"] / max(st["count"], 1)
+        achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
+        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": _traffic_for(name),
+                "peak_source": f"{peak_kind} hbm_gbs", "launches": st["count"],
+                "avg_launch_us": 1e3 * avg_ms, "algorithmic_bytes_per_launch": per_launch_bytes,
+                "share_of_step_time": st["ms"] / ms}
+    last = all_reps[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64+f32" if prec == pff.PFF_PREC_MIXED else "f64", "data": "synthetic",
+        "config": {"workload": w.name, "n_cells": "1024x1024", "n_dofs": w.n_dofs,
+                   "loading_steps_per_step": len(pressures), "precision": args.precision,
+                   "grading": "geometric from h_min=2e-4, ratio solved to fill [-10,10]",
+                   "l2": "working set (state, stencils, AMG, Krylov basis) is several GB, > L2",
+                   "parallelism": f"replicas x{world}"},
+        "solves_per_s": solves * world / (ms / 1e3),
+        "newton_its": [r["newton_its"] for r in last],
+        "krylov_its": [r["krylov_its"] for r in last],
+        "krylov_its_max": [r["krylov_its_max"] for r in last],
+        "tcv": tcv, "cod_center": float(cod[len(cod) // 2]),
+        "rel_err_vs_fp64_path": err,
+        "gpu_launches": int(launches),
+        "e2e": {"value": dofs / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "roofline": roof,
+        "kernels": {k: {"count": v["count"], "ms": round(v["ms"], 3),
+                        "GB/s": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 else None}
+                    for k, v in sorted(prof.items(), key=lambda kv: -kv[1]["ms"])[:12]},
+        "clocks": clocks,
+    }
+    if world == 1 and not args.no_cpu_baseline:
+        try:
+            line["cpu_baseline"] = cpu_baseline()
+        except Exception as e:   # the CPU leg must not hide the GPU number
+            line["cpu_baseline"] = {"error": str(e)[:200]}
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return reference_arm(args, rank, world)
+    return gpu_arm(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

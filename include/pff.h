@@ -65,8 +65,10 @@ typedef struct pff_problem pff_problem;
 /* Solver options.  pff_default_options fills the defaults given here. */
 typedef struct pff_options {
   int precision;        /* PFF_PREC_FP64 (default) or PFF_PREC_MIXED */
-  double c;             /* active-set constant c > 0 (Section 3 algorithm, step 2); 1 */
-  double tol_newton;    /* stop when the scaled reduced residual (inf-norm) fell by this; 1e-10 */
+  double c;             /* active-set constant c > 0 (Section 3 algorithm, step 2), in units
+                           of G_c/eps: indicator = F_phi/m + c (G_c/eps)(phi - phi_old); 0.1 */
+  double tol_newton;    /* stop when the scaled reduced residual (inf-norm) fell by this
+                           (or below atol_newton); 1e-10 */
   double tol_step;      /* ... and the last Newton step is below this, relative per block; 1e-9 */
   double tol_linear;    /* FGMRES relative residual (Table 1 uses 1e-8); 1e-8 */
   int max_newton;       /* Newton / active-set iterations per loading step; 50 */
@@ -75,11 +77,15 @@ typedef struct pff_options {
   int krylov_restart;   /* FGMRES restart length m; 40 */
   int max_krylov;       /* FGMRES iterations per linear solve; 600 */
   int cheb_degree;      /* Chebyshev smoother degree; 2 */
-  double amg_theta;     /* strength-of-connection threshold; 0.08 */
+  double amg_theta;     /* strength threshold on the distance Laplacian of the mesh nodes
+                           (w_ij = 1/|x_i - x_j|^2 strong iff w_ij^2 >= theta^2 wmax_i wmax_j); 0.25 */
   int amg_coarse_max;   /* largest coarse level (scalar rows) solved directly; 320 */
   int apply_variant;    /* PFF_APPLY_*; PFF_APPLY_AUTO */
   int precond;          /* PFF_PC_*; PFF_PC_AMG */
-  int reserved[8];
+  double cheb_ratio;    /* Chebyshev smoothing interval [lmax/ratio, 1.1 lmax]; 8 */
+  double tol_active;    /* active-set threshold tau, in units of G_c/eps; 1e-12 */
+  double atol_newton;   /* absolute floor of the scaled reduced residual test; 1e-14 */
+  int reserved[2];
 } pff_options;
 
 /* Per loading step (or per Newton iteration for pff_newton_step) report. */
@@ -118,8 +124,10 @@ int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_c
 int pff_set_material(pff_problem* prob, double E, double nu, double Gc, double kappa, double eps);
 
 /* Start a loading step with constant pressure p (Section 4 uses p = 1e-3):
- * forms the extrapolation phi~ (phi_old in the first step, clamp(2 phi_old -
- * phi_prev, 0, 1) afterwards) and resets the per-step Newton state. */
+ * forms the extrapolation phi~ of Section 2 (phi_old in the first two steps,
+ * whose history starts at the initial crack field rather than a computed
+ * solution; clamp(2 phi_old - phi_prev, 0, 1) afterwards) and resets the
+ * per-step Newton state. */
 int pff_set_pressure(pff_problem* prob, double p);
 
 /* Crack of half length / radius l0 centred at the origin (Section 4): phi =
@@ -202,6 +210,28 @@ int pff_precond_apply_dev(pff_problem* prob, const double* r_dev, double* z_dev)
  * the Jacobi-scaled residual).  *iters receives the iteration count. */
 int pff_linear_solve_dev(pff_problem* prob, const pff_options* opts, const double* b_dev,
                          double* x_dev, int* iters);
+
+/* Same as pff_set_state with device arrays of the current device (copied
+ * device-to-device on the problem's stream; NULL keeps the current value). */
+int pff_set_state_dev(pff_problem* prob, const double* u_dev, const double* phi_dev,
+                      const double* phi_old_dev, const double* phi_prev_dev, int steps_done);
+
+/* Instrumentation (process-wide, all problems) ----------------------------- */
+
+/* Enable (1) or disable (0) per-kernel timing and reset its totals.  When
+ * enabled, each instrumented launch records a CUDA event pair on its stream
+ * and is credited with its algorithmic bytes (every input and output array
+ * moved once).  Adds a few microseconds per launch. */
+int pff_profile_enable(int on);
+
+/* Synchronize the device and write per-kernel totals as a JSON object
+ * {"name": {"count": launches, "ms": total time, "bytes": algorithmic bytes}}
+ * into buf (NUL-terminated, truncated to buflen).  Returns the length needed
+ * including the NUL. */
+int pff_profile_report(char* buf, int buflen);
+
+/* Number of kernels launched by the library since it was loaded. */
+long long pff_launch_count(void);
 
 #ifdef __cplusplus
 }

@@ -44,7 +44,8 @@ class PffOptions(ctypes.Structure):
         ("max_halvings", ctypes.c_int), ("cycle_lock", ctypes.c_int), ("krylov_restart", ctypes.c_int),
         ("max_krylov", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("amg_theta", ctypes.c_double),
         ("amg_coarse_max", ctypes.c_int), ("apply_variant", ctypes.c_int), ("precond", ctypes.c_int),
-        ("reserved", ctypes.c_int * 8),
+        ("cheb_ratio", ctypes.c_double), ("tol_active", ctypes.c_double),
+        ("atol_newton", ctypes.c_double), ("reserved", ctypes.c_int * 2),
     ]
 
 
@@ -96,6 +97,10 @@ _SIGS = {
     "pff_precond_apply_dev": (ctypes.c_int, [_P, _P, _P]),
     "pff_linear_solve_dev": (ctypes.c_int, [_P, ctypes.POINTER(PffOptions), _P, _P,
                                             ctypes.POINTER(ctypes.c_int)]),
+    "pff_set_state_dev": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
+    "pff_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "pff_profile_report": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
+    "pff_launch_count": (ctypes.c_longlong, []),
 }
 
 _lib = None
@@ -107,7 +112,7 @@ def load_library(path: str = LIB_PATH):
     if _lib is not None:
         return _lib
     if not os.path.exists(path):
-        raise ImportError(f"{path} is missing: build it with `python -m paper_1806_09924_gb300.build`")
+        raise ImportError(f"{path} is missing: build it with `python paper_1806_09924_gb300/build.py`")
     lib = ctypes.CDLL(path)
     for name, (res, args) in _SIGS.items():
         fn = getattr(lib, name)
@@ -202,6 +207,12 @@ class Problem:
         bufs = [_host(a) for a in (u, phi, phi_old, phi_prev)]
         _check(self._lib.pff_set_state(self._h, *[b[1] for b in bufs], int(steps_done)))
 
+    def set_state_dev(self, u=None, phi=None, phi_old=None, phi_prev=None, steps_done=0):
+        n = self.n_nodes
+        _check(self._lib.pff_set_state_dev(self._h, _dev(u, "torch.float64", n * self.dim),
+                                           _dev(phi, "torch.float64", n), _dev(phi_old, "torch.float64", n),
+                                           _dev(phi_prev, "torch.float64", n), int(steps_done)))
+
     def set_stream(self, stream):
         ptr = stream if isinstance(stream, int) else getattr(stream, "cuda_stream", None)
         _check(self._lib.pff_set_stream(self._h, ctypes.c_void_p(ptr)))
@@ -275,6 +286,26 @@ class Problem:
         _check(self._lib.pff_linear_solve_dev(self._h, ctypes.byref(o), _dev(b, "torch.float64", self.n_dofs),
                                               _dev(x, "torch.float64", self.n_dofs), ctypes.byref(it)))
         return it.value
+
+
+def profile_enable(on: bool = True):
+    """Enable / disable per-kernel event timing (resets the totals)."""
+    _check(load_library().pff_profile_enable(1 if on else 0))
+
+
+def profile_report() -> dict:
+    """Per-kernel {"count", "ms", "bytes"} totals since profile_enable."""
+    import json
+    lib = load_library()
+    need = lib.pff_profile_report(None, 0)
+    buf = ctypes.create_string_buffer(need + 16)
+    lib.pff_profile_report(buf, need + 16)
+    return json.loads(buf.value.decode())
+
+
+def launch_count() -> int:
+    """Kernels launched by the library since it was loaded."""
+    return int(load_library().pff_launch_count())
 
 
 def problem_from_workload(w, crack: bool = True) -> Problem:

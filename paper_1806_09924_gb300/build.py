@@ -1,8 +1,9 @@
 """Build the CUDA library libpff.so in-tree for GB300 (sm_103a).
 
 Every translation unit under csrc/ is compiled in parallel with nvcc and
-linked into paper_1806_09924_gb300/libpff.so.  Run ``python -m
-paper_1806_09924_gb300.build`` or call ``build()``.
+linked into paper_1806_09924_gb300/libpff.so.  Run ``python
+paper_1806_09924_gb300/build.py`` (importing the package itself needs the
+built library) or call ``build()``.
 """
 from __future__ import annotations
 

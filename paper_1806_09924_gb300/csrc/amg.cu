@@ -15,13 +15,15 @@
 //     3. tentative prolongator: per-aggregate thin QR (modified Gram-Schmidt,
 //        twice) of the near-null space (rigid-body modes / constants); R gives
 //        the coarse near-null space
-//     4. P = (I - omega D^-1 A) P_tent, omega = 4 / (3 lambda_max(D^-1 A))
+//     4. P = (I - omega D_F^-1 A_F) P_tent, omega = 4 / (3 lambda_max(D^-1 A)),
+//        A_F = A with weak off-diagonal blocks lumped into the diagonal block
 //     5. R = P^T, A_c = R A P (two row-wise SpGEMMs with sorted unique columns)
 //     6. coarsest level: dense inverse (Gauss-Jordan with partial pivoting)
 //   V-cycle: Chebyshev(D^-1 A) pre/post smoothing, restriction, coarse solve,
 //   prolongation; FP64 or FP32 (mixed precision) values and vectors.
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 
 #include "pff_internal.h"
 
@@ -88,6 +90,67 @@ __global__ void k_strength(int n, int b, const int* __restrict__ rp, const int* 
     for (int e = 0; e < b * b; ++e) s += v[e] * v[e];
     snorm[k] = s;
     strong[k] = (J != I) && (s > theta2 * dnorm[I] * dnorm[J]);
+  }
+}
+
+// Distance-Laplacian strength (for meshes with stretched cells, where the Q1
+// matrix entries of the weak direction stay O(aspect ratio)): w_IJ = 1/|x_I -
+// x_J|^2, strong iff w_IJ^2 >= theta^2 wmax_I wmax_J, and the matrix block is
+// not negligible, ||A_IJ||^2 > mdrop^2 ||A_II|| ||A_JJ|| (this keeps the
+// couplings of kappa-degenerate crack nodes and eliminated columns weak).
+__device__ __forceinline__ double dist_w(const double* __restrict__ X, int cd, int I, int J) {
+  double d2 = 0.0;
+  for (int l = 0; l < cd; ++l) {
+    const double t = X[(int64_t)I * cd + l] - X[(int64_t)J * cd + l];
+    d2 += t * t;
+  }
+  return d2 > 0.0 ? 1.0 / d2 : 1e300;
+}
+
+__global__ void k_dist_wmax(int n, const int* __restrict__ rp, const int* __restrict__ col,
+                            const double* __restrict__ X, int cd, double* __restrict__ wmax) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  double m = 0.0;
+  for (int k = rp[I]; k < rp[I + 1]; ++k)
+    if (col[k] != I) m = fmax(m, dist_w(X, cd, I, col[k]));
+  wmax[I] = m;
+}
+
+__global__ void k_strength_dist(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
+                                const double* __restrict__ val, const double* __restrict__ dnorm,
+                                const double* __restrict__ X, int cd,
+                                const double* __restrict__ wmax, double theta2, double mdrop2,
+                                uint8_t* __restrict__ strong, double* __restrict__ snorm) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  if (I >= n) return;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int J = col[k];
+    if (J == I) {
+      strong[k] = 0;
+      snorm[k] = 0.0;
+      continue;
+    }
+    const double* v = val + (int64_t)k * b * b;
+    double m = 0.0;
+    for (int e = 0; e < b * b; ++e) m += v[e] * v[e];
+    const double w = dist_w(X, cd, I, J);
+    const bool s = (w * w >= theta2 * wmax[I] * wmax[J]) && (m > mdrop2 * dnorm[I] * dnorm[J]);
+    strong[k] = s;
+    snorm[k] = w;
+  }
+}
+
+// coarse-level coordinates: centroid of each aggregate's members
+__global__ void k_centroids(int nagg, const int* __restrict__ off, const int* __restrict__ members,
+                            const double* __restrict__ X, int cd, double* __restrict__ Xc) {
+  const int a = blockIdx.x * blockDim.x + threadIdx.x;
+  if (a >= nagg) return;
+  const int lo = off[a], hi = off[a + 1];
+  for (int l = 0; l < cd; ++l) {
+    double s = 0.0;
+    for (int t = lo; t < hi; ++t) s += X[(int64_t)members[t] * cd + l];
+    Xc[(int64_t)a * cd + l] = hi > lo ? s / (hi - lo) : 0.0;
   }
 }
 
@@ -352,7 +415,8 @@ __device__ __forceinline__ bool insert_unique(int* u, int& len, int c) {
 
 // P = (I - omega D^-1 A) P_tent: count unique aggregate columns per row
 __global__ void k_P_count(int n, const int* __restrict__ rp, const int* __restrict__ col,
-                          const int* __restrict__ agg, int* __restrict__ cnt, int* __restrict__ err) {
+                          const uint8_t* __restrict__ strong, const int* __restrict__ agg,
+                          int* __restrict__ cnt, int* __restrict__ err) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
   int u[CAP];
@@ -360,8 +424,8 @@ __global__ void k_P_count(int n, const int* __restrict__ rp, const int* __restri
   bool ok = true;
   if (agg[I] >= 0) ok &= insert_unique(u, len, agg[I]);
   for (int k = rp[I]; k < rp[I + 1]; ++k) {
-    const int a = agg[col[k]];
-    if (a >= 0) ok &= insert_unique(u, len, a);
+    const int J = col[k];
+    if (J != I && strong[k] && agg[J] >= 0) ok &= insert_unique(u, len, agg[J]);
   }
   if (!ok) atomicExch(err, 2);
   cnt[I] = len;
@@ -369,9 +433,9 @@ __global__ void k_P_count(int n, const int* __restrict__ rp, const int* __restri
 
 __global__ void k_P_fill(int n, int br, int nns, const int* __restrict__ rp,
                          const int* __restrict__ col, const double* __restrict__ val,
-                         const int* __restrict__ agg, const double* __restrict__ Qn,
-                         const double* __restrict__ dinv, double omega,
-                         const int* __restrict__ prp, int* __restrict__ pcol,
+                         const uint8_t* __restrict__ strong, const int* __restrict__ agg,
+                         const double* __restrict__ Qn, const double* __restrict__ dinv,
+                         double omega, const int* __restrict__ prp, int* __restrict__ pcol,
                          double* __restrict__ pval) {
   const int I = blockIdx.x * blockDim.x + threadIdx.x;
   if (I >= n) return;
@@ -379,8 +443,8 @@ __global__ void k_P_fill(int n, int br, int nns, const int* __restrict__ rp,
   int len = 0;
   if (agg[I] >= 0) insert_unique(u, len, agg[I]);
   for (int k = rp[I]; k < rp[I + 1]; ++k) {
-    const int a = agg[col[k]];
-    if (a >= 0) insert_unique(u, len, a);
+    const int J = col[k];
+    if (J != I && strong[k] && agg[J] >= 0) insert_unique(u, len, agg[J]);
   }
   const int base = prp[I];
   const int bs = br * nns;
@@ -389,23 +453,45 @@ __global__ void k_P_fill(int n, int br, int nns, const int* __restrict__ rp,
     double* dst = pval + (int64_t)(base + p) * bs;
     for (int e = 0; e < bs; ++e) dst[e] = 0.0;
   }
-  if (agg[I] >= 0) {
-    const int p = find_col(pcol, base, base + len, agg[I]);
-    if (p < 0) return;   // capacity overflow, reported by k_P_count
-    double* dst = pval + (int64_t)p * bs;
+  if (agg[I] < 0) return;   // isolated rows keep a zero prolongator row
+  const int pI = find_col(pcol, base, base + len, agg[I]);
+  if (pI < 0) return;       // capacity overflow, reported by k_P_count
+  {
+    double* dst = pval + (int64_t)pI * bs;
     for (int e = 0; e < bs; ++e) dst[e] = Qn[(int64_t)I * bs + e];
+  }
+  // filtered operator: weak off-diagonal blocks are lumped into the diagonal
+  // block (row sums, hence the translations, are kept)
+  double L[36];
+  for (int e = 0; e < br * br; ++e) L[e] = 0.0;
+  int kd = -1;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const int J = col[k];
+    if (J == I) kd = k;
+    if (J == I || !strong[k]) {
+      const double* Ablk = val + (int64_t)k * br * br;
+      for (int e = 0; e < br * br; ++e) L[e] += Ablk[e];
+    }
+  }
+  if (kd < 0) return;
+  double dF[6];
+  for (int r = 0; r < br; ++r) {
+    const double aii = val[(int64_t)kd * br * br + r * br + r];
+    dF[r] = L[r * br + r] > 0.1 * aii ? 1.0 / L[r * br + r] : dinv[(int64_t)I * br + r];
   }
   for (int k = rp[I]; k < rp[I + 1]; ++k) {
     const int J = col[k];
+    const bool diag = J == I;
+    if (!diag && !strong[k]) continue;
     const int a = agg[J];
     if (a < 0) continue;
-    const int p = find_col(pcol, base, base + len, a);
+    const int p = diag ? pI : find_col(pcol, base, base + len, a);
     if (p < 0) continue;
     double* dst = pval + (int64_t)p * bs;
-    const double* Ablk = val + (int64_t)k * br * br;
+    const double* Ablk = diag ? L : val + (int64_t)k * br * br;
     const double* Q = Qn + (int64_t)J * bs;
     for (int r = 0; r < br; ++r) {
-      const double w = omega * dinv[(int64_t)I * br + r];
+      const double w = omega * dF[r];
       for (int j = 0; j < nns; ++j) {
         double s = 0.0;
         for (int c = 0; c < br; ++c) s += Ablk[r * br + c] * Q[c * nns + j];
@@ -613,6 +699,29 @@ __global__ void k_dinv_spmv(int n, int b, const int* __restrict__ rp, const int*
   y[r] = dinv[r] * s;
 }
 
+// y = D^-1/2 A D^-1/2 x (D = scalar diagonal, dinv = 1/D or 0)
+__global__ void k_sym_spmv(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
+                           const double* __restrict__ val, const double* __restrict__ dinv,
+                           const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= (int64_t)n * b) return;
+  const int I = (int)(r / b), a = (int)(r % b);
+  double s = 0.0;
+  for (int k = rp[I]; k < rp[I + 1]; ++k) {
+    const double* v = val + ((int64_t)k * b + a) * b;
+    const int64_t j0 = (int64_t)col[k] * b;
+    for (int c = 0; c < b; ++c) s += v[c] * sqrt(dinv[j0 + c]) * x[j0 + c];
+  }
+  y[r] = sqrt(dinv[r]) * s;
+}
+
+// Lanczos three-term update w -= alpha v + beta v_prev
+__global__ void k_lanczos(int64_t n, double* __restrict__ w, const double* __restrict__ v,
+                          const double* __restrict__ vp, double alpha, double beta) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] -= alpha * v[i] + beta * vp[i];
+}
+
 __global__ void k_hash_vec(int64_t n, double* __restrict__ x) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = (double)(hash32((uint32_t)i * 2654435761u + 12345u) & 0xffffff) / 16777216.0 + 0.1;
@@ -712,10 +821,10 @@ void spmv_t<float>(const Bsr& A, const float* x, float* y, float a, float b, cud
 }
 
 template <class T>
-void smooth(const AmgLevel& L, int degree, const T* rhs, T* x, T* t, T* d, bool zero_start,
+void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* t, T* d, bool zero_start,
             cudaStream_t s) {
   // Chebyshev iteration for D^-1 A on [lmax/30, 1.1 lmax]
-  const double beta = 1.1 * L.lmax, alpha = L.lmax / 30.0;
+  const double beta = 1.1 * L.lmax, alpha = L.lmax / ratio;
   const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
   const double sigma = theta / delta;
   double rho = 1.0 / sigma;
@@ -724,12 +833,19 @@ void smooth(const AmgLevel& L, int degree, const T* rhs, T* x, T* t, T* d, bool 
   const unsigned g = grid_for((int64_t)nb * b, 256);
   T* cur = x;
   T* nxt = t;
+  // algorithmic bytes of one step: matrix (values, columns, row pointers) once,
+  // plus dinv, rhs, x_in, x_out and d read + write (x_in / d skipped from zero)
+  const double mat_b = (double)A.nnzb * (b * b * (double)sizeof(T) + 4.0) + 4.0 * (nb + 1.0);
+  const double nvec = (double)nb * b * sizeof(T);
+  const char* tag = sizeof(T) == 8 ? "cheb_f64" : "cheb_f32";
   // first step: d = r / theta
+  ProfScope ps0(tag, (zero_start ? 0.0 : mat_b) + nvec * (zero_start ? 4.0 : 6.0), s);
   k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
                               T(0), T(1.0 / theta), zero_start ? 1 : 0);
   std::swap(cur, nxt);
   for (int k = 1; k < degree; ++k) {
     const double rn = 1.0 / (2.0 * sigma - rho);
+    ProfScope psk(tag, mat_b + 6.0 * nvec, s);
     k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
                                 T(rn * rho), T(2.0 * rn / delta), 0);
     std::swap(cur, nxt);
@@ -745,6 +861,7 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
     const T* M = nullptr;
     if constexpr (sizeof(T) == 8) M = reinterpret_cast<const T*>(amg.cinv);
     else M = reinterpret_cast<const T*>(amg.cinvf);
+    ProfScope ps("coarse_solve", (double)sizeof(T) * amg.nc * (amg.nc + 2.0), s);
     k_dense_mv<T><<<grid_for(amg.nc, 8), 256, 0, s>>>(amg.nc, M, rhs, x);
     PFF_LAUNCH("coarse");
     return;
@@ -753,21 +870,26 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
   T* t = reinterpret_cast<T*>(L.t);
   T* d = reinterpret_cast<T*>(L.d);
   T* r = reinterpret_cast<T*>(L.r);
-  smooth<T>(L, amg.cheb_degree, rhs, x, t, d, true, s);
+  smooth<T>(L, amg.cheb_degree, amg.cheb_ratio, rhs, x, t, d, true, s);
   if (L.terminal) {
-    smooth<T>(L, amg.cheb_degree, rhs, x, t, d, false, s);
+    smooth<T>(L, amg.cheb_degree, amg.cheb_ratio, rhs, x, t, d, false, s);
     return;
   }
   const Bsr& A = L.A;
+  {
+    ProfScope ps(sizeof(T) == 8 ? "resid_f64" : "resid_f32",
+                 (double)A.nnzb * (A.br * A.bc * (double)sizeof(T) + 4.0) + 4.0 * (A.nrows + 1.0) +
+                     3.0 * sizeof(T) * (double)A.nrows * A.br, s);
   k_resid<T><<<grid_for((int64_t)A.nrows * A.br, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr, A.col,
                                                                     vals<T>(A), rhs, x, r);
+  }
   const bool last = l + 1 == (int)amg.lev.size();
   T* cb = last ? reinterpret_cast<T*>(amg.cb) : reinterpret_cast<T*>(amg.lev[l + 1].b);
   T* cx = last ? reinterpret_cast<T*>(amg.cx) : reinterpret_cast<T*>(amg.lev[l + 1].x);
   spmv_t<T>(L.R, r, cb, T(1), T(0), s);
   vcycle_level<T>(amg, l + 1, cb, cx, s);
   spmv_t<T>(L.P, cx, x, T(1), T(1), s);
-  smooth<T>(L, amg.cheb_degree, rhs, x, t, d, false, s);
+  smooth<T>(L, amg.cheb_degree, amg.cheb_ratio, rhs, x, t, d, false, s);
 }
 
 struct SetupScratch {
@@ -777,25 +899,80 @@ struct SetupScratch {
   double* h_red = nullptr;
 };
 
+// largest eigenvalue of the symmetric tridiagonal matrix (alpha, beta) by bisection
+// on the Sturm sequence count
+double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& b) {
+  const int m = (int)a.size();
+  double lo = 1e300, hi = -1e300;
+  for (int i = 0; i < m; ++i) {
+    const double r = (i > 0 ? std::fabs(b[i - 1]) : 0.0) + (i + 1 < m ? std::fabs(b[i]) : 0.0);
+    lo = std::min(lo, a[i] - r);
+    hi = std::max(hi, a[i] + r);
+  }
+  auto count_below = [&](double x) {   // number of eigenvalues < x
+    int c = 0;
+    double q = 1.0;
+    for (int i = 0; i < m; ++i) {
+      const double bb = i > 0 ? b[i - 1] * b[i - 1] : 0.0;
+      q = a[i] - x - (i > 0 ? bb / q : 0.0);
+      if (q == 0.0) q = -1e-300;
+      if (q < 0.0) ++c;
+    }
+    return c;
+  };
+  for (int it = 0; it < 200 && hi - lo > 1e-12 * std::max(1.0, std::fabs(hi)); ++it) {
+    const double mid = 0.5 * (lo + hi);
+    if (count_below(mid) < m) lo = mid;
+    else hi = mid;
+  }
+  return hi;
+}
+
+// lambda_max(D^-1 A) by Lanczos on the similar symmetric matrix D^-1/2 A D^-1/2:
+// the extreme Ritz value converges from below much faster than power iteration
+// on the clustered spectra of graded meshes.
 double estimate_lmax(const Bsr& A, const double* dinv, cudaStream_t s, double* partials,
                      double* dred, double* hred) {
   const int64_t n = (int64_t)A.nrows * A.br;
-  double* x = dalloc<double>(n);
-  double* y = dalloc<double>(n);
-  k_hash_vec<<<grid_for(n, 256), 256, 0, s>>>(n, x);
-  double lam = 1.0;
-  for (int it = 0; it < 12; ++it) {
-    dot_dev(x, x, n, dred, partials, s);
-    k_scale<<<grid_for(n, 256), 256, 0, s>>>(n, x, dred);
-    k_dinv_spmv<<<grid_for(n, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr, A.col, A.val, dinv, x, y);
-    dot_dev(y, y, n, dred, partials, s);
+  double* v = dalloc<double>(n);
+  double* vp = dalloc<double>(n);
+  double* w = dalloc<double>(n);
+  PFF_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * n, s));
+  count_launch();
+  k_hash_vec<<<grid_for(n, 256), 256, 0, s>>>(n, v);
+  dot_dev(v, v, n, dred, partials, s);
+  count_launch();
+  k_scale<<<grid_for(n, 256), 256, 0, s>>>(n, v, dred);
+  std::vector<double> al, be;
+  double beta = 0.0;
+  const int steps = (int)std::min<int64_t>(30, n);
+  for (int j = 0; j < steps; ++j) {
+    count_launch();
+    k_sym_spmv<<<grid_for(n, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr, A.col, A.val, dinv, v, w);
+    dot_dev(w, v, n, dred, partials, s);
     PFF_CUDA(cudaMemcpyAsync(hred, dred, sizeof(double), cudaMemcpyDeviceToHost, s));
     PFF_CUDA(cudaStreamSynchronize(s));
-    lam = std::sqrt(*hred);
-    std::swap(x, y);
+    const double alpha = *hred;
+    al.push_back(alpha);
+    count_launch();
+    k_lanczos<<<grid_for(n, 256), 256, 0, s>>>(n, w, v, vp, alpha, beta);
+    dot_dev(w, w, n, dred, partials, s);
+    PFF_CUDA(cudaMemcpyAsync(hred, dred, sizeof(double), cudaMemcpyDeviceToHost, s));
+    PFF_CUDA(cudaStreamSynchronize(s));
+    const double bn = std::sqrt(std::max(*hred, 0.0));
+    if (!(bn > 1e-14 * std::fabs(alpha)) || j + 1 == steps) break;
+    be.push_back(bn);
+    std::swap(vp, v);    // v_prev <- v
+    count_launch();
+    k_scale<<<grid_for(n, 256), 256, 0, s>>>(n, w, dred);   // w / ||w||
+    std::swap(v, w);     // v <- w / ||w||
+    beta = bn;
   }
-  dfree(x);
-  dfree(y);
+  be.resize(al.size() > 0 ? al.size() - 1 : 0);
+  const double lam = al.empty() ? 1.0 : tridiag_max_eig(al, be);
+  dfree(v);
+  dfree(vp);
+  dfree(w);
   PFF_LAUNCH("lmax");
   return lam > 0.0 ? lam : 1.0;
 }
@@ -809,6 +986,7 @@ void spgemm(const Bsr& X, const Bsr& Y, Bsr& C, int* err, cudaStream_t s) {
   C.rowptr = dalloc<int>(X.nrows + 1);
   int* cnt = dalloc<int>(X.nrows + 1);
   const unsigned g = grid_for(X.nrows, 128);
+  count_launch();
   k_mm_count<<<g, 128, 0, s>>>(X.nrows, X.rowptr, X.col, Y.rowptr, Y.col, cnt, err);
   PFF_LAUNCH("mm_count");
   int total = 0;
@@ -816,6 +994,7 @@ void spgemm(const Bsr& X, const Bsr& Y, Bsr& C, int* err, cudaStream_t s) {
   C.nnzb = total;
   C.col = dalloc<int>(total);
   C.val = dalloc<double>((size_t)total * C.br * C.bc);
+  count_launch();
   k_mm_fill<<<g, 128, 0, s>>>(X.nrows, X.br, X.bc, Y.bc, X.rowptr, X.col, X.val, Y.rowptr, Y.col,
                               Y.val, C.rowptr, C.col, C.val);
   PFF_LAUNCH("mm_fill");
@@ -833,15 +1012,19 @@ void transpose(const Bsr& P, Bsr& R, cudaStream_t s) {
   int* cursor = dalloc<int>(R.nrows + 1);
   PFF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (R.nrows + 1), s));
   PFF_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (R.nrows + 1), s));
+  count_launch();
   k_T_count<<<grid_for(P.nrows, 256), 256, 0, s>>>(P.nrows, P.rowptr, P.col, cnt);
   int total = 0;
   exclusive_scan_int(cnt, R.rowptr, R.nrows, &total, s);
   R.col = dalloc<int>(total);
   int* src = dalloc<int>(total);
+  count_launch();
   k_T_fill<<<grid_for(P.nrows, 256), 256, 0, s>>>(P.nrows, P.rowptr, P.col, R.rowptr, cursor,
                                                   R.col, src);
+  count_launch();
   k_sort_segments<<<grid_for(R.nrows, 128), 128, 0, s>>>(R.nrows, R.rowptr, R.col, src);
   R.val = dalloc<double>((size_t)total * R.br * R.bc);
+  count_launch();
   k_T_vals<<<grid_for(total, 256), 256, 0, s>>>(total, P.br, P.bc, src, P.val, R.val);
   PFF_LAUNCH("transpose");
   PFF_CUDA(cudaStreamSynchronize(s));
@@ -868,6 +1051,7 @@ void copy_bsr(const Bsr& A, Bsr& C, cudaStream_t s) {
 void make_float(Bsr& A, cudaStream_t s) {
   const int64_t nv = A.nnzb * A.br * A.bc;
   A.valf = dalloc<float>(nv);
+  count_launch();
   k_to_float<<<grid_for(nv, 256), 256, 0, s>>>(nv, A.val, A.valf);
   PFF_LAUNCH("to_float");
 }
@@ -910,6 +1094,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
   amg.release();
   amg.mixed = prm.mixed;
   amg.cheb_degree = prm.cheb_degree;
+  amg.cheb_ratio = prm.cheb_ratio;
   SetupScratch sc;
   sc.err = dalloc<int>(4);
   PFF_CUDA(cudaMallocHost(&sc.h_err, sizeof(int) * 4));
@@ -923,6 +1108,13 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
   int nb = A.nrows, br = A.br;
   double* B = dalloc<double>((size_t)nb * br * nns);
   PFF_CUDA(cudaMemcpyAsync(B, Bin, sizeof(double) * (size_t)nb * br * nns, cudaMemcpyDeviceToDevice, s));
+  const int cd = prm.coord_dim;
+  double* X = nullptr;   // node coordinates of the current level (distance strength)
+  if (prm.coords && cd > 0) {
+    X = dalloc<double>((size_t)nb * cd);
+    PFF_CUDA(cudaMemcpyAsync(X, prm.coords, sizeof(double) * (size_t)nb * cd,
+                             cudaMemcpyDeviceToDevice, s));
+  }
 
   for (int level = 0;; ++level) {
     const int n = nb * br;
@@ -933,11 +1125,14 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
       double* Dm = dalloc<double>((size_t)n * n);
       amg.cinv = dalloc<double>((size_t)n * n);
       PFF_CUDA(cudaMemsetAsync(Dm, 0, sizeof(double) * (size_t)n * n, s));
+      count_launch();
       k_densify<<<grid_for(nb, 128), 128, 0, s>>>(nb, br, A.rowptr, A.col, A.val, Dm, n);
+      count_launch();
       k_gauss_jordan<<<1, 256, 0, s>>>(n, Dm, amg.cinv, sc.err);
       PFF_LAUNCH("coarse inverse");
       if (amg.mixed) {
         amg.cinvf = dalloc<float>((size_t)n * n);
+        count_launch();
         k_to_float<<<grid_for((int64_t)n * n, 256), 256, 0, s>>>((int64_t)n * n, amg.cinv, amg.cinvf);
       }
       amg.cx = dalloc<double>(n);
@@ -952,13 +1147,27 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     L.n = n;
     L.dinv = dalloc<double>(n);
     double* dnorm = dalloc<double>(nb);
+    count_launch();
     k_diag<<<grid_for(nb, 256), 256, 0, s>>>(nb, br, A.rowptr, A.col, A.val, dnorm, L.dinv, sc.err);
     // strength
     uint8_t* s0 = dalloc<uint8_t>(A.nnzb);
     uint8_t* strong = dalloc<uint8_t>(A.nnzb);
     double* snorm = dalloc<double>(A.nnzb);
-    k_strength<<<grid_for(nb, 256), 256, 0, s>>>(nb, br, A.rowptr, A.col, A.val, dnorm,
-                                                 prm.theta * prm.theta, s0, snorm);
+    if (X) {
+      double* wmax = dalloc<double>(nb);
+      count_launch(2);
+      k_dist_wmax<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, X, cd, wmax);
+      k_strength_dist<<<grid_for(nb, 256), 256, 0, s>>>(nb, br, A.rowptr, A.col, A.val, dnorm, X, cd,
+                                                        wmax, prm.theta * prm.theta,
+                                                        prm.mdrop * prm.mdrop, s0, snorm);
+      PFF_CUDA(cudaStreamSynchronize(s));
+      dfree(wmax);
+    } else {
+      count_launch();
+      k_strength<<<grid_for(nb, 256), 256, 0, s>>>(nb, br, A.rowptr, A.col, A.val, dnorm,
+                                                   prm.theta * prm.theta, s0, snorm);
+    }
+    count_launch();
     k_symmetrize<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, s0, strong);
     PFF_LAUNCH("strength");
     // MIS(2)
@@ -968,12 +1177,16 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     unsigned long long* M2 = dalloc<unsigned long long>(nb);
     int* und = dalloc<int>(1);
     int* h_und = sc.h_err + 1;
+    count_launch();
     k_mis_init<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, strong, state, iso);
     int rounds = 0;
     for (;; ++rounds) {
       PFF_CUDA(cudaMemsetAsync(und, 0, sizeof(int), s));
+      count_launch();
       k_mis_max1<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, strong, state, M1);
+      count_launch();
       k_mis_max2<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, strong, M1, M2);
+      count_launch();
       k_mis_decide<<<grid_for(nb, 256), 256, 0, s>>>(nb, state, M2, und);
       PFF_LAUNCH("mis");
       PFF_CUDA(cudaMemcpyAsync(h_und, und, sizeof(int), cudaMemcpyDeviceToHost, s));
@@ -984,13 +1197,16 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     // aggregates
     int* flag = dalloc<int>(nb + 1);
     int* rootid = dalloc<int>(nb + 1);
+    count_launch();
     k_root_flags<<<grid_for(nb, 256), 256, 0, s>>>(nb, state, flag);
     int nagg = 0;
     exclusive_scan_int(flag, rootid, nb, &nagg, s);
     int* agg1 = dalloc<int>(nb);
     int* agg = dalloc<int>(nb);
+    count_launch();
     k_agg_pass1<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, strong, snorm, state, iso,
                                                   rootid, agg1);
+    count_launch();
     k_agg_pass2<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, strong, snorm, agg1, agg);
     PFF_LAUNCH("aggregate");
     if (nagg == 0 || (int64_t)nagg * nns > (int64_t)(0.9 * n) || level >= prm.max_levels) {
@@ -1005,6 +1221,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
       if (amg.mixed) {
         make_float(L.A, s);
         L.dinvf = dalloc<float>(n);
+        count_launch();
         k_to_float<<<grid_for(n, 256), 256, 0, s>>>(n, L.dinv, L.dinvf);
       }
       PFF_CUDA(cudaStreamSynchronize(s));
@@ -1031,18 +1248,30 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     int* members = dalloc<int>(nb);
     PFF_CUDA(cudaMemsetAsync(cnt, 0, sizeof(int) * (nagg + 1), s));
     PFF_CUDA(cudaMemsetAsync(cursor, 0, sizeof(int) * (nagg + 1), s));
+    count_launch();
     k_count_members<<<grid_for(nb, 256), 256, 0, s>>>(nb, agg, cnt);
     int nmem = 0;
     exclusive_scan_int(cnt, off, nagg, &nmem, s);
+    count_launch();
     k_fill_members<<<grid_for(nb, 256), 256, 0, s>>>(nb, agg, off, cursor, members);
+    count_launch();
     k_sort_segments<<<grid_for(nagg, 128), 128, 0, s>>>(nagg, off, members, nullptr);
     // tentative prolongator + coarse near-null space
     double* Qn = dalloc<double>((size_t)nb * br * nns);
     double* Bc = dalloc<double>((size_t)nagg * nns * nns);
+    count_launch();
     k_zero_rows<<<grid_for(nb, 256), 256, 0, s>>>(nb, br * nns, agg, Qn);
+    count_launch();
     k_tentative<<<grid_for(nagg, 64), 64, 0, s>>>(nagg, br, nns, off, members, B, (int64_t)nb * br,
                                                   Qn, Bc, (int64_t)nagg * nns);
     PFF_LAUNCH("tentative");
+    double* Xc = nullptr;
+    if (X) {
+      Xc = dalloc<double>((size_t)nagg * cd);
+      count_launch();
+      k_centroids<<<grid_for(nagg, 128), 128, 0, s>>>(nagg, off, members, X, cd, Xc);
+      PFF_LAUNCH("centroids");
+    }
     // smoothed prolongator
     L.lmax = estimate_lmax(L.A, L.dinv, s, partials, sc.red, sc.h_red);
     const double omega = 4.0 / (3.0 * L.lmax);
@@ -1053,14 +1282,16 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     P.bc = nns;
     P.rowptr = dalloc<int>(nb + 1);
     int* pc = dalloc<int>(nb + 1);
-    k_P_count<<<grid_for(nb, 128), 128, 0, s>>>(nb, A.rowptr, A.col, agg, pc, sc.err);
+    count_launch();
+    k_P_count<<<grid_for(nb, 128), 128, 0, s>>>(nb, A.rowptr, A.col, strong, agg, pc, sc.err);
     int pnnz = 0;
     exclusive_scan_int(pc, P.rowptr, nb, &pnnz, s);
     P.nnzb = pnnz;
     P.col = dalloc<int>(pnnz);
     P.val = dalloc<double>((size_t)pnnz * br * nns);
-    k_P_fill<<<grid_for(nb, 128), 128, 0, s>>>(nb, br, nns, A.rowptr, A.col, A.val, agg, Qn, L.dinv,
-                                               omega, P.rowptr, P.col, P.val);
+    count_launch();
+    k_P_fill<<<grid_for(nb, 128), 128, 0, s>>>(nb, br, nns, A.rowptr, A.col, A.val, strong, agg, Qn,
+                                               L.dinv, omega, P.rowptr, P.col, P.val);
     PFF_LAUNCH("P");
     check_err(sc, s, "prolongator");
     transpose(P, L.R, s);
@@ -1069,6 +1300,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     spgemm(L.A, P, AP, sc.err, s);
     spgemm(L.R, AP, Ac, sc.err, s);
     check_err(sc, s, "Galerkin product");
+    count_launch();
     k_fix_diag<<<grid_for(Ac.nrows, 128), 128, 0, s>>>(Ac.nrows, Ac.br, Ac.rowptr, Ac.col, Ac.val);
     PFF_LAUNCH("fix_diag");
     AP.release();
@@ -1083,6 +1315,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
       make_float(L.P, s);
       make_float(L.R, s);
       L.dinvf = dalloc<float>(n);
+      count_launch();
       k_to_float<<<grid_for(n, 256), 256, 0, s>>>(n, L.dinv, L.dinvf);
     }
     PFF_CUDA(cudaStreamSynchronize(s));
@@ -1106,25 +1339,38 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     dfree(Qn);
     dfree(pc);
     dfree(B);
+    dfree(X);
     amg.lev.push_back(L);
     // next level
     A = Ac;
     B = Bc;
+    X = Xc;
     nb = Ac.nrows;
     br = Ac.br;
   }
   dfree(B);
+  dfree(X);
   dfree(partials);
   dfree(sc.err);
   dfree(sc.red);
   cudaFreeHost(sc.h_err);
   cudaFreeHost(sc.h_red);
   amg.built = 1;
+  if (verbose()) {
+    std::fprintf(stderr, "[pff] AMG (%s): %zu levels + coarse %d\n", amg.mixed ? "fp32" : "fp64",
+                 amg.lev.size(), amg.nc);
+    for (size_t l = 0; l < amg.lev.size(); ++l) {
+      const auto& L = amg.lev[l];
+      std::fprintf(stderr, "[pff]   level %zu: rows %d (block %d) nnzb %lld lmax %.4g%s\n", l,
+                   L.A.nrows, L.A.br, (long long)L.A.nnzb, L.lmax, L.terminal ? " terminal" : "");
+    }
+  }
 }
 
 void amg_vcycle(Amg& amg, const double* r, double* z, cudaStream_t s) {
   if (amg.lev.empty()) {
     // whole problem is the coarse level
+    ProfScope ps("coarse_solve", 8.0 * amg.nc * (amg.nc + 2.0), s);
     k_dense_mv<double><<<grid_for(amg.nc, 8), 256, 0, s>>>(amg.nc, amg.cinv, r, z);
     PFF_LAUNCH("coarse only");
     return;
@@ -1134,8 +1380,12 @@ void amg_vcycle(Amg& amg, const double* r, double* z, cudaStream_t s) {
   if (amg.mixed) {
     float* b = reinterpret_cast<float*>(L0.b);
     float* x = reinterpret_cast<float*>(L0.x);
-    k_convert<double, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, b);
+    {
+      ProfScope ps("convert", 12.0 * n, s);
+      k_convert<double, float><<<grid_for(n, 256), 256, 0, s>>>(n, r, b);
+    }
     vcycle_level<float>(amg, 0, b, x, s);
+    ProfScope ps("convert", 12.0 * n, s);
     k_convert<float, double><<<grid_for(n, 256), 256, 0, s>>>(n, x, z);
   } else {
     PFF_CUDA(cudaMemcpyAsync(L0.b, r, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));

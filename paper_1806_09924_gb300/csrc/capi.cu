@@ -94,8 +94,9 @@ void release(pff_problem* P) {
   using pff::dfree;
   for (int a = 0; a < 3; ++a) dfree(P->X[a]);
   double* dbl[] = {P->u, P->phi, P->phi_old, P->phi_prev, P->phit, P->mass, P->S, P->Sinv,
+                   P->Sw, P->Sinvw,
                    P->indicator, P->d_scalars, P->partials, P->Kuu, P->Kpu, P->Kpp, P->F,
-                   P->Ft, P->dU, P->dUA, P->ut, P->phit_trial, P->Ftrial, P->Bu, P->Bp,
+                   P->Ft, P->dU, P->dUA, P->ut, P->phit_trial, P->Ftrial, P->Bu, P->Bp, P->xyz,
                    P->V, P->Z, P->w, P->h, P->tmp};
   for (double* p : dbl) dfree(p);
   dfree(P->active);
@@ -159,7 +160,7 @@ void pff_default_options(pff_options* o) {
   if (!o) return;
   std::memset(o, 0, sizeof(*o));
   o->precision = PFF_PREC_FP64;
-  o->c = 1.0;
+  o->c = 0.1;
   o->tol_newton = 1e-10;
   o->tol_step = 1e-9;
   o->tol_linear = 1e-8;
@@ -169,10 +170,13 @@ void pff_default_options(pff_options* o) {
   o->krylov_restart = 40;
   o->max_krylov = 600;
   o->cheb_degree = 2;
-  o->amg_theta = 0.08;
+  o->amg_theta = 0.25;
   o->amg_coarse_max = 320;
   o->apply_variant = PFF_APPLY_AUTO;
   o->precond = PFF_PC_AMG;
+  o->cheb_ratio = 8.0;
+  o->tol_active = 1e-12;
+  o->atol_newton = 1e-14;
 }
 
 const char* pff_last_error(void) { return pff::g_msg.c_str(); }
@@ -220,6 +224,8 @@ int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_c
     P->mass = dalloc<double>(n);
     P->S = dalloc<double>(N);
     P->Sinv = dalloc<double>(N);
+    P->Sw = dalloc<double>(N);
+    P->Sinvw = dalloc<double>(N);
     P->indicator = dalloc<double>(n);
     P->active = dalloc<uint8_t>(n);
     P->active_prev = dalloc<uint8_t>(n);
@@ -256,6 +262,8 @@ int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_c
     pff::launch_lumped_mass(m, n, P->mass, P->stream);
     P->Bu = dalloc<double>((size_t)n * dim * (dim == 2 ? 3 : 6));
     pff::launch_rigid_modes(m, n, P->Bu, P->stream);
+    P->xyz = dalloc<double>((size_t)n * dim);
+    pff::launch_node_coords(m, n, P->xyz, P->stream);
     pff::build_stencil_bsr_structure(m, n, dim, P->Auu, P->stream);
     pff::build_stencil_bsr_structure(m, n, 1, P->App, P->stream);
     const double E = 1.0, nu = 0.2;
@@ -331,6 +339,22 @@ int pff_set_state(pff_problem* P, const double* u, const double* phi, const doub
   P->steps_done = steps_done;
   refresh_phi_tilde(P);
   sync(P);
+  API_END
+}
+
+int pff_set_state_dev(pff_problem* P, const double* u, const double* phi, const double* phi_old,
+                      const double* phi_prev, int steps_done) {
+  API_BEGIN
+  need(P != nullptr, "problem is NULL");
+  need(steps_done >= 0, "steps_done must be >= 0");
+  const size_t n = (size_t)P->n_nodes;
+  const auto d2d = cudaMemcpyDeviceToDevice;
+  if (u) PFF_CUDA(cudaMemcpyAsync(P->u, u, sizeof(double) * n * P->dim, d2d, P->stream));
+  if (phi) PFF_CUDA(cudaMemcpyAsync(P->phi, phi, sizeof(double) * n, d2d, P->stream));
+  if (phi_old) PFF_CUDA(cudaMemcpyAsync(P->phi_old, phi_old, sizeof(double) * n, d2d, P->stream));
+  if (phi_prev) PFF_CUDA(cudaMemcpyAsync(P->phi_prev, phi_prev, sizeof(double) * n, d2d, P->stream));
+  P->steps_done = steps_done;
+  refresh_phi_tilde(P);
   API_END
 }
 
@@ -487,7 +511,7 @@ int pff_active_set_dev(pff_problem* P, double c, uint8_t* active_dev, double* in
   need(P != nullptr, "problem is NULL");
   need(c > 0 && std::isfinite(c), "c must be > 0");
   pff::compute_residual(P, P->u, P->phi, P->F);
-  pff::compute_active_set(P, c, 1 << 30, false);
+  pff::compute_active_set(P, c, 1e-12, 1 << 30, false);
   if (active_dev)
     PFF_CUDA(cudaMemcpyAsync(active_dev, P->active, P->n_nodes, cudaMemcpyDeviceToDevice, P->stream));
   if (indicator_dev)

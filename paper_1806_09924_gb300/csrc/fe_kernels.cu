@@ -727,8 +727,8 @@ __global__ void __launch_bounds__(BLK) k_apply_matfree(MeshDev m, Material mat, 
 // ------------------------------------------------------------- active set ---
 __global__ void k_active_set(int64_t n, int dim, const double* __restrict__ F,
                              const double* __restrict__ mass, const double* __restrict__ phi,
-                             const double* __restrict__ phi_old, double c, int have_prev,
-                             int lock_after, uint8_t* __restrict__ raw_prev,
+                             const double* __restrict__ phi_old, double c, double tau,
+                             int have_prev, int lock_after, uint8_t* __restrict__ raw_prev,
                              int* __restrict__ toggles, uint8_t* __restrict__ locked,
                              uint8_t* __restrict__ active, double* __restrict__ indicator,
                              int* __restrict__ counters) {
@@ -736,7 +736,7 @@ __global__ void k_active_set(int64_t n, int dim, const double* __restrict__ F,
   bool A = false, changed = false;
   if (i < n) {
     const double ind = F[(int64_t)dim * n + i] / mass[i] + c * (phi[i] - phi_old[i]);
-    const bool raw = ind > 0.0;
+    const bool raw = ind > tau;
     bool lk = false;
     if (have_prev) {
       const int tg = toggles[i] + (raw != (raw_prev[i] != 0));
@@ -756,9 +756,11 @@ __global__ void k_active_set(int64_t n, int dim, const double* __restrict__ F,
   }
   const unsigned na = __ballot_sync(0xffffffffu, A);
   const unsigned nc = __ballot_sync(0xffffffffu, changed);
+  const unsigned nl = __ballot_sync(0xffffffffu, i < n && locked[i]);
   if ((threadIdx.x & 31) == 0) {
     if (na) atomicAdd(&counters[0], __popc(na));
     if (nc) atomicAdd(&counters[1], __popc(nc));
+    if (nl) atomicAdd(&counters[3], __popc(nl));
   }
 }
 
@@ -850,6 +852,15 @@ __global__ void k_rigid_modes(MeshDev m, int64_t n, double* __restrict__ B) {
   }
   for (int k = 0; k < NNS; ++k)
     for (int a = 0; a < D; ++a) B[k * ld + i * D + a] = v[k][a];
+}
+
+template <int D>
+__global__ void k_node_coords(MeshDev m, int64_t n, double* __restrict__ xyz) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  for (int l = 0; l < D; ++l) xyz[i * D + l] = m.X[l][idx[l]];
 }
 
 // -------------------------------------------------------------- functionals --
@@ -994,32 +1005,44 @@ __global__ void k_cod(MeshDev m, const CodColumn* __restrict__ cols, const doubl
     }                      \
   } while (0)
 
+namespace {
+constexpr double B8 = 8.0;
+inline double NSd(int d) { return d == 2 ? 9.0 : 27.0; }
+}  // namespace
+
 void launch_phi_tilde(const MeshDev& m, int64_t n, int steps_done, const double* phi_old,
                       const double* phi_prev, double* phit, cudaStream_t s) {
-  k_phi_tilde<<<grid_for(n, 256), 256, 0, s>>>(n, steps_done == 0, phi_old, phi_prev, phit);
+  ProfScope ps("phi_tilde", 3.0 * B8 * n, s);
+  // extrapolation needs two computed time levels: the initial crack field is not one
+  k_phi_tilde<<<grid_for(n, 256), 256, 0, s>>>(n, steps_done <= 1, phi_old, phi_prev, phit);
   PFF_LAUNCH("phi_tilde");
 }
 
 void launch_lumped_mass(const MeshDev& m, int64_t n, double* mass, cudaStream_t s) {
   Material dummy{1, 0, 1, 0, 1, 0, 0, 0};
+  ProfScope ps("lumped_mass", B8 * n, s);
   DISPATCH(m.dim, (k_mass_and_sphi<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, dummy, n, mass, nullptr)));
   PFF_LAUNCH("lumped_mass");
 }
 
 void launch_residual(const MeshDev& m, const Material& mat, int64_t n, const double* u,
                      const double* phi, const double* phit, double* F, cudaStream_t s) {
+  // reads u, phi, phi~; writes F
+  ProfScope ps("residual", B8 * n * (2.0 * m.dim + 3.0), s);
   DISPATCH(m.dim, (k_residual<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, u, phi, phit, F)));
   PFF_LAUNCH("residual");
 }
 
 void launch_assemble_uu(const MeshDev& m, const Material& mat, int64_t n, const double* phit,
                         double* Kuu, cudaStream_t s) {
+  ProfScope ps("assemble_uu", B8 * n * (1.0 + NSd(m.dim) * m.dim * m.dim), s);
   DISPATCH(m.dim, (k_assemble_uu<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, phit, Kuu)));
   PFF_LAUNCH("assemble_uu");
 }
 
 void launch_assemble_phi(const MeshDev& m, const Material& mat, int64_t n, const double* u,
                          const double* phi, double* Kpu, double* Kpp, cudaStream_t s) {
+  ProfScope ps("assemble_phi", B8 * n * ((m.dim + 1.0) + NSd(m.dim) * (m.dim + 1.0)), s);
   DISPATCH(m.dim,
            (k_assemble_phi<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, u, phi, Kpu, Kpp)));
   PFF_LAUNCH("assemble_phi");
@@ -1028,6 +1051,7 @@ void launch_assemble_phi(const MeshDev& m, const Material& mat, int64_t n, const
 void launch_scaling(const MeshDev& m, const Material& mat, int64_t n, const double* Kuu,
                     double* S, double* Sinv, cudaStream_t s) {
   const int d = m.dim;
+  ProfScope ps("scaling", B8 * n * (3.0 * d + 3.0), s, 3);
   DISPATCH(d, (k_scaling_u<D><<<grid_for(n, 256), 256, 0, s>>>(n, Kuu, S, Sinv)));
   DISPATCH(d, (k_mass_and_sphi<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, nullptr,
                                                                     S + (int64_t)d * n)));
@@ -1038,14 +1062,19 @@ void launch_scaling(const MeshDev& m, const Material& mat, int64_t n, const doub
 void launch_reduce_phi(const MeshDev& m, int64_t n, const uint8_t* active, const double* phi,
                        const double* phi_old, const double* F, double* Ft, double* dUA,
                        double* Kpu, double* Kpp, cudaStream_t s) {
+  // reads F, phi, phi_old, active, Kpp; writes Ft, dUA, Kpp (masked)
+  ProfScope ps("reduce_phi", n * (B8 * (3.0 * (m.dim + 1) + 2.0 + 2.0 * NSd(m.dim)) + 1.0), s);
   DISPATCH(m.dim, (k_reduce_phi<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, active, phi, phi_old, F,
                                                                      Ft, dUA, Kpu, Kpp)));
   PFF_LAUNCH("reduce_phi");
 }
 
-void launch_apply_assembled(const MeshDev& m, int64_t n, const double* Kuu, const double* Kpu,
+void launch_apply_assembled(const MeshDev& m, const int64_t n, const double* Kuu, const double* Kpu,
                             const double* Kpp, const double* x, double* y, const double* Sinv,
                             cudaStream_t s) {
+  // stencils (d^2 + d + 1 values per slot), x, y, Sinv
+  const double per = NSd(m.dim) * (m.dim * m.dim + m.dim + 1.0) + (m.dim + 1.0) * (Sinv ? 3.0 : 2.0);
+  ProfScope ps("apply_assembled", B8 * n * per, s);
   DISPATCH(m.dim, (k_apply_assembled<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, Kuu, Kpu, Kpp, x, y,
                                                                          Sinv)));
   PFF_LAUNCH("apply_assembled");
@@ -1054,18 +1083,21 @@ void launch_apply_assembled(const MeshDev& m, int64_t n, const double* Kuu, cons
 void launch_apply_matfree(const MeshDev& m, const Material& mat, int64_t n, const double* u,
                           const double* phi, const double* phit, const uint8_t* active,
                           const double* x, double* y, const double* Sinv, cudaStream_t s) {
+  // u, phi, phi~, active, x, y, Sinv
+  const double per = B8 * (m.dim + 2.0 + (m.dim + 1.0) * (Sinv ? 3.0 : 2.0)) + 1.0;
+  ProfScope ps("apply_matfree", n * per, s);
   DISPATCH(m.dim, (k_apply_matfree<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, u, phi, phit,
                                                                        active, x, y, Sinv)));
   PFF_LAUNCH("apply_matfree");
 }
 
 void launch_active_set(int64_t n, int dim, const double* F, const double* mass, const double* phi,
-                       const double* phi_old, double c, int have_prev, int lock_after,
+                       const double* phi_old, double c, double tau, int have_prev, int lock_after,
                        uint8_t* raw_prev, int* toggles, uint8_t* locked, uint8_t* active,
-                       uint8_t* /*active_prev*/, double* indicator, int* counters,
-                       cudaStream_t s) {
-  PFF_CUDA(cudaMemsetAsync(counters, 0, 2 * sizeof(int), s));
-  k_active_set<<<grid_for(n, 256), 256, 0, s>>>(n, dim, F, mass, phi, phi_old, c, have_prev,
+                       double* indicator, int* counters, cudaStream_t s) {
+  PFF_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(int), s));
+  ProfScope ps("active_set", n * (B8 * (indicator ? 5.0 : 4.0) + 14.0), s);
+  k_active_set<<<grid_for(n, 256), 256, 0, s>>>(n, dim, F, mass, phi, phi_old, c, tau, have_prev,
                                                 lock_after, raw_prev, toggles, locked, active,
                                                 indicator, counters);
   PFF_LAUNCH("active_set");
@@ -1073,6 +1105,7 @@ void launch_active_set(int64_t n, int dim, const double* F, const double* mass, 
 
 void launch_scaled_reduced(const MeshDev& m, int64_t n, const double* F, const double* Sinv,
                            const uint8_t* active, double* rho, cudaStream_t s) {
+  ProfScope ps("scaled_reduced", n * (B8 * 3.0 * (m.dim + 1.0) + 1.0), s);
   DISPATCH(m.dim, (k_scaled_reduced<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, F, Sinv, active, rho)));
   PFF_LAUNCH("scaled_reduced");
 }
@@ -1082,6 +1115,7 @@ void build_stencil_bsr_structure(const MeshDev& m, int64_t n, int b, Bsr& A, cud
   A.br = A.bc = b;
   A.rowptr = dalloc<int>(n + 1);
   int* cnt = dalloc<int>(n + 1);
+  count_launch();
   DISPATCH(m.dim, (k_stencil_count<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, cnt)));
   PFF_LAUNCH("stencil_count");
   int total = 0;
@@ -1089,6 +1123,7 @@ void build_stencil_bsr_structure(const MeshDev& m, int64_t n, int b, Bsr& A, cud
   A.nnzb = total;
   A.col = dalloc<int>(total);
   A.val = dalloc<double>((size_t)total * b * b);
+  count_launch();
   DISPATCH(m.dim, (k_stencil_cols<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, A.rowptr, A.col)));
   PFF_LAUNCH("stencil_cols");
   PFF_CUDA(cudaStreamSynchronize(s));
@@ -1097,18 +1132,27 @@ void build_stencil_bsr_structure(const MeshDev& m, int64_t n, int b, Bsr& A, cud
 
 void launch_stencil_to_bsr(const MeshDev& m, int64_t n, int b, const double* K, const Bsr& A,
                            cudaStream_t s) {
+  ProfScope ps("stencil_to_bsr", 2.0 * B8 * A.nnzb * b * b + 4.0 * n, s);
   DISPATCH(m.dim, (k_stencil_vals<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, b, K, A.rowptr, A.val)));
   PFF_LAUNCH("stencil_vals");
 }
 
 void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s) {
+  count_launch();
   DISPATCH(m.dim, (k_rigid_modes<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, B)));
   PFF_LAUNCH("rigid_modes");
+}
+
+void launch_node_coords(const MeshDev& m, int64_t n, double* xyz, cudaStream_t s) {
+  count_launch();
+  DISPATCH(m.dim, (k_node_coords<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, xyz)));
+  PFF_LAUNCH("node_coords");
 }
 
 void tcv_dev(const MeshDev& m, int64_t n_cells, const double* u, const double* phi, double* out,
              double* partials, cudaStream_t s) {
   const int nb = (int)std::min<int64_t>(RED_PARTIALS, (n_cells + 255) / 256);
+  ProfScope ps("tcv", B8 * n_cells * (m.dim + 1.0), s, 2);
   DISPATCH(m.dim, (k_tcv<D><<<nb, 256, 0, s>>>(m, n_cells, u, phi, partials)));
   k_sum_partials<<<1, 256, 0, s>>>(partials, nb, out);
   PFF_LAUNCH("tcv");
@@ -1117,6 +1161,7 @@ void tcv_dev(const MeshDev& m, int64_t n_cells, const double* u, const double* p
 void cod_dev(const MeshDev& m, const CodColumn* cols, int ncols, const double* u, const double* phi,
              double* out, int /*npts*/, cudaStream_t s) {
   if (ncols == 0) return;
+  ProfScope ps("cod", 0.0, s);
   DISPATCH(m.dim, (k_cod<D><<<ncols, 128, 0, s>>>(m, cols, u, phi, out)));
   PFF_LAUNCH("cod");
 }

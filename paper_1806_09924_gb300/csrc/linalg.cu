@@ -175,6 +175,7 @@ __global__ void k_bsr_spmv(int nrows, int br, int bc, const int* __restrict__ ro
 void dot_dev(const double* x, const double* y, int64_t n, double* out, double* partials,
              cudaStream_t s) {
   const int g = red_grid(n);
+  ProfScope ps("dot", (x == y ? 8.0 : 16.0) * n, s, 2);
   k_dot<<<g, RB, 0, s>>>(x, y, n, partials);
   k_final<<<1, RB, 0, s>>>(partials, g, 0, 0, out);
   PFF_LAUNCH("dot");
@@ -182,6 +183,7 @@ void dot_dev(const double* x, const double* y, int64_t n, double* out, double* p
 
 void nrm_inf_dev(const double* x, int64_t n, double* out, double* partials, cudaStream_t s) {
   const int g = red_grid(n);
+  ProfScope ps("nrm_inf", 8.0 * n, s, 2);
   k_nrm_inf<<<g, RB, 0, s>>>(x, n, partials);
   k_final<<<1, RB, 0, s>>>(partials, g, 0, 1, out);
   PFF_LAUNCH("nrm_inf");
@@ -190,6 +192,7 @@ void nrm_inf_dev(const double* x, int64_t n, double* out, double* partials, cuda
 void multidot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* out,
                   double* partials, cudaStream_t s) {
   const int g = std::min(red_grid(n), 256);
+  ProfScope ps("multidot", 8.0 * n * (nv + 1.0), s, (nv + 7) / 8 + 1);
   int k0 = 0;
   while (k0 < nv) {
     const int k = std::min(8, nv - k0);
@@ -211,6 +214,7 @@ void multidot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t 
 
 void multi_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n,
                     double sign, cudaStream_t s) {
+  ProfScope ps("multi_axpy", 8.0 * n * (nv + 2.0), s);
   k_multi_axpy<<<grid_for(n, 256), 256, 0, s>>>(V, ld, nv, h, w, n, sign);
   PFF_LAUNCH("multi_axpy");
 }
@@ -219,6 +223,7 @@ void exclusive_scan_int(const int* in, int* out, int n, int* total_host, cudaStr
   const int nb = std::max(1, (n + SB - 1) / SB);
   int* bsum = dalloc<int>(nb + 1);
   int* tot = bsum + nb;
+  count_launch(3);
   k_scan_block<<<nb, SB, 0, s>>>(in, out, n, bsum);
   k_scan_sums<<<1, 32, 0, s>>>(bsum, nb, tot);
   k_scan_add<<<nb, SB, 0, s>>>(out, n, bsum, tot);
@@ -231,9 +236,15 @@ void exclusive_scan_int(const int* in, int* out, int n, int* total_host, cudaStr
   dfree(bsum);
 }
 
+double bsr_bytes(const Bsr& A, int elem, bool beta) {
+  return (double)A.nnzb * (A.br * A.bc * (double)elem + 4.0) + 4.0 * (A.nrows + 1.0) +
+         (double)elem * ((double)A.ncols * A.bc + (double)A.nrows * A.br * (beta ? 2.0 : 1.0));
+}
+
 void bsr_spmv(const Bsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s) {
   const int64_t rows = (int64_t)A.nrows * A.br;
   if (rows == 0) return;
+  ProfScope ps("spmv_f64", bsr_bytes(A, 8, beta != 0.0), s);
   k_bsr_spmv<double><<<grid_for(rows, 256), 256, 0, s>>>(A.nrows, A.br, A.bc, A.rowptr, A.col,
                                                          A.val, x, y, alpha, beta);
   PFF_LAUNCH("bsr_spmv");
@@ -242,6 +253,7 @@ void bsr_spmv(const Bsr& A, const double* x, double* y, double alpha, double bet
 void bsr_spmv_f(const Bsr& A, const float* x, float* y, float alpha, float beta, cudaStream_t s) {
   const int64_t rows = (int64_t)A.nrows * A.br;
   if (rows == 0) return;
+  ProfScope ps("spmv_f32", bsr_bytes(A, 4, beta != 0.0f), s);
   k_bsr_spmv<float><<<grid_for(rows, 256), 256, 0, s>>>(A.nrows, A.br, A.bc, A.rowptr, A.col,
                                                         A.valf, x, y, alpha, beta);
   PFF_LAUNCH("bsr_spmv_f");

@@ -36,6 +36,27 @@ void check_cuda(cudaError_t e, const char* what);
 #define PFF_CUDA(x) ::pff::check_cuda((x), #x)
 #define PFF_LAUNCH(what) ::pff::check_cuda(cudaGetLastError(), what)
 
+// ------------------------------------------------------- launch accounting --
+// Every kernel launch is counted; when profiling is enabled, the launches of a
+// ProfScope are also timed with a CUDA event pair and credited with their
+// algorithmic bytes (each input / output array moved once).
+void count_launch(int k = 1);
+// diagnostics on stderr when the environment variable PFF_VERBOSE is set
+bool verbose();
+class ProfScope {
+ public:
+  ProfScope(const char* name, double bytes, cudaStream_t s, int kernels = 1);
+  ~ProfScope();
+  ProfScope(const ProfScope&) = delete;
+  ProfScope& operator=(const ProfScope&) = delete;
+
+ private:
+  const char* name_;
+  double bytes_;
+  cudaStream_t s_;
+  void* a_;
+};
+
 // ------------------------------------------------------------ device memory --
 void* dmalloc(size_t bytes);
 void dfree(void* p);
@@ -92,6 +113,7 @@ struct Amg {
   double *cx = nullptr, *cb = nullptr;
   bool mixed = false;
   int cheb_degree = 2;
+  double cheb_ratio = 30.0;
   int built = 0;
   void release();
 };
@@ -100,8 +122,14 @@ struct AmgParams {
   double theta = 0.08;
   int coarse_max = 320;
   int cheb_degree = 2;
+  double cheb_ratio = 30.0;
   bool mixed = false;
   int max_levels = 20;
+  // fine-level node coordinates (n x coord_dim, device); when given, strength
+  // is measured on the distance Laplacian (theta) with a matrix drop (mdrop)
+  const double* coords = nullptr;
+  int coord_dim = 0;
+  double mdrop = 1e-3;
 };
 
 // Build a hierarchy for the block matrix A (FP64 values, block size br) with
@@ -164,12 +192,15 @@ void launch_apply_assembled(const MeshDev& m, int64_t n, const double* Kuu, cons
 void launch_apply_matfree(const MeshDev& m, const Material& mat, int64_t n, const double* u,
                           const double* phi, const double* phit, const uint8_t* active,
                           const double* x, double* y, const double* Sinv, cudaStream_t s);
-// Active set (step 2 of the Section 3 algorithm) with cycle locking.
-// counters[0] = |A|, counters[1] = changes vs. previous A (if have_prev)
+// Active set (step 2 of the Section 3 algorithm) with cycle locking:
+// A = {indicator > tau} plus locked indices.  counters[0] = |A|, counters[1] =
+// changes vs. the previous A (if have_prev), counters[3] = locked indices.
 void launch_active_set(int64_t n, int dim, const double* F, const double* mass, const double* phi,
-                       const double* phi_old, double c, int have_prev, int lock_after,
+                       const double* phi_old, double c, double tau, int have_prev, int lock_after,
                        uint8_t* raw_prev, int* toggles, uint8_t* locked, uint8_t* active,
-                       uint8_t* active_prev, double* indicator, int* counters, cudaStream_t s);
+                       double* indicator, int* counters, cudaStream_t s);
+
+
 // rho = Sinv .* F on free rows (not Dirichlet, not active), 0 elsewhere
 void launch_scaled_reduced(const MeshDev& m, int64_t n, const double* F, const double* Sinv,
                            const uint8_t* active, double* rho, cudaStream_t s);
@@ -179,6 +210,8 @@ void launch_stencil_to_bsr(const MeshDev& m, int64_t n, int b, const double* K, 
 void build_stencil_bsr_structure(const MeshDev& m, int64_t n, int b, Bsr& A, cudaStream_t s);
 // rigid-body (u) near-null space, column-major n*dim x nns
 void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s);
+// node coordinates [n][dim]
+void launch_node_coords(const MeshDev& m, int64_t n, double* xyz, cudaStream_t s);
 // TCV partial sums (deterministic) and COD line integrals
 void tcv_dev(const MeshDev& m, int64_t n_cells, const double* u, const double* phi, double* out,
              double* partials, cudaStream_t s);
@@ -207,6 +240,8 @@ struct pff_problem {
   double *u = nullptr, *phi = nullptr, *phi_old = nullptr, *phi_prev = nullptr, *phit = nullptr;
   int steps_done = 0;
   double *mass = nullptr, *S = nullptr, *Sinv = nullptr;
+  double *Sw = nullptr, *Sinvw = nullptr;           // block-balanced scaling of a Newton solve
+  const double *op_S = nullptr, *op_Sinv = nullptr;  // scaling FGMRES uses (null: S, Sinv)
   uint8_t *active = nullptr, *active_prev = nullptr, *raw_prev = nullptr, *locked = nullptr;
   int* toggles = nullptr;
   double* indicator = nullptr;
@@ -226,6 +261,7 @@ struct pff_problem {
 
   // preconditioner
   pff::Bsr Auu, App;
+  double* xyz = nullptr;  // node coordinates [n][dim] (AMG distance strength)
   double* Bu = nullptr;   // rigid-body modes
   double* Bp = nullptr;   // constants
   pff::Amg amg_u, amg_p;
@@ -265,7 +301,7 @@ void begin_loading_step(pff_problem* P, double p);
 int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep);
 void end_loading_step(pff_problem* P);
 void compute_residual(pff_problem* P, const double* u, const double* phi, double* F);
-void compute_active_set(pff_problem* P, double c, int lock_after, bool track);
+void compute_active_set(pff_problem* P, double c_rel, double tol_active, int lock_after, bool track);
 void assemble_all(pff_problem* P);
 void precond_setup(pff_problem* P, const pff_options& o);
 void precond_apply(pff_problem* P, const double* r, double* z);

@@ -1,0 +1,154 @@
+// Opt-in per-kernel timing with CUDA events and a process-wide launch counter.
+//
+// When enabled (pff_profile_enable), every instrumented launcher records an
+// event pair on the stream it launches on, together with the algorithmic
+// bytes of that launch (the bytes the operation must move at minimum: each
+// input and output array once).  pff_profile_report synchronizes, resolves the
+// pending events and returns per-kernel totals as JSON.  The launch counter
+// counts every kernel the library launches, instrumented or not.
+#include <algorithm>
+#include <atomic>
+#include <cstdlib>
+#include <cstring>
+#include <cstdio>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "pff_internal.h"
+
+namespace pff {
+
+std::atomic<long long> g_launches{0};
+
+namespace {
+
+struct Pending {
+  const char* name;
+  double bytes;
+  cudaEvent_t a, b;
+};
+
+struct Acc {
+  long long count = 0;
+  double ms = 0.0;
+  double bytes = 0.0;
+};
+
+struct Profiler {
+  std::mutex mu;
+  bool on = false;
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> pool;
+  std::map<std::string, Acc> acc;
+
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    cudaEventCreate(&e);
+    return e;
+  }
+
+  // resolve completed records (all of them when `all`, after a device sync)
+  void flush(bool all) {
+    std::vector<Pending> keep;
+    for (auto& p : pending) {
+      if (!all && cudaEventQuery(p.b) != cudaSuccess) {
+        keep.push_back(p);
+        continue;
+      }
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+        Acc& a = acc[p.name];
+        a.count += 1;
+        a.ms += ms;
+        a.bytes += p.bytes;
+      }
+      cudaGetLastError();
+      pool.push_back(p.a);
+      pool.push_back(p.b);
+    }
+    pending.swap(keep);
+  }
+};
+
+Profiler& prof() {
+  static Profiler* p = new Profiler();
+  return *p;
+}
+
+}  // namespace
+
+bool verbose() {
+  static const bool v = std::getenv("PFF_VERBOSE") != nullptr;
+  return v;
+}
+
+void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+ProfScope::ProfScope(const char* name, double bytes, cudaStream_t s, int kernels)
+    : name_(name), bytes_(bytes), s_(s), a_(nullptr) {
+  count_launch(kernels);
+  Profiler& P = prof();
+  if (!P.on) return;
+  std::lock_guard<std::mutex> g(P.mu);
+  if (P.pending.size() > 4096) P.flush(false);
+  a_ = P.get();
+  cudaEventRecord(static_cast<cudaEvent_t>(a_), s_);
+}
+
+ProfScope::~ProfScope() {
+  if (!a_) return;
+  Profiler& P = prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  cudaEvent_t b = P.get();
+  cudaEventRecord(b, s_);
+  P.pending.push_back({name_, bytes_, static_cast<cudaEvent_t>(a_), b});
+}
+
+}  // namespace pff
+
+extern "C" {
+
+int pff_profile_enable(int on) {
+  auto& P = pff::prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  cudaDeviceSynchronize();
+  P.flush(true);
+  P.acc.clear();
+  P.on = on != 0;
+  return PFF_OK;
+}
+
+int pff_profile_report(char* buf, int buflen) {
+  auto& P = pff::prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  cudaDeviceSynchronize();
+  P.flush(true);
+  std::string s = "{";
+  bool first = true;
+  for (auto& kv : P.acc) {
+    char tmp[256];
+    std::snprintf(tmp, sizeof(tmp), "%s\"%s\": {\"count\": %lld, \"ms\": %.6f, \"bytes\": %.0f}",
+                  first ? "" : ", ", kv.first.c_str(), kv.second.count, kv.second.ms,
+                  kv.second.bytes);
+    s += tmp;
+    first = false;
+  }
+  s += "}";
+  if (buf && buflen > 0) {
+    const size_t n = std::min<size_t>(s.size(), (size_t)buflen - 1);
+    std::memcpy(buf, s.data(), n);
+    buf[n] = 0;
+  }
+  return (int)s.size() + 1;
+}
+
+long long pff_launch_count(void) { return pff::g_launches.load(); }
+
+}  // extern "C"

@@ -5,10 +5,11 @@
 //
 // Newton iteration k of a loading step:
 //   1. F = -r(U^k)                                 (residual kernel)
-//   2. A_k = {i : F_phi,i/m_i + c(phi_i - phi_old,i) > 0}, plus indices locked
-//      after `cycle_lock` membership changes      (active-set kernel)
+//   2. A_k = {i : F_phi,i/m_i + c(phi_i - phi_old,i) > tau}, plus indices
+//      locked after `cycle_lock` membership changes (active-set kernel); c and
+//      the printed rule's threshold tau are given in units of G_c/eps
 //   3. stop if k > 0, A_k = A_{k-1}, the scaled reduced residual fell by
-//      tol_newton and the previous step was below tol_step
+//      tol_newton (or below atol_newton) and the previous step was below tol_step
 //   4. assemble M_phi_u, M_phi_phi (M_uu once per loading step), eliminate the
 //      Dirichlet / active rows and columns (active entries get
 //      delta phi = phi_old - phi, moved to the right-hand side)
@@ -20,6 +21,7 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
 
 #include "pff_internal.h"
 
@@ -71,12 +73,38 @@ __global__ void k_lambda(int64_t n, int dim, const double* __restrict__ F,
   if (i < n) out[i] = fabs(F[(int64_t)dim * n + i] / mass[i]);
 }
 
-__global__ void k_count_ties(int64_t n, const double* __restrict__ ind, const double* __restrict__ lam_inf,
-                             double c, int* __restrict__ cnt) {
+__global__ void k_count_ties(int64_t n, const double* __restrict__ ind, double tau,
+                             int* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool tie = i < n && fabs(ind[i]) < 1e-14 * (*lam_inf + c);
+  const bool tie = i < n && fabs(ind[i]) <= tau;
   const unsigned b = __ballot_sync(0xffffffffu, tie);
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(cnt, __popc(b));
+}
+
+void launch_update(cudaStream_t s, int64_t n, int dim, const double* u, const double* phi,
+                   const double* phi_old, const uint8_t* active, const double* dU, double omega,
+                   double* uo, double* po) {
+  ProfScope ps("update", n * (8.0 * (3.0 * dim + 4.0) + 1.0), s);
+  k_update<<<grid_for(n, 256), 256, 0, s>>>(n, dim, u, phi, phi_old, active, dU, omega, uo, po);
+  PFF_LAUNCH("update");
+}
+
+// Sw = S / w_block, Sinvw = w_block * Sinv (w_u on the displacement rows, w_p on the rest)
+__global__ void k_block_weights(int64_t N, int64_t nu, const double* __restrict__ S,
+                                const double* __restrict__ Sinv, double wu, double wp,
+                                double* __restrict__ Sw, double* __restrict__ Sinvw) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  const double w = i < nu ? wu : wp;
+  Sw[i] = S[i] / w;
+  Sinvw[i] = Sinv[i] * w;
+}
+
+void launch_block_weights(cudaStream_t s, int64_t N, int64_t nu, const double* S,
+                          const double* Sinv, double wu, double wp, double* Sw, double* Sinvw) {
+  ProfScope ps("block_weights", 32.0 * N, s);
+  k_block_weights<<<grid_for(N, 256), 256, 0, s>>>(N, nu, S, Sinv, wu, wp, Sw, Sinvw);
+  PFF_LAUNCH("block_weights");
 }
 
 void sync(pff_problem* P) { PFF_CUDA(cudaStreamSynchronize(P->stream)); }
@@ -90,6 +118,7 @@ double fetch(pff_problem* P, const double* d) {
 }  // namespace
 
 void scale_into(const double* s, const double* x, double* y, int64_t n, cudaStream_t st) {
+  ProfScope ps("vec_mul", 24.0 * n, st);
   k_mul<<<grid_for(n, 256), 256, 0, st>>>(n, s, x, y);
   PFF_LAUNCH("scale");
 }
@@ -116,10 +145,11 @@ void compute_residual(pff_problem* P, const double* u, const double* phi, double
   launch_residual(P->mesh(), P->mat, P->n_nodes, u, phi, P->phit, F, P->stream);
 }
 
-void compute_active_set(pff_problem* P, double c, int lock_after, bool track) {
-  launch_active_set(P->n_nodes, P->dim, P->F, P->mass, P->phi, P->phi_old, c, track ? 1 : 0,
-                    lock_after, P->raw_prev, P->toggles, P->locked, P->active, nullptr,
-                    P->indicator, P->counters, P->stream);
+void compute_active_set(pff_problem* P, double c_rel, double tol_active, int lock_after, bool track) {
+  const double scale = P->mat.Gc / P->mat.eps;   // indicator constants in units of G_c/eps
+  launch_active_set(P->n_nodes, P->dim, P->F, P->mass, P->phi, P->phi_old, c_rel * scale,
+                    tol_active * scale, track ? 1 : 0, lock_after, P->raw_prev, P->toggles,
+                    P->locked, P->active, P->indicator, P->counters, P->stream);
 }
 
 void assemble_all(pff_problem* P) {
@@ -152,6 +182,9 @@ void precond_setup(pff_problem* P, const pff_options& o) {
   ap.theta = o.amg_theta;
   ap.coarse_max = o.amg_coarse_max;
   ap.cheb_degree = o.cheb_degree;
+  ap.cheb_ratio = o.cheb_ratio > 1.0 ? o.cheb_ratio : 30.0;
+  ap.coords = P->xyz;
+  ap.coord_dim = P->dim;
   ap.mixed = o.precision == PFF_PREC_MIXED;
   const auto m = P->mesh();
   if (!P->amg_u_valid || P->amg_u.mixed != ap.mixed) {
@@ -166,7 +199,10 @@ void precond_setup(pff_problem* P, const pff_options& o) {
 // z = diag(V_u, V_phi) (S .* r) -- the right preconditioner of the scaled system
 void precond_apply(pff_problem* P, const double* r, double* z) {
   const int64_t N = P->n_dofs, nu = (int64_t)P->dim * P->n_nodes;
-  k_mul<<<grid_for(N, 256), 256, 0, P->stream>>>(N, P->S, r, P->tmp);
+  {
+    ProfScope ps("vec_mul", 24.0 * N, P->stream);
+    k_mul<<<grid_for(N, 256), 256, 0, P->stream>>>(N, P->op_S ? P->op_S : P->S, r, P->tmp);
+  }
   PFF_LAUNCH("precond scale");
   amg_vcycle(P->amg_u, P->tmp, z, P->stream);
   amg_vcycle(P->amg_p, P->tmp + nu, z + nu, P->stream);
@@ -205,7 +241,10 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
   PFF_CUDA(cudaMemcpyAsync(w, b, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
   double beta = beta0;
   while (true) {
-    k_normalize<<<g, 256, 0, s>>>(N, w, P->d_scalars, V);   // d_scalars holds ||r||^2
+    {
+      ProfScope ps("normalize", 16.0 * N, s);
+      k_normalize<<<g, 256, 0, s>>>(N, w, P->d_scalars, V);   // d_scalars holds ||r||^2
+    }
     PFF_LAUNCH("normalize");
     std::fill(gv.begin(), gv.end(), 0.0);
     gv[0] = beta;
@@ -215,7 +254,7 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
       double* vj = V + (int64_t)j * N;
       double* zj = Z + (int64_t)j * N;
       precond(P, o, vj, zj);
-      apply_jacobian(P, P->apply_variant, zj, w, P->Sinv);
+      apply_jacobian(P, P->apply_variant, zj, w, P->op_Sinv ? P->op_Sinv : P->Sinv);
       // CGS2
       multidot_dev(V, N, j + 1, w, N, dh, P->partials, s);
       multi_axpy_dev(V, N, j + 1, dh, w, N, -1.0, s);
@@ -229,7 +268,10 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[(m + 2) + i];
       H[(size_t)(j + 1) * m + j] = hn;
       // V_{j+1} = w / hn  (norm squared already on device)
-      k_normalize<<<g, 256, 0, s>>>(N, w, dh + 2 * (m + 2), V + (int64_t)(j + 1) * N);
+      {
+        ProfScope ps("normalize", 16.0 * N, s);
+        k_normalize<<<g, 256, 0, s>>>(N, w, dh + 2 * (m + 2), V + (int64_t)(j + 1) * N);
+      }
       PFF_LAUNCH("normalize");
       for (int i = 0; i < j; ++i) {
         const double a = H[(size_t)i * m + j], bb = H[(size_t)(i + 1) * m + j];
@@ -270,8 +312,11 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
       return PFF_ERR_NOT_CONVERGED;
     }
     // explicit restart residual r = b - A x
-    apply_jacobian(P, P->apply_variant, x, w, P->Sinv);
-    k_sub<<<g, 256, 0, s>>>(N, b, w, w);
+    apply_jacobian(P, P->apply_variant, x, w, P->op_Sinv ? P->op_Sinv : P->Sinv);
+    {
+      ProfScope ps("vec_sub", 24.0 * N, s);
+      k_sub<<<g, 256, 0, s>>>(N, b, w, w);
+    }
     dot_dev(w, w, N, P->d_scalars, P->partials, s);
     beta = std::sqrt(fetch(P, P->d_scalars));
     if (beta <= target) return PFF_OK;
@@ -309,13 +354,12 @@ static double scaled_norms(pff_problem* P, const double* F, double* l2) {
   return P->h_scalars[0];
 }
 
-static int count_ties(pff_problem* P, double c) {
+// nodes whose active-set indicator is numerically zero (|indicator| <= tau)
+static int count_ties(pff_problem* P, double tau) {
   const int64_t n = P->n_nodes;
-  k_lambda<<<grid_for(n, 256), 256, 0, P->stream>>>(n, P->dim, P->F, P->mass, P->tmp);
-  nrm_inf_dev(P->tmp, n, P->d_scalars, P->partials, P->stream);
+  count_launch();
   PFF_CUDA(cudaMemsetAsync(P->counters + 2, 0, sizeof(int), P->stream));
-  k_count_ties<<<grid_for(n, 256), 256, 0, P->stream>>>(n, P->indicator, P->d_scalars, c,
-                                                        P->counters + 2);
+  k_count_ties<<<grid_for(n, 256), 256, 0, P->stream>>>(n, P->indicator, tau, P->counters + 2);
   PFF_CUDA(cudaMemcpyAsync(P->h_counters + 2, P->counters + 2, sizeof(int), cudaMemcpyDeviceToHost,
                            P->stream));
   sync(P);
@@ -331,8 +375,8 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   pff_step_report& R = P->cur;
   // 1-2. residual and active set
   compute_residual(P, P->u, P->phi, P->F);
-  compute_active_set(P, o.c, o.cycle_lock, P->have_prev);
-  PFF_CUDA(cudaMemcpyAsync(P->h_counters, P->counters, 2 * sizeof(int), cudaMemcpyDeviceToHost, s));
+  compute_active_set(P, o.c, o.tol_active, o.cycle_lock, P->have_prev);
+  PFF_CUDA(cudaMemcpyAsync(P->h_counters, P->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   double rho_l2 = 0.0;
   const double rho_inf = scaled_norms(P, P->F, &rho_l2);
   const int n_active = P->h_counters[0];
@@ -346,14 +390,15 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   R.rho = rho_inf;
   R.active = n_active;
   R.changed = n_changed;
+  R.locked = P->h_counters[3];
   // 3. stopping test
-  const bool done = (P->have_prev && n_changed == 0 && rho_inf <= o.tol_newton * P->rho0 &&
-                     P->last_small) ||
+  const bool done = (P->have_prev && n_changed == 0 &&
+                     rho_inf <= std::max(o.tol_newton * P->rho0, o.atol_newton) && P->last_small) ||
                     P->rho0 == 0.0;
   if (done) {
     R.converged = 1;
     R.newton_its = P->k;
-    R.ties = count_ties(P, o.c);
+    R.ties = count_ties(P, o.tol_active * P->mat.Gc / P->mat.eps);
     PFF_CUDA(cudaMemcpyAsync(P->h_counters, P->counters, sizeof(int), cudaMemcpyDeviceToHost, s));
     R.status = PFF_OK;
     if (rep) *rep = R;
@@ -369,12 +414,31 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   // 4. reduced Jacobian and right-hand side
   assemble_all(P);
   precond_setup(P, o);
-  // 5. linear solve on the scaled system
-  k_mul<<<grid_for(N, 256), 256, 0, s>>>(N, P->Sinv, P->Ft, P->tmp);
-  PFF_LAUNCH("scale rhs");
-  PFF_CUDA(cudaMemcpyAsync(P->Ftrial, P->tmp, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+  // 5. linear solve on the scaled system.  The displacement and phase-field
+  // blocks of S^-1 F~ differ by orders of magnitude (displacements vs. a
+  // dimensionless phase field), so each block's rows are further divided by the
+  // norm of its own right-hand side: the FGMRES tolerance then applies to both
+  // blocks instead of only the larger one.
+  const int64_t nu = (int64_t)dim * n;
+  scale_into(P->Sinv, P->Ft, P->tmp, N, s);
+  dot_dev(P->tmp, P->tmp, nu, P->d_scalars + 4, P->partials, s);
+  dot_dev(P->tmp + nu, P->tmp + nu, n, P->d_scalars + 5, P->partials, s);
+  PFF_CUDA(cudaMemcpyAsync(P->h_scalars + 4, P->d_scalars + 4, 2 * sizeof(double),
+                           cudaMemcpyDeviceToHost, s));
+  sync(P);
+  // a block already at round-off relative to the other is not amplified past 1e6
+  const double bu0 = std::sqrt(P->h_scalars[4]), bp0 = std::sqrt(P->h_scalars[5]);
+  const double floor_b = 1e-6 * std::sqrt(bu0 * bu0 + bp0 * bp0);
+  const double bu = std::max(bu0, floor_b), bp = std::max(bp0, floor_b);
+  const double wu = bu > 0.0 ? 1.0 / bu : 1.0, wp = bp > 0.0 ? 1.0 / bp : 1.0;
+  launch_block_weights(s, N, nu, P->S, P->Sinv, wu, wp, P->Sw, P->Sinvw);
+  scale_into(P->Sinvw, P->Ft, P->Ftrial, N, s);
+  P->op_S = P->Sw;
+  P->op_Sinv = P->Sinvw;
   int its = 0;
   const int lrc = fgmres(P, o, P->Ftrial, P->dU, &its);
+  P->op_S = nullptr;
+  P->op_Sinv = nullptr;
   R.krylov_its += its;
   R.krylov_its_max = std::max(R.krylov_its_max, its);
   if (lrc == PFF_ERR_NAN) {
@@ -382,10 +446,12 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
     if (rep) *rep = R;
     return lrc;
   }
-  k_add<<<grid_for(N, 256), 256, 0, s>>>(N, P->dUA, P->dU);
+  {
+    ProfScope ps("vec_add", 24.0 * N, s);
+    k_add<<<grid_for(N, 256), 256, 0, s>>>(N, P->dUA, P->dU);
+  }
   // step size test on the full step
-  k_update<<<grid_for(n, 256), 256, 0, s>>>(n, dim, P->u, P->phi, P->phi_old, P->active, P->dU, 1.0,
-                                            P->ut, P->phit_trial);
+  launch_update(s, n, dim, P->u, P->phi, P->phi_old, P->active, P->dU, 1.0, P->ut, P->phit_trial);
   nrm_inf_dev(P->dU, (int64_t)dim * n, P->d_scalars, P->partials, s);
   nrm_inf_dev(P->ut, (int64_t)dim * n, P->d_scalars + 1, P->partials, s);
   nrm_inf_dev(P->dU + (int64_t)dim * n, n, P->d_scalars + 2, P->partials, s);
@@ -394,13 +460,15 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   sync(P);
   const double* hs = P->h_scalars;
   const bool small = hs[0] <= o.tol_step * hs[1] && hs[2] <= o.tol_step * hs[3];
+  const double step_u = hs[1] > 0 ? hs[0] / hs[1] : hs[0];
+  const double step_phi = hs[3] > 0 ? hs[2] / hs[3] : hs[2];
   // 6. line search
   double omega = 1.0;
   if (!small) {
     for (int t = 0; t <= o.max_halvings; ++t) {
       if (t > 0)
-        k_update<<<grid_for(n, 256), 256, 0, s>>>(n, dim, P->u, P->phi, P->phi_old, P->active,
-                                                  P->dU, omega, P->ut, P->phit_trial);
+        launch_update(s, n, dim, P->u, P->phi, P->phi_old, P->active, P->dU, omega, P->ut,
+                      P->phit_trial);
       compute_residual(P, P->ut, P->phit_trial, P->Ftrial);
       double l2 = 0.0;
       scaled_norms(P, P->Ftrial, &l2);
@@ -408,13 +476,19 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
       if (t == o.max_halvings) {
         omega = 1.0;
         R.linesearch_fails += 1;
-        k_update<<<grid_for(n, 256), 256, 0, s>>>(n, dim, P->u, P->phi, P->phi_old, P->active,
-                                                  P->dU, omega, P->ut, P->phit_trial);
+        launch_update(s, n, dim, P->u, P->phi, P->phi_old, P->active, P->dU, omega, P->ut,
+                      P->phit_trial);
         break;
       }
       omega *= 0.5;
     }
   }
+  if (verbose())
+    std::fprintf(stderr,
+                 "[pff] newton k=%d rho=%.3e rho0=%.3e active=%d changed=%d krylov=%d step_u=%.3e "
+                 "step_phi=%.3e small=%d omega=%g\n",
+                 P->k, rho_inf, P->rho0, n_active, n_changed, its, step_u, step_phi, (int)small,
+                 omega);
   std::swap(P->u, P->ut);
   std::swap(P->phi, P->phit_trial);
   P->last_small = small;

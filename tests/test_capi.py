@@ -14,7 +14,8 @@ HEADER = os.path.join(ROOT, "include", "pff.h")
 
 @pytest.fixture(scope="module")
 def lib():
-    from paper_1806_09924_gb300 import build as B
+    import __graft_entry__ as G
+    B = G._build_module()
     if not os.path.exists(B.LIB):
         B.build()
     import paper_1806_09924_gb300 as pff
@@ -58,7 +59,7 @@ def test_struct_layout_matches_header(tmp_path):
 def test_defaults_and_argument_errors_without_gpu(lib):
     import paper_1806_09924_gb300 as pff
     o = pff.options()
-    assert o.tol_linear == 1e-8 and o.c == 1.0 and o.precision == pff.PFF_PREC_FP64
+    assert o.tol_linear == 1e-8 and o.c == 0.1 and o.amg_theta == 0.25 and o.precision == pff.PFF_PREC_FP64
     assert o.krylov_restart == 40 and o.max_newton == 50
     h = ctypes.c_void_p()
     nc = (ctypes.c_int32 * 3)(4, 4, 4)
