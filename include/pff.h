@@ -216,6 +216,31 @@ int pff_linear_solve_dev(pff_problem* prob, const pff_options* opts, const doubl
 int pff_set_state_dev(pff_problem* prob, const double* u_dev, const double* phi_dev,
                       const double* phi_old_dev, const double* phi_prev_dev, int steps_done);
 
+/* Allocation-free TCV / COD ------------------------------------------------ */
+
+/* The paper has no counterpart of this entry point; it exists for callers that
+ * must not allocate device memory when they evaluate the crack functionals --
+ * code running while a stream is being captured into a CUDA graph, or an
+ * application whose device memory is all handed out by its own pool.
+ *
+ * Same results as pff_eval_tcv_cod (same kernels, same arguments and
+ * layouts), but all scratch memory (COD line descriptors, per-line integrals,
+ * TCV partial sums) lives in one fixed array of the library (about 200 KB,
+ * declared with __device__ storage) that every GPU using the library holds
+ * until the process exits; nothing is allocated with cudaMalloc, cudaFree or
+ * any allocating library routine.  At most PFF_NOALLOC_MAX_POINTS COD points
+ * per call: larger n_pts returns PFF_ERR_CAPACITY without doing any work.
+ *
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Every call on a device shares the one array: calls whose work overlaps on
+ * the GPU (several problems or threads on different streams at once) race and
+ * must be serialized by the caller.  No part of the array needs to start at
+ * zero: each slot a call reads was written earlier in the same call. */
+#define PFF_NOALLOC_MAX_POINTS 1024
+int pff_eval_tcv_cod_noalloc(pff_problem* prob, int n_pts, const double* pts, double* tcv,
+                             double* cod);
+
 /* Instrumentation (process-wide, all problems) ----------------------------- */
 
 /* Enable (1) or disable (0) per-kernel timing and reset its totals.  When

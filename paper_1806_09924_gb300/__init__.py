@@ -101,7 +101,10 @@ _SIGS = {
     "pff_profile_enable": (ctypes.c_int, [ctypes.c_int]),
     "pff_profile_report": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "pff_launch_count": (ctypes.c_longlong, []),
+    "pff_eval_tcv_cod_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
 }
+
+PFF_NOALLOC_MAX_POINTS = 1024
 
 _lib = None
 
@@ -246,6 +249,17 @@ class Problem:
         cod = np.zeros(max(npts, 1))
         _check(self._lib.pff_eval_tcv_cod(self._h, npts, pptr, ctypes.byref(tcv),
                                           cod.ctypes.data_as(ctypes.c_void_p)))
+        return tcv.value, cod[:npts]
+
+    def eval_tcv_cod_noalloc(self, pts=()):
+        """pff_eval_tcv_cod without device allocation (fixed scratch, at most
+        PFF_NOALLOC_MAX_POINTS points)."""
+        pts_arr, pptr = _host(np.asarray(pts, dtype=np.float64).reshape(-1))
+        npts = pts_arr.size // (self.dim - 1)
+        tcv = ctypes.c_double()
+        cod = np.zeros(max(npts, 1))
+        _check(self._lib.pff_eval_tcv_cod_noalloc(self._h, npts, pptr, ctypes.byref(tcv),
+                                                  cod.ctypes.data_as(ctypes.c_void_p)))
         return tcv.value, cod[:npts]
 
     def get_solution(self):

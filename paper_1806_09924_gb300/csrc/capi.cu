@@ -10,11 +10,6 @@
 
 namespace pff {
 
-struct Failure {
-  int code;
-  std::string msg;
-};
-
 namespace {
 thread_local std::string g_msg;
 }

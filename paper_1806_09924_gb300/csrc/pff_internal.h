@@ -30,6 +30,12 @@ struct Error {
   std::string msg;
 };
 
+// exception carrying a PFF_ERR_* code to the extern "C" boundary
+struct Failure {
+  int code;
+  std::string msg;
+};
+
 void set_error(int code, const std::string& msg);
 [[noreturn]] void fail(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
