@@ -11,8 +11,8 @@ phi <= phi_old (Section 2):
        neither c nor the threshold of its printed rule; both are read in units
        of the crack-energy stiffness G_c/eps, which makes the two terms of the
        indicator commensurate: c = c_rel G_c/eps, tau = tol_active G_c/eps
-       (tol_active = 1e-12: indicators below it are numerically zero, e.g. far
-       from the crack where phi differs from 1 by ~1e-13); indices
+       (tol_active = 1e-10: indicators below it are numerically zero, e.g. far
+       from the crack where they are ~1e-11 .. 1e-13); indices
        that change membership ``cycle_lock`` times in this loading step are
        locked active (Section 3: alternating active-set indices are detected
        and constrained to avoid cycles)
@@ -59,7 +59,7 @@ class Options:
     max_halvings: int = 10
     cycle_lock: int = 3
     full_jacobian: bool = False
-    tol_active: float = 1e-12    # threshold tau of step 2, in units of G_c / eps
+    tol_active: float = 1e-10    # threshold tau of step 2, in units of G_c / eps
 
 
 @dataclass
