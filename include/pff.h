@@ -83,7 +83,7 @@ typedef struct pff_options {
   int apply_variant;    /* PFF_APPLY_*; PFF_APPLY_AUTO */
   int precond;          /* PFF_PC_*; PFF_PC_AMG */
   double cheb_ratio;    /* Chebyshev smoothing interval [lmax/ratio, 1.1 lmax]; 8 */
-  double tol_active;    /* active-set threshold tau, in units of G_c/eps; 1e-12 */
+  double tol_active;    /* active-set threshold tau, in units of G_c/eps; 1e-10 */
   double atol_newton;   /* absolute floor of the scaled reduced residual test; 1e-14 */
   int reserved[2];
 } pff_options;
@@ -248,6 +248,11 @@ int pff_eval_tcv_cod_noalloc(pff_problem* prob, int n_pts, const double* pts, do
  * and is credited with its algorithmic bytes (every input and output array
  * moved once).  Adds a few microseconds per launch. */
 int pff_profile_enable(int on);
+
+/* Restrict the timing to launches of one kernel name (as reported by
+ * pff_profile_report); NULL times every instrumented launch again.  Timing a
+ * single kernel keeps the event overhead off the rest of the run. */
+int pff_profile_select(const char* name);
 
 /* Synchronize the device and write per-kernel totals as a JSON object
  * {"name": {"count": launches, "ms": total time, "bytes": algorithmic bytes}}

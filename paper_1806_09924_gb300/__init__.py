@@ -99,6 +99,7 @@ _SIGS = {
                                             ctypes.POINTER(ctypes.c_int)]),
     "pff_set_state_dev": (ctypes.c_int, [_P, _P, _P, _P, _P, ctypes.c_int]),
     "pff_profile_enable": (ctypes.c_int, [ctypes.c_int]),
+    "pff_profile_select": (ctypes.c_int, [ctypes.c_char_p]),
     "pff_profile_report": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "pff_launch_count": (ctypes.c_longlong, []),
     "pff_eval_tcv_cod_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
@@ -305,6 +306,11 @@ class Problem:
 def profile_enable(on: bool = True):
     """Enable / disable per-kernel event timing (resets the totals)."""
     _check(load_library().pff_profile_enable(1 if on else 0))
+
+
+def profile_select(name=None):
+    """Time only launches of kernel `name` (None: all instrumented launches)."""
+    _check(load_library().pff_profile_select(name.encode() if name else None))
 
 
 def profile_report() -> dict:

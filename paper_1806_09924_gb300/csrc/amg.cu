@@ -821,6 +821,65 @@ void spmv_t<float>(const Bsr& A, const float* x, float* y, float a, float b, cud
 }
 
 template <class T>
+const T* stencil_vals(const AmgLevel& L);
+template <>
+const double* stencil_vals<double>(const AmgLevel& L) { return L.st; }
+template <>
+const float* stencil_vals<float>(const AmgLevel& L) { return L.stf; }
+
+template <class T>
+void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s);
+
+// Levels 1.. of the cycle (many small, launch-bound kernels) replayed as one
+// CUDA graph.  It is captured on first use after each build, on a private
+// stream, and launched on the caller's stream; if capture is not possible the
+// levels run as ordinary launches.
+template <class T>
+void coarse_cycle(Amg& amg, T* cb, T* cx, cudaStream_t s) {
+  if (!amg.graph && amg.use_graph) {
+    bool ok = true;
+    if (!amg.cap_stream) ok = cudaStreamCreateWithFlags(&amg.cap_stream, cudaStreamNonBlocking) == cudaSuccess;
+    if (ok) ok = cudaStreamBeginCapture(amg.cap_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (ok) {
+      set_capturing(true);
+      try {
+        vcycle_level<T>(amg, 1, cb, cx, amg.cap_stream);
+      } catch (...) {
+        ok = false;
+      }
+      set_capturing(false);
+      cudaGraph_t g = nullptr;
+      if (cudaStreamEndCapture(amg.cap_stream, &g) != cudaSuccess) ok = false;
+      if (ok && g) {
+        size_t nn = 0;
+        cudaGraphGetNodes(g, nullptr, &nn);
+        std::vector<cudaGraphNode_t> nodes(nn);
+        cudaGraphGetNodes(g, nodes.data(), &nn);
+        int kern = 0;
+        for (auto nd : nodes) {
+          cudaGraphNodeType t;
+          if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
+        }
+        amg.graph_kernels = kern;
+        if (cudaGraphInstantiate(&amg.graph, g, 0) != cudaSuccess) {
+          amg.graph = nullptr;
+          ok = false;
+        }
+      }
+      if (g) cudaGraphDestroy(g);
+    }
+    cudaGetLastError();
+    if (!ok) amg.use_graph = false;
+  }
+  if (amg.graph) {
+    ProfScope ps("coarse_levels_graph", 0.0, s, amg.graph_kernels);
+    PFF_CUDA(cudaGraphLaunch(amg.graph, s));
+  } else {
+    vcycle_level<T>(amg, 1, cb, cx, s);
+  }
+}
+
+template <class T>
 void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* t, T* d, bool zero_start,
             cudaStream_t s) {
   // Chebyshev iteration for D^-1 A on [lmax/30, 1.1 lmax]
@@ -839,15 +898,25 @@ void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* 
   const double nvec = (double)nb * b * sizeof(T);
   const char* tag = sizeof(T) == 8 ? "cheb_f64" : "cheb_f32";
   // first step: d = r / theta
-  ProfScope ps0(tag, (zero_start ? 0.0 : mat_b) + nvec * (zero_start ? 4.0 : 6.0), s);
-  k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
-                              T(0), T(1.0 / theta), zero_start ? 1 : 0);
+  if (L.stencil) {
+    launch_stencil_cheb<T>(L.mesh, nb, b, stencil_vals<T>(L), dinvs<T>(L), rhs, cur, nxt, d, 0.0,
+                           1.0 / theta, zero_start ? 1 : 0, s);
+  } else {
+    ProfScope ps0(tag, (zero_start ? 0.0 : mat_b) + nvec * (zero_start ? 4.0 : 6.0), s);
+    k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
+                                T(0), T(1.0 / theta), zero_start ? 1 : 0);
+  }
   std::swap(cur, nxt);
   for (int k = 1; k < degree; ++k) {
     const double rn = 1.0 / (2.0 * sigma - rho);
-    ProfScope psk(tag, mat_b + 6.0 * nvec, s);
-    k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
-                                T(rn * rho), T(2.0 * rn / delta), 0);
+    if (L.stencil) {
+      launch_stencil_cheb<T>(L.mesh, nb, b, stencil_vals<T>(L), dinvs<T>(L), rhs, cur, nxt, d,
+                             rn * rho, 2.0 * rn / delta, 0, s);
+    } else {
+      ProfScope psk(tag, mat_b + 6.0 * nvec, s);
+      k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
+                                  T(rn * rho), T(2.0 * rn / delta), 0);
+    }
     std::swap(cur, nxt);
     rho = rn;
   }
@@ -876,18 +945,21 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
     return;
   }
   const Bsr& A = L.A;
-  {
+  if (L.stencil) {
+    launch_stencil_resid<T>(L.mesh, A.nrows, A.br, stencil_vals<T>(L), rhs, x, r, s);
+  } else {
     ProfScope ps(sizeof(T) == 8 ? "resid_f64" : "resid_f32",
                  (double)A.nnzb * (A.br * A.bc * (double)sizeof(T) + 4.0) + 4.0 * (A.nrows + 1.0) +
                      3.0 * sizeof(T) * (double)A.nrows * A.br, s);
-  k_resid<T><<<grid_for((int64_t)A.nrows * A.br, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr, A.col,
-                                                                    vals<T>(A), rhs, x, r);
+    k_resid<T><<<grid_for((int64_t)A.nrows * A.br, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr,
+                                                                      A.col, vals<T>(A), rhs, x, r);
   }
   const bool last = l + 1 == (int)amg.lev.size();
   T* cb = last ? reinterpret_cast<T*>(amg.cb) : reinterpret_cast<T*>(amg.lev[l + 1].b);
   T* cx = last ? reinterpret_cast<T*>(amg.cx) : reinterpret_cast<T*>(amg.lev[l + 1].x);
   spmv_t<T>(L.R, r, cb, T(1), T(0), s);
-  vcycle_level<T>(amg, l + 1, cb, cx, s);
+  if (l == 0 && amg.use_graph) coarse_cycle<T>(amg, cb, cx, s);
+  else vcycle_level<T>(amg, l + 1, cb, cx, s);
   spmv_t<T>(L.P, cx, x, T(1), T(1), s);
   smooth<T>(L, amg.cheb_degree, amg.cheb_ratio, rhs, x, t, d, false, s);
 }
@@ -1066,6 +1138,11 @@ void check_err(SetupScratch& sc, cudaStream_t s, const char* where) {
 }  // namespace
 
 void Amg::release() {
+  if (graph) cudaGraphExecDestroy(graph);
+  graph = nullptr;
+  graph_kernels = 0;
+  if (cap_stream) cudaStreamDestroy(cap_stream);
+  cap_stream = nullptr;
   for (auto& L : lev) {
     L.A.release();
     L.P.release();
@@ -1095,6 +1172,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
   amg.mixed = prm.mixed;
   amg.cheb_degree = prm.cheb_degree;
   amg.cheb_ratio = prm.cheb_ratio;
+  amg.use_graph = prm.use_graph;
   SetupScratch sc;
   sc.err = dalloc<int>(4);
   PFF_CUDA(cudaMallocHost(&sc.h_err, sizeof(int) * 4));

@@ -4,7 +4,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <stdexcept>
+#include <unordered_set>
 
 #include "pff_internal.h"
 
@@ -28,9 +30,44 @@ void check_cuda(cudaError_t e, const char* what) {
   throw Failure{code, std::string(what) + ": " + cudaGetErrorString(e)};
 }
 
+// Device memory.  While an AllocStream scope names a (non-default) stream, memory
+// comes from the device's stream-ordered pool on that stream (cudaMallocAsync /
+// cudaFreeAsync: no device-wide synchronization, freed blocks cached for reuse);
+// otherwise plain cudaMalloc / cudaFree.
+namespace {
+thread_local cudaStream_t t_alloc_stream = nullptr;
+std::mutex g_async_mu;
+std::unordered_set<void*> g_async_ptrs;
+bool g_pool_ready[64] = {false};
+
+void prepare_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+  if (g_pool_ready[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;   // keep freed blocks in this process's pool
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
+  cudaGetLastError();
+  g_pool_ready[dev] = true;
+}
+}  // namespace
+
+AllocStream::AllocStream(cudaStream_t s) : prev_(t_alloc_stream) { t_alloc_stream = s; }
+AllocStream::~AllocStream() { t_alloc_stream = prev_; }
+
 void* dmalloc(size_t bytes) {
   void* p = nullptr;
-  const cudaError_t e = cudaMalloc(&p, bytes ? bytes : 16);
+  cudaError_t e;
+  if (t_alloc_stream) {
+    std::lock_guard<std::mutex> g(g_async_mu);
+    prepare_pool();
+    e = cudaMallocAsync(&p, bytes ? bytes : 16, t_alloc_stream);
+    if (e == cudaSuccess) g_async_ptrs.insert(p);
+  } else {
+    e = cudaMalloc(&p, bytes ? bytes : 16);
+  }
   if (e != cudaSuccess) {
     cudaGetLastError();
     throw Failure{PFF_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed: " +
@@ -40,7 +77,18 @@ void* dmalloc(size_t bytes) {
 }
 
 void dfree(void* p) {
-  if (p) cudaFree(p);
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> g(g_async_mu);
+    auto it = g_async_ptrs.find(p);
+    if (it != g_async_ptrs.end()) {
+      g_async_ptrs.erase(it);
+      // outside an AllocStream scope the owner has synchronized its stream first
+      cudaFreeAsync(p, t_alloc_stream);
+      return;
+    }
+  }
+  cudaFree(p);
 }
 
 }  // namespace pff
@@ -94,6 +142,8 @@ void release(pff_problem* P) {
                    P->Ft, P->dU, P->dUA, P->ut, P->phit_trial, P->Ftrial, P->Bu, P->Bp, P->xyz,
                    P->V, P->Z, P->w, P->h, P->tmp};
   for (double* p : dbl) dfree(p);
+  dfree(P->Kuu_f);
+  dfree(P->Kpp_f);
   dfree(P->active);
   dfree(P->active_prev);
   dfree(P->raw_prev);
@@ -170,7 +220,7 @@ void pff_default_options(pff_options* o) {
   o->apply_variant = PFF_APPLY_AUTO;
   o->precond = PFF_PC_AMG;
   o->cheb_ratio = 8.0;
-  o->tol_active = 1e-12;
+  o->tol_active = 1e-10;
   o->atol_newton = 1e-14;
 }
 
@@ -356,6 +406,7 @@ int pff_set_state_dev(pff_problem* P, const double* u, const double* phi, const 
 int pff_newton_step(pff_problem* P, const pff_options* opts, pff_step_report* rep) {
   API_BEGIN
   need(P != nullptr, "problem is NULL");
+  pff::AllocStream alloc_scope(P->stream);
   pff_options o;
   pff_default_options(&o);
   if (opts) o = *opts;
@@ -380,6 +431,7 @@ int pff_solve_loading_steps(pff_problem* P, int n_steps, const double* p_schedul
                             const pff_options* opts, pff_step_report* reports) {
   API_BEGIN
   need(P != nullptr, "problem is NULL");
+  pff::AllocStream alloc_scope(P->stream);
   need(n_steps >= 0 && (n_steps == 0 || p_schedule != nullptr), "bad schedule");
   pff_options o;
   pff_default_options(&o);
@@ -412,6 +464,7 @@ int pff_solve_loading_steps(pff_problem* P, int n_steps, const double* p_schedul
 int pff_eval_tcv_cod(pff_problem* P, int n_pts, const double* pts, double* tcv, double* cod) {
   API_BEGIN
   need(P != nullptr, "problem is NULL");
+  pff::AllocStream alloc_scope(P->stream);
   need(n_pts >= 0 && (n_pts == 0 || pts != nullptr), "bad COD points");
   const auto m = P->mesh();
   if (tcv) {
@@ -506,7 +559,7 @@ int pff_active_set_dev(pff_problem* P, double c, uint8_t* active_dev, double* in
   need(P != nullptr, "problem is NULL");
   need(c > 0 && std::isfinite(c), "c must be > 0");
   pff::compute_residual(P, P->u, P->phi, P->F);
-  pff::compute_active_set(P, c, 1e-12, 1 << 30, false);
+  pff::compute_active_set(P, c, 1e-10, 1 << 30, false);
   if (active_dev)
     PFF_CUDA(cudaMemcpyAsync(active_dev, P->active, P->n_nodes, cudaMemcpyDeviceToDevice, P->stream));
   if (indicator_dev)
@@ -535,6 +588,7 @@ int pff_apply_jacobian_dev(pff_problem* P, int variant, const double* x_dev, dou
 int pff_precond_setup(pff_problem* P, const pff_options* opts) {
   API_BEGIN
   need(P != nullptr, "problem is NULL");
+  pff::AllocStream alloc_scope(P->stream);
   need(P->phi_assembled, "call pff_assemble first");
   pff_options o;
   pff_default_options(&o);
@@ -559,6 +613,7 @@ int pff_linear_solve_dev(pff_problem* P, const pff_options* opts, const double* 
                          double* x_dev, int* iters) {
   API_BEGIN
   need(P != nullptr && b_dev && x_dev, "NULL argument");
+  pff::AllocStream alloc_scope(P->stream);
   need(P->phi_assembled, "call pff_assemble first");
   pff_options o;
   pff_default_options(&o);

@@ -854,6 +854,100 @@ __global__ void k_rigid_modes(MeshDev m, int64_t n, double* __restrict__ B) {
     for (int a = 0; a < D; ++a) B[k * ld + i * D + a] = v[k][a];
 }
 
+// ------------------------------------------- stencil smoother (AMG level 0) --
+// The finest AMG level of each block is the assembled node stencil itself
+// (Kuu with B = d, Kpp with B = 1, slot-major).  One Chebyshev step, fused with
+// the operator apply:  res = dinv .* (rhs - K x_in),  d = cd d + cr res,
+// x_out = x_in + d.  With zero_x the iterate starts at 0 (no apply).
+template <class T, int D, int B>
+__global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
+                                                      const T* __restrict__ K,
+                                                      const T* __restrict__ dinv,
+                                                      const T* __restrict__ rhs,
+                                                      const T* __restrict__ xin,
+                                                      T* __restrict__ xout, T* __restrict__ d,
+                                                      T cd, T cr, int zero_x) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NS = D == 2 ? 9 : 27;
+  T acc[B];
+#pragma unroll
+  for (int a = 0; a < B; ++a) acc[a] = T(0);
+  if (!zero_x) {
+    int idx[3];
+    node_index<D>(i, m, idx);
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int64_t j = neighbour<D>(idx, s, m);
+      if (j < 0) continue;
+      T xj[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) xj[c] = xin[j * B + c];
+#pragma unroll
+      for (int a = 0; a < B; ++a)
+#pragma unroll
+        for (int c = 0; c < B; ++c) acc[a] += K[((int64_t)(s * B + a) * B + c) * n + i] * xj[c];
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < B; ++a) {
+    const int64_t r = i * B + a;
+    const T res = dinv[r] * (rhs[r] - acc[a]);
+    const T dn = (zero_x ? T(0) : cd * d[r]) + cr * res;
+    d[r] = dn;
+    xout[r] = (zero_x ? T(0) : xin[r]) + dn;
+  }
+}
+
+// r = rhs - K x
+template <class T, int D, int B>
+__global__ void __launch_bounds__(256) k_stencil_resid(MeshDev m, int64_t n,
+                                                       const T* __restrict__ K,
+                                                       const T* __restrict__ rhs,
+                                                       const T* __restrict__ x,
+                                                       T* __restrict__ r) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NS = D == 2 ? 9 : 27;
+  int idx[3];
+  node_index<D>(i, m, idx);
+  T acc[B];
+#pragma unroll
+  for (int a = 0; a < B; ++a) acc[a] = T(0);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int64_t j = neighbour<D>(idx, s, m);
+    if (j < 0) continue;
+    T xj[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) xj[c] = x[j * B + c];
+#pragma unroll
+    for (int a = 0; a < B; ++a)
+#pragma unroll
+      for (int c = 0; c < B; ++c) acc[a] += K[((int64_t)(s * B + a) * B + c) * n + i] * xj[c];
+  }
+#pragma unroll
+  for (int a = 0; a < B; ++a) r[i * B + a] = rhs[i * B + a] - acc[a];
+}
+
+// inverse diagonal of a node stencil (block size B, centre slot c0)
+__global__ void k_stencil_dinv(int64_t n, int B, int c0, const double* __restrict__ K,
+                               double* __restrict__ dinv, float* __restrict__ dinvf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int a = 0; a < B; ++a) {
+    const double v = K[((int64_t)(c0 * B + a) * B + a) * n + i];
+    const double r = v != 0.0 ? 1.0 / v : 0.0;
+    dinv[i * B + a] = r;
+    if (dinvf) dinvf[i * B + a] = (float)r;
+  }
+}
+
+__global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
 template <int D>
 __global__ void k_node_coords(MeshDev m, int64_t n, double* __restrict__ xyz) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1141,6 +1235,61 @@ void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s) 
   count_launch();
   DISPATCH(m.dim, (k_rigid_modes<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, B)));
   PFF_LAUNCH("rigid_modes");
+}
+
+#define STENCIL_DISPATCH(dim, b, KERNEL, ...)                                   \
+  do {                                                                           \
+    const unsigned g_ = grid_for(n, 256);                                        \
+    if ((dim) == 2 && (b) == 2) KERNEL<T, 2, 2><<<g_, 256, 0, s>>>(__VA_ARGS__); \
+    else if ((dim) == 2 && (b) == 1) KERNEL<T, 2, 1><<<g_, 256, 0, s>>>(__VA_ARGS__); \
+    else if ((dim) == 3 && (b) == 3) KERNEL<T, 3, 3><<<g_, 256, 0, s>>>(__VA_ARGS__); \
+    else if ((dim) == 3 && (b) == 1) KERNEL<T, 3, 1><<<g_, 256, 0, s>>>(__VA_ARGS__); \
+    else fail(PFF_ERR_INVALID_ARG, "stencil block size must be dim or 1");     \
+  } while (0)
+
+template <class T>
+void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T* dinv,
+                         const T* rhs, const T* xin, T* xout, T* d, double cd, double cr,
+                         int zero_x, cudaStream_t s) {
+  // stencil values (unless starting from zero), then dinv, rhs, x_in, x_out, d read + write
+  const double bytes = sizeof(T) * (double)n *
+                       ((zero_x ? 0.0 : NSd(m.dim) * b * b) + b * (zero_x ? 4.0 : 6.0));
+  ProfScope ps(sizeof(T) == 8 ? "cheb0_f64" : "cheb0_f32", bytes, s);
+  STENCIL_DISPATCH(m.dim, b, k_stencil_cheb, m, n, K, dinv, rhs, xin, xout, d, (T)cd, (T)cr, zero_x);
+  PFF_LAUNCH("stencil_cheb");
+}
+
+template <class T>
+void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const T* rhs, const T* x,
+                          T* r, cudaStream_t s) {
+  const double bytes = sizeof(T) * (double)n * (NSd(m.dim) * b * b + 3.0 * b);
+  ProfScope ps(sizeof(T) == 8 ? "resid0_f64" : "resid0_f32", bytes, s);
+  STENCIL_DISPATCH(m.dim, b, k_stencil_resid, m, n, K, rhs, x, r);
+  PFF_LAUNCH("stencil_resid");
+}
+
+template void launch_stencil_cheb<float>(const MeshDev&, int64_t, int, const float*, const float*,
+                                         const float*, const float*, float*, float*, double, double,
+                                         int, cudaStream_t);
+template void launch_stencil_cheb<double>(const MeshDev&, int64_t, int, const double*,
+                                          const double*, const double*, const double*, double*,
+                                          double*, double, double, int, cudaStream_t);
+template void launch_stencil_resid<float>(const MeshDev&, int64_t, int, const float*, const float*,
+                                          const float*, float*, cudaStream_t);
+template void launch_stencil_resid<double>(const MeshDev&, int64_t, int, const double*,
+                                           const double*, const double*, double*, cudaStream_t);
+
+void launch_stencil_dinv(const MeshDev& m, int64_t n, int b, const double* K, double* dinv,
+                         float* dinvf, cudaStream_t s) {
+  ProfScope ps("stencil_dinv", (double)n * b * (8.0 + 8.0 + (dinvf ? 4.0 : 0.0)), s);
+  k_stencil_dinv<<<grid_for(n, 256), 256, 0, s>>>(n, b, m.dim == 2 ? 4 : 13, K, dinv, dinvf);
+  PFF_LAUNCH("stencil_dinv");
+}
+
+void convert_d2f(const double* a, float* b, int64_t n, cudaStream_t s) {
+  ProfScope ps("to_f32", 12.0 * n, s);
+  k_d2f<<<grid_for(n, 256), 256, 0, s>>>(n, a, b);
+  PFF_LAUNCH("d2f");
 }
 
 void launch_node_coords(const MeshDev& m, int64_t n, double* xyz, cudaStream_t s) {

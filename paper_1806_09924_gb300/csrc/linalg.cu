@@ -191,7 +191,9 @@ void nrm_inf_dev(const double* x, int64_t n, double* out, double* partials, cuda
 
 void multidot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* out,
                   double* partials, cudaStream_t s) {
-  const int g = std::min(red_grid(n), 256);
+  // up to 1024 blocks (about 7 per SM): enough loads in flight to stream V at HBM speed;
+  // the partial sums need nv * g <= 65536 doubles (nv <= 64)
+  const int g = red_grid(n);
   ProfScope ps("multidot", 8.0 * n * (nv + 1.0), s, (nv + 7) / 8 + 1);
   int k0 = 0;
   while (k0 < nv) {

@@ -47,6 +47,9 @@ void check_cuda(cudaError_t e, const char* what);
 // ProfScope are also timed with a CUDA event pair and credited with their
 // algorithmic bytes (each input / output array moved once).
 void count_launch(int k = 1);
+// while a stream is being captured into a graph, launches are neither counted
+// nor timed (the graph's replays are)
+void set_capturing(bool on);
 // diagnostics on stderr when the environment variable PFF_VERBOSE is set
 bool verbose();
 class ProfScope {
@@ -66,6 +69,16 @@ class ProfScope {
 // ------------------------------------------------------------ device memory --
 void* dmalloc(size_t bytes);
 void dfree(void* p);
+// Scope in which dmalloc / dfree are stream-ordered on stream s (a non-default
+// stream; with s == nullptr the plain synchronous calls are used).
+class AllocStream {
+ public:
+  explicit AllocStream(cudaStream_t s);
+  ~AllocStream();
+
+ private:
+  cudaStream_t prev_;
+};
 template <class T>
 T* dalloc(size_t n) {
   return static_cast<T*>(dmalloc(n * sizeof(T) + 16));
@@ -107,6 +120,12 @@ struct AmgLevel {
   double lmax = 1.0;          // estimate of the largest eigenvalue of D^-1 A
   int n = 0;                  // scalar rows
   bool terminal = false;      // no coarser level (every row isolated): smoothing only
+  // the finest level may smooth on the assembled node stencil (slot-major,
+  // block size A.br) instead of its BSR copy
+  bool stencil = false;
+  MeshDev mesh{};
+  const double* st = nullptr;
+  const float* stf = nullptr;
   // V-cycle work vectors (stored as doubles; FP32 cycles reinterpret them)
   double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
 };
@@ -121,6 +140,11 @@ struct Amg {
   int cheb_degree = 2;
   double cheb_ratio = 30.0;
   int built = 0;
+  // levels 1.. captured as one CUDA graph (see coarse_cycle in amg.cu)
+  bool use_graph = true;
+  cudaGraphExec_t graph = nullptr;
+  int graph_kernels = 0;
+  cudaStream_t cap_stream = nullptr;
   void release();
 };
 
@@ -136,6 +160,7 @@ struct AmgParams {
   const double* coords = nullptr;
   int coord_dim = 0;
   double mdrop = 1e-3;
+  bool use_graph = true;
 };
 
 // Build a hierarchy for the block matrix A (FP64 values, block size br) with
@@ -218,6 +243,18 @@ void build_stencil_bsr_structure(const MeshDev& m, int64_t n, int b, Bsr& A, cud
 void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s);
 // node coordinates [n][dim]
 void launch_node_coords(const MeshDev& m, int64_t n, double* xyz, cudaStream_t s);
+// AMG finest level on the node stencil (T = float or double; b = dim or 1)
+template <class T>
+void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T* dinv,
+                         const T* rhs, const T* xin, T* xout, T* d, double cd, double cr,
+                         int zero_x, cudaStream_t s);
+template <class T>
+void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const T* rhs, const T* x,
+                          T* r, cudaStream_t s);
+void convert_d2f(const double* a, float* b, int64_t n, cudaStream_t s);
+// dinv (and its FP32 copy, may be null) = inverse diagonal of a node stencil
+void launch_stencil_dinv(const MeshDev& m, int64_t n, int b, const double* K, double* dinv,
+                         float* dinvf, cudaStream_t s);
 // TCV partial sums (deterministic) and COD line integrals
 void tcv_dev(const MeshDev& m, int64_t n_cells, const double* u, const double* phi, double* out,
              double* partials, cudaStream_t s);
@@ -259,6 +296,7 @@ struct pff_problem {
 
   // assembled stencils
   double *Kuu = nullptr, *Kpu = nullptr, *Kpp = nullptr;
+  float *Kuu_f = nullptr, *Kpp_f = nullptr;   // FP32 copies for the mixed-precision AMG
   bool uu_assembled = false, phi_assembled = false;
 
   // work vectors (n_dofs)
@@ -272,6 +310,9 @@ struct pff_problem {
   double* Bp = nullptr;   // constants
   pff::Amg amg_u, amg_p;
   bool amg_u_valid = false;
+  // the phase-field hierarchy is reused while the active set barely moves
+  int64_t phi_amg_changes = 0;   // active-set changes since the last build
+  int phi_amg_age = 0;           // Newton iterations since the last build
   int precision = PFF_PREC_FP64;
 
   // Krylov workspace
@@ -309,7 +350,7 @@ void end_loading_step(pff_problem* P);
 void compute_residual(pff_problem* P, const double* u, const double* phi, double* F);
 void compute_active_set(pff_problem* P, double c_rel, double tol_active, int lock_after, bool track);
 void assemble_all(pff_problem* P);
-void precond_setup(pff_problem* P, const pff_options& o);
+void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse = false);
 void precond_apply(pff_problem* P, const double* r, double* z);
 int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int* iters);
 void apply_jacobian(pff_problem* P, int variant, const double* x, double* y, const double* Sinv);

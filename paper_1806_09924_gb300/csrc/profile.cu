@@ -39,6 +39,7 @@ struct Acc {
 struct Profiler {
   std::mutex mu;
   bool on = false;
+  std::string only;   // when set, only launches of this name are timed
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   std::map<std::string, Acc> acc;
@@ -89,13 +90,22 @@ bool verbose() {
   return v;
 }
 
-void count_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+namespace {
+thread_local bool t_capturing = false;
+}
+
+void set_capturing(bool on) { t_capturing = on; }
+
+void count_launch(int k) {
+  if (!t_capturing) g_launches.fetch_add(k, std::memory_order_relaxed);
+}
 
 ProfScope::ProfScope(const char* name, double bytes, cudaStream_t s, int kernels)
     : name_(name), bytes_(bytes), s_(s), a_(nullptr) {
   count_launch(kernels);
   Profiler& P = prof();
-  if (!P.on) return;
+  if (!P.on || t_capturing) return;
+  if (!P.only.empty() && P.only != name_) return;
   std::lock_guard<std::mutex> g(P.mu);
   if (P.pending.size() > 4096) P.flush(false);
   a_ = P.get();
@@ -122,6 +132,13 @@ int pff_profile_enable(int on) {
   P.flush(true);
   P.acc.clear();
   P.on = on != 0;
+  return PFF_OK;
+}
+
+int pff_profile_select(const char* name) {
+  auto& P = pff::prof();
+  std::lock_guard<std::mutex> g(P.mu);
+  P.only = name ? name : "";
   return PFF_OK;
 }
 

@@ -51,13 +51,20 @@ __global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __r
   if (i < n) c[i] = a[i] * b[i];
 }
 
-// w /= sqrt(*nrm2) (into dst)
+// w /= sqrt(*nrm2) (into dst); the scale is computed once per block (FP64
+// square roots and divides are slow on this GPU)
 __global__ void k_normalize(int64_t n, const double* __restrict__ w, const double* __restrict__ nrm2,
                             double* __restrict__ dst) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const double nn = *nrm2;
-  const double s = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-  if (i < n) dst[i] = w[i] * s;
+  __shared__ double sc;
+  if (threadIdx.x == 0) {
+    const double nn = *nrm2;
+    sc = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+  }
+  __syncthreads();
+  const double s = sc;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = w[i] * s;
 }
 
 __global__ void k_sub(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
@@ -175,7 +182,7 @@ void apply_jacobian(pff_problem* P, int variant, const double* x, double* y, con
   }
 }
 
-void precond_setup(pff_problem* P, const pff_options& o) {
+void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   P->precision = o.precision;
   if (o.precond == PFF_PC_JACOBI) return;
   AmgParams ap;
@@ -187,13 +194,47 @@ void precond_setup(pff_problem* P, const pff_options& o) {
   ap.coord_dim = P->dim;
   ap.mixed = o.precision == PFF_PREC_MIXED;
   const auto m = P->mesh();
+  const int64_t n = P->n_nodes;
+  const int ns = n_slots(P->dim);
+  // the finest level of each hierarchy smooths on the assembled stencil itself
+  auto use_stencil = [&](Amg& amg, const double* K, float*& Kf, int64_t count) {
+    if (amg.lev.empty()) return;
+    AmgLevel& L0 = amg.lev[0];
+    L0.stencil = true;
+    L0.mesh = m;
+    L0.st = K;
+    if (ap.mixed) {
+      if (!Kf) Kf = dalloc<float>(count);
+      convert_d2f(K, Kf, count, P->stream);
+      L0.stf = Kf;
+    }
+  };
   if (!P->amg_u_valid || P->amg_u.mixed != ap.mixed) {
-    launch_stencil_to_bsr(m, P->n_nodes, P->dim, P->Kuu, P->Auu, P->stream);
+    ProfScope ps("amg_setup_u", 0.0, P->stream, 0);   // wall time of the build (syncs inside)
+    launch_stencil_to_bsr(m, n, P->dim, P->Kuu, P->Auu, P->stream);
     amg_build(P->amg_u, P->Auu, P->Bu, P->dim == 2 ? 3 : 6, ap, P->stream);
+    use_stencil(P->amg_u, P->Kuu, P->Kuu_f, (int64_t)ns * P->dim * P->dim * n);
     P->amg_u_valid = true;
   }
-  launch_stencil_to_bsr(m, P->n_nodes, 1, P->Kpp, P->App, P->stream);
-  amg_build(P->amg_p, P->App, P->Bp, 1, ap, P->stream);
+  // Phase-field block: rebuild at the start of a loading step and whenever the
+  // active set moved by more than 1 % of the nodes (or every 5 iterations);
+  // otherwise keep the hierarchy and refresh only the finest level's stencil
+  // values and diagonal.  FGMRES converges to its tolerance either way: a
+  // stale coarse space costs iterations, not accuracy.
+  const bool rebuild = !allow_reuse || !P->amg_p.built || P->amg_p.mixed != ap.mixed || P->k == 0 ||
+                       P->phi_amg_changes > n / 100 || P->phi_amg_age >= 5 || P->amg_p.lev.empty();
+  if (rebuild) {
+    ProfScope ps("amg_setup_phi", 0.0, P->stream, 0);
+    launch_stencil_to_bsr(m, n, 1, P->Kpp, P->App, P->stream);
+    amg_build(P->amg_p, P->App, P->Bp, 1, ap, P->stream);
+    P->phi_amg_changes = 0;
+    P->phi_amg_age = 0;
+  } else {
+    AmgLevel& L0 = P->amg_p.lev[0];
+    launch_stencil_dinv(m, n, 1, P->Kpp, L0.dinv, ap.mixed ? L0.dinvf : nullptr, P->stream);
+    P->phi_amg_age += 1;
+  }
+  use_stencil(P->amg_p, P->Kpp, P->Kpp_f, (int64_t)ns * n);
 }
 
 // z = diag(V_u, V_phi) (S .* r) -- the right preconditioner of the scaled system
@@ -219,7 +260,7 @@ static void precond(pff_problem* P, const pff_options& o, const double* r, doubl
 // Restarted flexible GMRES (right preconditioned, CGS2 orthogonalization) for
 // (S^-1 G~) x = b; b is already scaled.  Returns PFF_OK or PFF_ERR_NOT_CONVERGED.
 int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int* iters) {
-  const int m = std::max(2, o.krylov_restart);
+  const int m = std::min(60, std::max(2, o.krylov_restart));   // multidot partials hold 64 vectors
   ensure_krylov(P, m);
   const int64_t N = P->n_dofs;
   cudaStream_t s = P->stream;
@@ -413,7 +454,8 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   }
   // 4. reduced Jacobian and right-hand side
   assemble_all(P);
-  precond_setup(P, o);
+  if (P->have_prev) P->phi_amg_changes += n_changed;
+  precond_setup(P, o, true);
   // 5. linear solve on the scaled system.  The displacement and phase-field
   // blocks of S^-1 F~ differ by orders of magnitude (displacements vs. a
   // dimensionless phase field), so each block's rows are further divided by the

@@ -137,13 +137,18 @@ def _gpu_solution(w, pressures, **kw):
     return P, u, phi, act.astype(bool), reps
 
 
+TIE_BAND = 1e-7   # in units of G_c / eps
+
+
 def _assert_solution_parity(mesh, st, u, phi, act):
     """u, phi within RTOL_SOL; active sets identical wherever the oracle's indicator
-    exceeds 1e-9 G_c/eps (flipping a node below that moves phi by <~ 1e-8)."""
+    exceeds TIE_BAND G_c/eps.  With the threshold tau of the active-set rule, a node
+    whose multiplier is within about tau (H_ii/m_i)/c of zero is a fixed point both
+    active and inactive; flipping such a node moves phi by <~ 1e-8."""
     assert rel(u, st.u) <= RTOL_SOL
     assert rel(phi, st.phi) <= RTOL_SOL
     ind = st.indicator
-    clear = np.abs(ind) > 1e-9 * st.prm.Gc / st.prm.eps
+    clear = np.abs(ind) > TIE_BAND * st.prm.Gc / st.prm.eps
     mism = np.count_nonzero(act[clear] != st.active[clear])
     assert mism == 0, f"{mism} active-set mismatches away from ties"
     return int(np.count_nonzero(act != st.active))
