@@ -25,7 +25,9 @@ phi <= phi_old (Section 2):
        (sparse direct solves; the paper uses GMRES + AMG for this step)
     6. line search: omega = 1, halved while the scaled reduced residual does
        not decrease (at most ``max_halvings`` times)
-  until the active set is unchanged, the scaled reduced residual has dropped
+  until the active set is unchanged (membership changes of nodes whose
+  indicator is within the band tol_change G_c/eps do not count: with tau > 0
+  such a node is a fixed point both ways), the scaled reduced residual has dropped
   by ``tol_newton`` (or below the round-off floor ``atol_newton``; a loading
   step that starts near its solution cannot drop by 1e-10) and the last
   Newton step was below ``tol_step``.
@@ -60,6 +62,7 @@ class Options:
     cycle_lock: int = 3
     full_jacobian: bool = False
     tol_active: float = 1e-10    # threshold tau of step 2, in units of G_c / eps
+    tol_change: float = 1e-9     # membership changes within this band (G_c/eps units) are ties
 
 
 @dataclass
@@ -188,7 +191,10 @@ def loading_step(st: State, p: float, opts: Options = Options()) -> StepReport:
             rep.rho0 = rho_inf
         rep.history.append(rho_inf)
         rep.changed = int(np.count_nonzero(A != A_prev)) if A_prev is not None else int(A.sum())
-        done = (A_prev is not None and np.array_equal(A, A_prev)
+        band = opts.tol_change * prm.Gc / prm.eps
+        significant = (A_prev is not None
+                       and not np.any((A != A_prev) & (np.abs(ind) > band)))
+        done = (significant
                 and rho_inf <= max(opts.tol_newton * rep.rho0, opts.atol_newton)
                 and last_small) or rep.rho0 == 0.0
         if done or k == opts.max_newton:
