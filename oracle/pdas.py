@@ -25,12 +25,13 @@ phi <= phi_old (Section 2):
        (sparse direct solves; the paper uses GMRES + AMG for this step)
     6. line search: omega = 1, halved while the scaled reduced residual does
        not decrease (at most ``max_halvings`` times)
-  until the active set is unchanged (membership changes of nodes whose
-  indicator is within the band tol_change G_c/eps do not count: with tau > 0
-  such a node is a fixed point both ways), the scaled reduced residual has dropped
+  until the active set is unchanged, the scaled reduced residual has dropped
   by ``tol_newton`` (or below the round-off floor ``atol_newton``; a loading
   step that starts near its solution cannot drop by 1e-10) and the last
-  Newton step was below ``tol_step``.
+  Newton step was below ``tol_step``.  A node whose indicator lies within
+  tol_change G_c/eps of zero is a tie (it meets the complementarity
+  conditions, to that band, as active and as free): its membership changes
+  do not count and its row takes no part in the residual test.
 
 After a converged loading step phi_prev <- phi_old, phi_old <- phi.  The
 extrapolation phi~ (Section 2, "linear extrapolation in time") is read as
@@ -192,10 +193,14 @@ def loading_step(st: State, p: float, opts: Options = Options()) -> StepReport:
         rep.history.append(rho_inf)
         rep.changed = int(np.count_nonzero(A != A_prev)) if A_prev is not None else int(A.sum())
         band = opts.tol_change * prm.Gc / prm.eps
-        significant = (A_prev is not None
-                       and not np.any((A != A_prev) & (np.abs(ind) > band)))
-        done = (significant
-                and rho_inf <= max(opts.tol_newton * rep.rho0, opts.atol_newton)
+        tie = np.abs(ind) <= band
+        unchanged = A_prev is not None and not np.any((A != A_prev) & ~tie)
+        # a tie row meets complementarity as either member: it takes no part in the test
+        rho_stop = rho.copy()
+        rho_stop[nu_dofs:][tie] = 0.0
+        rho_stop_inf = float(np.max(np.abs(rho_stop))) if rho.size else 0.0
+        done = (unchanged
+                and rho_stop_inf <= max(opts.tol_newton * rep.rho0, opts.atol_newton)
                 and last_small) or rep.rho0 == 0.0
         if done or k == opts.max_newton:
             rep.converged = bool(done)
