@@ -85,6 +85,9 @@ typedef struct pff_options {
   double cheb_ratio;    /* Chebyshev smoothing interval [lmax/ratio, 1.1 lmax]; 8 */
   double tol_active;    /* active-set threshold tau, in units of G_c/eps; 1e-10 */
   double atol_newton;   /* absolute floor of the scaled reduced residual test; 1e-14 */
+  double tol_change;    /* the active set counts as unchanged when every index that changed
+                           membership has |indicator| <= tol_change G_c/eps (such an index is
+                           a tie: both memberships satisfy the complementarity test); 1e-9 */
   int reserved[2];
 } pff_options;
 

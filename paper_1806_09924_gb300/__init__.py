@@ -45,7 +45,8 @@ class PffOptions(ctypes.Structure):
         ("max_krylov", ctypes.c_int), ("cheb_degree", ctypes.c_int), ("amg_theta", ctypes.c_double),
         ("amg_coarse_max", ctypes.c_int), ("apply_variant", ctypes.c_int), ("precond", ctypes.c_int),
         ("cheb_ratio", ctypes.c_double), ("tol_active", ctypes.c_double),
-        ("atol_newton", ctypes.c_double), ("reserved", ctypes.c_int * 2),
+        ("atol_newton", ctypes.c_double), ("tol_change", ctypes.c_double),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 

@@ -222,6 +222,7 @@ void pff_default_options(pff_options* o) {
   o->cheb_ratio = 8.0;
   o->tol_active = 1e-10;
   o->atol_newton = 1e-14;
+  o->tol_change = 1e-9;
 }
 
 const char* pff_last_error(void) { return pff::g_msg.c_str(); }
@@ -559,7 +560,7 @@ int pff_active_set_dev(pff_problem* P, double c, uint8_t* active_dev, double* in
   need(P != nullptr, "problem is NULL");
   need(c > 0 && std::isfinite(c), "c must be > 0");
   pff::compute_residual(P, P->u, P->phi, P->F);
-  pff::compute_active_set(P, c, 1e-10, 1 << 30, false);
+  pff::compute_active_set(P, c, 1e-10, 1e-9, 1 << 30, false);
   if (active_dev)
     PFF_CUDA(cudaMemcpyAsync(active_dev, P->active, P->n_nodes, cudaMemcpyDeviceToDevice, P->stream));
   if (indicator_dev)

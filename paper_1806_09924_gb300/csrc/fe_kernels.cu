@@ -728,12 +728,12 @@ __global__ void __launch_bounds__(BLK) k_apply_matfree(MeshDev m, Material mat, 
 __global__ void k_active_set(int64_t n, int dim, const double* __restrict__ F,
                              const double* __restrict__ mass, const double* __restrict__ phi,
                              const double* __restrict__ phi_old, double c, double tau,
-                             int have_prev, int lock_after, uint8_t* __restrict__ raw_prev,
+                             double band, int have_prev, int lock_after, uint8_t* __restrict__ raw_prev,
                              int* __restrict__ toggles, uint8_t* __restrict__ locked,
                              uint8_t* __restrict__ active, double* __restrict__ indicator,
                              int* __restrict__ counters) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  bool A = false, changed = false;
+  bool A = false, changed = false, significant = false;
   if (i < n) {
     const double ind = F[(int64_t)dim * n + i] / mass[i] + c * (phi[i] - phi_old[i]);
     const bool raw = ind > tau;
@@ -745,6 +745,7 @@ __global__ void k_active_set(int64_t n, int dim, const double* __restrict__ F,
       locked[i] = lk;
       A = raw || lk;
       changed = A != (active[i] != 0);
+      significant = changed && fabs(ind) > band;
     } else {
       toggles[i] = 0;
       locked[i] = 0;
@@ -756,10 +757,12 @@ __global__ void k_active_set(int64_t n, int dim, const double* __restrict__ F,
   }
   const unsigned na = __ballot_sync(0xffffffffu, A);
   const unsigned nc = __ballot_sync(0xffffffffu, changed);
+  const unsigned ns = __ballot_sync(0xffffffffu, significant);
   const unsigned nl = __ballot_sync(0xffffffffu, i < n && locked[i]);
   if ((threadIdx.x & 31) == 0) {
     if (na) atomicAdd(&counters[0], __popc(na));
     if (nc) atomicAdd(&counters[1], __popc(nc));
+    if (ns) atomicAdd(&counters[2], __popc(ns));
     if (nl) atomicAdd(&counters[3], __popc(nl));
   }
 }
@@ -1186,12 +1189,13 @@ void launch_apply_matfree(const MeshDev& m, const Material& mat, int64_t n, cons
 }
 
 void launch_active_set(int64_t n, int dim, const double* F, const double* mass, const double* phi,
-                       const double* phi_old, double c, double tau, int have_prev, int lock_after,
+                       const double* phi_old, double c, double tau, double band, int have_prev,
+                       int lock_after,
                        uint8_t* raw_prev, int* toggles, uint8_t* locked, uint8_t* active,
                        double* indicator, int* counters, cudaStream_t s) {
   PFF_CUDA(cudaMemsetAsync(counters, 0, 4 * sizeof(int), s));
   ProfScope ps("active_set", n * (B8 * (indicator ? 5.0 : 4.0) + 14.0), s);
-  k_active_set<<<grid_for(n, 256), 256, 0, s>>>(n, dim, F, mass, phi, phi_old, c, tau, have_prev,
+  k_active_set<<<grid_for(n, 256), 256, 0, s>>>(n, dim, F, mass, phi, phi_old, c, tau, band, have_prev,
                                                 lock_after, raw_prev, toggles, locked, active,
                                                 indicator, counters);
   PFF_LAUNCH("active_set");

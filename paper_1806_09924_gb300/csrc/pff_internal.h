@@ -227,7 +227,8 @@ void launch_apply_matfree(const MeshDev& m, const Material& mat, int64_t n, cons
 // A = {indicator > tau} plus locked indices.  counters[0] = |A|, counters[1] =
 // changes vs. the previous A (if have_prev), counters[3] = locked indices.
 void launch_active_set(int64_t n, int dim, const double* F, const double* mass, const double* phi,
-                       const double* phi_old, double c, double tau, int have_prev, int lock_after,
+                       const double* phi_old, double c, double tau, double band, int have_prev,
+                       int lock_after,
                        uint8_t* raw_prev, int* toggles, uint8_t* locked, uint8_t* active,
                        double* indicator, int* counters, cudaStream_t s);
 
@@ -348,7 +349,8 @@ void begin_loading_step(pff_problem* P, double p);
 int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep);
 void end_loading_step(pff_problem* P);
 void compute_residual(pff_problem* P, const double* u, const double* phi, double* F);
-void compute_active_set(pff_problem* P, double c_rel, double tol_active, int lock_after, bool track);
+void compute_active_set(pff_problem* P, double c_rel, double tol_active, double tol_change,
+                        int lock_after, bool track);
 void assemble_all(pff_problem* P);
 void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse = false);
 void precond_apply(pff_problem* P, const double* r, double* z);

@@ -88,6 +88,13 @@ __global__ void k_count_ties(int64_t n, const double* __restrict__ ind, double t
   if ((threadIdx.x & 31) == 0 && b) atomicAdd(cnt, __popc(b));
 }
 
+// zero the phase-field rows of rho whose indicator lies in the tie band
+__global__ void k_zero_ties(int64_t n, int dim, const double* __restrict__ ind, double band,
+                            double* __restrict__ rho) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n && fabs(ind[i]) <= band) rho[(int64_t)dim * n + i] = 0.0;
+}
+
 void launch_update(cudaStream_t s, int64_t n, int dim, const double* u, const double* phi,
                    const double* phi_old, const uint8_t* active, const double* dU, double omega,
                    double* uo, double* po) {
@@ -152,10 +159,11 @@ void compute_residual(pff_problem* P, const double* u, const double* phi, double
   launch_residual(P->mesh(), P->mat, P->n_nodes, u, phi, P->phit, F, P->stream);
 }
 
-void compute_active_set(pff_problem* P, double c_rel, double tol_active, int lock_after, bool track) {
+void compute_active_set(pff_problem* P, double c_rel, double tol_active, double tol_change,
+                        int lock_after, bool track) {
   const double scale = P->mat.Gc / P->mat.eps;   // indicator constants in units of G_c/eps
   launch_active_set(P->n_nodes, P->dim, P->F, P->mass, P->phi, P->phi_old, c_rel * scale,
-                    tol_active * scale, track ? 1 : 0, lock_after, P->raw_prev, P->toggles,
+                    tol_active * scale, tol_change * scale, track ? 1 : 0, lock_after, P->raw_prev, P->toggles,
                     P->locked, P->active, P->indicator, P->counters, P->stream);
 }
 
@@ -407,6 +415,20 @@ static int count_ties(pff_problem* P, double tau) {
   return P->h_counters[2];
 }
 
+// inf-norm of the scaled reduced residual left in P->tmp by scaled_norms, without the tie rows
+// (a node whose indicator is within the band meets complementarity as active and as free)
+static double stop_norm(pff_problem* P, double band) {
+  const int64_t n = P->n_nodes;
+  count_launch();
+  k_zero_ties<<<grid_for(n, 256), 256, 0, P->stream>>>(n, P->dim, P->indicator, band, P->tmp);
+  PFF_LAUNCH("zero_ties");
+  nrm_inf_dev(P->tmp, P->n_dofs, P->d_scalars, P->partials, P->stream);
+  PFF_CUDA(cudaMemcpyAsync(P->h_scalars, P->d_scalars, sizeof(double), cudaMemcpyDeviceToHost,
+                           P->stream));
+  sync(P);
+  return P->h_scalars[0];
+}
+
 int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep) {
   if (!P->in_step) fail(PFF_ERR_INVALID_ARG, "no loading step in progress (call pff_set_pressure)");
   cudaStream_t s = P->stream;
@@ -416,12 +438,13 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   pff_step_report& R = P->cur;
   // 1-2. residual and active set
   compute_residual(P, P->u, P->phi, P->F);
-  compute_active_set(P, o.c, o.tol_active, o.cycle_lock, P->have_prev);
+  compute_active_set(P, o.c, o.tol_active, o.tol_change, o.cycle_lock, P->have_prev);
   PFF_CUDA(cudaMemcpyAsync(P->h_counters, P->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   double rho_l2 = 0.0;
   const double rho_inf = scaled_norms(P, P->F, &rho_l2);
   const int n_active = P->h_counters[0];
   const int n_changed = P->have_prev ? P->h_counters[1] : n_active;
+  const int n_significant = P->have_prev ? P->h_counters[2] : n_active;
   if (!std::isfinite(rho_inf)) {
     R.status = PFF_ERR_NAN;
     if (rep) *rep = R;
@@ -433,9 +456,10 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   R.changed = n_changed;
   R.locked = P->h_counters[3];
   // 3. stopping test
-  const bool done = (P->have_prev && n_changed == 0 &&
-                     rho_inf <= std::max(o.tol_newton * P->rho0, o.atol_newton) && P->last_small) ||
-                    P->rho0 == 0.0;
+  const double rho_tol = std::max(o.tol_newton * P->rho0, o.atol_newton);
+  bool done = P->rho0 == 0.0;
+  if (!done && P->have_prev && n_significant == 0 && P->last_small)
+    done = rho_inf <= rho_tol || stop_norm(P, o.tol_change * P->mat.Gc / P->mat.eps) <= rho_tol;
   if (done) {
     R.converged = 1;
     R.newton_its = P->k;
@@ -527,10 +551,10 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   }
   if (verbose())
     std::fprintf(stderr,
-                 "[pff] newton k=%d rho=%.3e rho0=%.3e active=%d changed=%d krylov=%d step_u=%.3e "
-                 "step_phi=%.3e small=%d omega=%g\n",
-                 P->k, rho_inf, P->rho0, n_active, n_changed, its, step_u, step_phi, (int)small,
-                 omega);
+                 "[pff] newton k=%d rho=%.3e rho0=%.3e active=%d changed=%d (outside band %d) krylov=%d "
+                 "step_u=%.3e step_phi=%.3e small=%d omega=%g\n",
+                 P->k, rho_inf, P->rho0, n_active, n_changed, n_significant, its, step_u, step_phi,
+                 (int)small, omega);
   std::swap(P->u, P->ut);
   std::swap(P->phi, P->phit_trial);
   P->last_small = small;
