@@ -15,6 +15,7 @@ cpu_baseline / --impl reference = the CPU oracle (oracle/) on a bounded sample
          of the same workload recipe, on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+       [--cells C]   (same recipe at C x C cells: small cases for profiler captures)
 Multi-GPU runs (torchrun) are independent replicas: each rank solves its own
 copy of the workload; value sums the ranks' work over the slowest rank's time.
 """
@@ -201,6 +202,8 @@ def gpu_arm(args, rank, world, local_rank):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
 
     w = W.config(WORKLOAD_INDEX)
+    if args.cells:
+        w = W.scaled_workload(w, args.cells)
     prec = pff.PFF_PREC_MIXED if args.precision == "mixed" else pff.PFF_PREC_FP64
     opts = pff.options(precision=prec)
     stream = torch.cuda.Stream()
@@ -335,7 +338,8 @@ def gpu_arm(args, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64+f32" if prec == pff.PFF_PREC_MIXED else "f64", "data": "synthetic",
-        "config": {"workload": w.name, "n_cells": "1024x1024", "n_dofs": w.n_dofs,
+        "config": {"workload": w.name, "n_cells": "x".join(str(c) for c in w.n_cells),
+                   "n_dofs": w.n_dofs,
                    "loading_steps_per_step": len(pressures), "precision": args.precision,
                    "grading": "geometric from h_min=2e-4, ratio solved to fill [-10,10]",
                    "l2": "working set (state, stencils, AMG, Krylov basis) is several GB, > L2",
@@ -375,6 +379,8 @@ def main():
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cells", type=int, default=0,
+                    help="run the same recipe at this many cells per axis (profiling captures)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -88,7 +88,10 @@ typedef struct pff_options {
   double tol_change;    /* the active set counts as unchanged when every index that changed
                            membership has |indicator| <= tol_change G_c/eps (such an index is
                            a tie: both memberships satisfy the complementarity test); 1e-9 */
-  int reserved[2];
+  int spmv_group;       /* lanes per block row in the AMG hierarchy's block-sparse kernels:
+                           0 = chosen per matrix from its mean row length (default),
+                           4, 8, 16 or 32 = fixed, -1 = one thread per scalar row (reference) */
+  int reserved;
 } pff_options;
 
 /* Per loading step (or per Newton iteration for pff_newton_step) report. */

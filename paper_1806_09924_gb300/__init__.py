@@ -46,7 +46,7 @@ class PffOptions(ctypes.Structure):
         ("amg_coarse_max", ctypes.c_int), ("apply_variant", ctypes.c_int), ("precond", ctypes.c_int),
         ("cheb_ratio", ctypes.c_double), ("tol_active", ctypes.c_double),
         ("atol_newton", ctypes.c_double), ("tol_change", ctypes.c_double),
-        ("reserved", ctypes.c_int * 2),
+        ("spmv_group", ctypes.c_int), ("reserved", ctypes.c_int),
     ]
 
 

@@ -740,44 +740,6 @@ __global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __res
 
 // --------------------------------------------------------------- V-cycle ---
 template <class T>
-__global__ void k_cheb(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
-                       const T* __restrict__ val, const T* __restrict__ dinv,
-                       const T* __restrict__ rhs, const T* __restrict__ xin, T* __restrict__ xout,
-                       T* __restrict__ d, T cd, T cr, int zero_x) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= (int64_t)n * b) return;
-  T s = 0;
-  if (!zero_x) {
-    const int I = (int)(r / b), a = (int)(r % b);
-    for (int k = rp[I]; k < rp[I + 1]; ++k) {
-      const T* v = val + ((int64_t)k * b + a) * b;
-      const T* xx = xin + (int64_t)col[k] * b;
-      for (int c = 0; c < b; ++c) s += v[c] * xx[c];
-    }
-  }
-  const T res = dinv[r] * (rhs[r] - s);
-  const T dn = cd * (zero_x ? T(0) : d[r]) + cr * res;
-  d[r] = dn;
-  xout[r] = (zero_x ? T(0) : xin[r]) + dn;
-}
-
-template <class T>
-__global__ void k_resid(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
-                        const T* __restrict__ val, const T* __restrict__ rhs,
-                        const T* __restrict__ x, T* __restrict__ r) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (int64_t)n * b) return;
-  const int I = (int)(i / b), a = (int)(i % b);
-  T s = 0;
-  for (int k = rp[I]; k < rp[I + 1]; ++k) {
-    const T* v = val + ((int64_t)k * b + a) * b;
-    const T* xx = x + (int64_t)col[k] * b;
-    for (int c = 0; c < b; ++c) s += v[c] * xx[c];
-  }
-  r[i] = rhs[i] - s;
-}
-
-template <class T>
 __global__ void k_dense_mv(int n, const T* __restrict__ M, const T* __restrict__ x, T* __restrict__ y) {
   const int row = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
@@ -794,13 +756,6 @@ __global__ void k_convert(int64_t n, const Tin* __restrict__ a, Tout* __restrict
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (Tout)a[i];
 }
-
-template <class T>
-const T* vals(const Bsr& A);
-template <>
-const double* vals<double>(const Bsr& A) { return A.val; }
-template <>
-const float* vals<float>(const Bsr& A) { return A.valf; }
 
 template <class T>
 const T* dinvs(const AmgLevel& L);
@@ -889,22 +844,14 @@ void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* 
   double rho = 1.0 / sigma;
   const Bsr& A = L.A;
   const int nb = A.nrows, b = A.br;
-  const unsigned g = grid_for((int64_t)nb * b, 256);
   T* cur = x;
   T* nxt = t;
-  // algorithmic bytes of one step: matrix (values, columns, row pointers) once,
-  // plus dinv, rhs, x_in, x_out and d read + write (x_in / d skipped from zero)
-  const double mat_b = (double)A.nnzb * (b * b * (double)sizeof(T) + 4.0) + 4.0 * (nb + 1.0);
-  const double nvec = (double)nb * b * sizeof(T);
-  const char* tag = sizeof(T) == 8 ? "cheb_f64" : "cheb_f32";
   // first step: d = r / theta
   if (L.stencil) {
     launch_stencil_cheb<T>(L.mesh, nb, b, stencil_vals<T>(L), dinvs<T>(L), rhs, cur, nxt, d, 0.0,
                            1.0 / theta, zero_start ? 1 : 0, s);
   } else {
-    ProfScope ps0(tag, (zero_start ? 0.0 : mat_b) + nvec * (zero_start ? 4.0 : 6.0), s);
-    k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
-                                T(0), T(1.0 / theta), zero_start ? 1 : 0);
+    bsr_cheb<T>(A, dinvs<T>(L), rhs, cur, nxt, d, T(0), T(1.0 / theta), zero_start, s);
   }
   std::swap(cur, nxt);
   for (int k = 1; k < degree; ++k) {
@@ -913,9 +860,7 @@ void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* 
       launch_stencil_cheb<T>(L.mesh, nb, b, stencil_vals<T>(L), dinvs<T>(L), rhs, cur, nxt, d,
                              rn * rho, 2.0 * rn / delta, 0, s);
     } else {
-      ProfScope psk(tag, mat_b + 6.0 * nvec, s);
-      k_cheb<T><<<g, 256, 0, s>>>(nb, b, A.rowptr, A.col, vals<T>(A), dinvs<T>(L), rhs, cur, nxt, d,
-                                  T(rn * rho), T(2.0 * rn / delta), 0);
+      bsr_cheb<T>(A, dinvs<T>(L), rhs, cur, nxt, d, T(rn * rho), T(2.0 * rn / delta), false, s);
     }
     std::swap(cur, nxt);
     rho = rn;
@@ -948,11 +893,7 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
   if (L.stencil) {
     launch_stencil_resid<T>(L.mesh, A.nrows, A.br, stencil_vals<T>(L), rhs, x, r, s);
   } else {
-    ProfScope ps(sizeof(T) == 8 ? "resid_f64" : "resid_f32",
-                 (double)A.nnzb * (A.br * A.bc * (double)sizeof(T) + 4.0) + 4.0 * (A.nrows + 1.0) +
-                     3.0 * sizeof(T) * (double)A.nrows * A.br, s);
-    k_resid<T><<<grid_for((int64_t)A.nrows * A.br, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr,
-                                                                      A.col, vals<T>(A), rhs, x, r);
+    bsr_resid<T>(A, rhs, x, r, s);
   }
   const bool last = l + 1 == (int)amg.lev.size();
   T* cb = last ? reinterpret_cast<T*>(amg.cb) : reinterpret_cast<T*>(amg.lev[l + 1].b);
@@ -1433,6 +1374,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
   dfree(sc.red);
   cudaFreeHost(sc.h_err);
   cudaFreeHost(sc.h_red);
+  for (auto& L : amg.lev) L.A.group = L.P.group = L.R.group = prm.spmv_group;
   amg.built = 1;
   if (verbose()) {
     std::fprintf(stderr, "[pff] AMG (%s): %zu levels + coarse %d\n", amg.mixed ? "fp32" : "fp64",

@@ -199,6 +199,26 @@ std::vector<std::pair<int, double>> columns(const std::vector<double>& X, double
 
 }  // namespace
 
+extern "C" void pff_default_options(pff_options* o);
+
+namespace {
+// defaults overridden by the caller's options, checked
+pff_options resolve_options(const pff_options* opts) {
+  pff_options o;
+  pff_default_options(&o);
+  if (opts) o = *opts;
+  need(o.precision == PFF_PREC_FP64 || o.precision == PFF_PREC_MIXED, "unknown precision");
+  need(o.krylov_restart >= 1 && o.max_krylov >= 1, "krylov_restart and max_krylov must be >= 1");
+  need(o.cheb_degree >= 1, "cheb_degree must be >= 1");
+  need(o.max_newton >= 0 && o.max_halvings >= 0, "negative iteration limit");
+  need(o.tol_change >= 0.0 && o.tol_active >= 0.0, "negative active-set band");
+  need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 4 || o.spmv_group == 8 ||
+           o.spmv_group == 16 || o.spmv_group == 32,
+       "spmv_group must be 0, -1, 4, 8, 16 or 32");
+  return o;
+}
+}  // namespace
+
 extern "C" {
 
 void pff_default_options(pff_options* o) {
@@ -408,9 +428,7 @@ int pff_newton_step(pff_problem* P, const pff_options* opts, pff_step_report* re
   API_BEGIN
   need(P != nullptr, "problem is NULL");
   pff::AllocStream alloc_scope(P->stream);
-  pff_options o;
-  pff_default_options(&o);
-  if (opts) o = *opts;
+  const pff_options o = resolve_options(opts);
   if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
     P->apply_variant = o.apply_variant;
   const int rc = pff::newton_iteration(P, o, rep);
@@ -434,9 +452,7 @@ int pff_solve_loading_steps(pff_problem* P, int n_steps, const double* p_schedul
   need(P != nullptr, "problem is NULL");
   pff::AllocStream alloc_scope(P->stream);
   need(n_steps >= 0 && (n_steps == 0 || p_schedule != nullptr), "bad schedule");
-  pff_options o;
-  pff_default_options(&o);
-  if (opts) o = *opts;
+  const pff_options o = resolve_options(opts);
   if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
     P->apply_variant = o.apply_variant;
   int rc_all = PFF_OK;
@@ -591,9 +607,7 @@ int pff_precond_setup(pff_problem* P, const pff_options* opts) {
   need(P != nullptr, "problem is NULL");
   pff::AllocStream alloc_scope(P->stream);
   need(P->phi_assembled, "call pff_assemble first");
-  pff_options o;
-  pff_default_options(&o);
-  if (opts) o = *opts;
+  const pff_options o = resolve_options(opts);
   P->amg_u_valid = false;
   pff::precond_setup(P, o);
   sync(P);
@@ -616,9 +630,7 @@ int pff_linear_solve_dev(pff_problem* P, const pff_options* opts, const double* 
   need(P != nullptr && b_dev && x_dev, "NULL argument");
   pff::AllocStream alloc_scope(P->stream);
   need(P->phi_assembled, "call pff_assemble first");
-  pff_options o;
-  pff_default_options(&o);
-  if (opts) o = *opts;
+  const pff_options o = resolve_options(opts);
   if (o.precond == PFF_PC_AMG) need(P->amg_u.built && P->amg_p.built, "call pff_precond_setup first");
   if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
     P->apply_variant = o.apply_variant;

@@ -153,23 +153,6 @@ __global__ void k_scan_add(int* __restrict__ out, int n, const int* __restrict__
   if (i == 0) out[n] = *total;
 }
 
-// ------------------------------------------------------------------ SpMV ---
-template <class T>
-__global__ void k_bsr_spmv(int nrows, int br, int bc, const int* __restrict__ rowptr,
-                           const int* __restrict__ col, const T* __restrict__ val,
-                           const T* __restrict__ x, T* __restrict__ y, T alpha, T beta) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= (int64_t)nrows * br) return;
-  const int I = (int)(r / br), a = (int)(r % br);
-  T s = 0;
-  for (int k = rowptr[I]; k < rowptr[I + 1]; ++k) {
-    const T* v = val + ((int64_t)k * br + a) * bc;
-    const T* xx = x + (int64_t)col[k] * bc;
-    for (int c = 0; c < bc; ++c) s += v[c] * xx[c];
-  }
-  y[r] = beta == T(0) ? alpha * s : alpha * s + beta * y[r];
-}
-
 }  // namespace
 
 void dot_dev(const double* x, const double* y, int64_t n, double* out, double* partials,
@@ -236,29 +219,6 @@ void exclusive_scan_int(const int* in, int* out, int n, int* total_host, cudaStr
   }
   PFF_CUDA(cudaStreamSynchronize(s));
   dfree(bsum);
-}
-
-double bsr_bytes(const Bsr& A, int elem, bool beta) {
-  return (double)A.nnzb * (A.br * A.bc * (double)elem + 4.0) + 4.0 * (A.nrows + 1.0) +
-         (double)elem * ((double)A.ncols * A.bc + (double)A.nrows * A.br * (beta ? 2.0 : 1.0));
-}
-
-void bsr_spmv(const Bsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s) {
-  const int64_t rows = (int64_t)A.nrows * A.br;
-  if (rows == 0) return;
-  ProfScope ps("spmv_f64", bsr_bytes(A, 8, beta != 0.0), s);
-  k_bsr_spmv<double><<<grid_for(rows, 256), 256, 0, s>>>(A.nrows, A.br, A.bc, A.rowptr, A.col,
-                                                         A.val, x, y, alpha, beta);
-  PFF_LAUNCH("bsr_spmv");
-}
-
-void bsr_spmv_f(const Bsr& A, const float* x, float* y, float alpha, float beta, cudaStream_t s) {
-  const int64_t rows = (int64_t)A.nrows * A.br;
-  if (rows == 0) return;
-  ProfScope ps("spmv_f32", bsr_bytes(A, 4, beta != 0.0f), s);
-  k_bsr_spmv<float><<<grid_for(rows, 256), 256, 0, s>>>(A.nrows, A.br, A.bc, A.rowptr, A.col,
-                                                        A.valf, x, y, alpha, beta);
-  PFF_LAUNCH("bsr_spmv_f");
 }
 
 void Bsr::release() {

@@ -109,6 +109,8 @@ struct Bsr {
   int* col = nullptr;         // nnzb, sorted within a row
   double* val = nullptr;      // nnzb * br * bc, block row-major
   float* valf = nullptr;      // FP32 copy (mixed precision)
+  int group = 0;              // lanes per block row of the vector kernels: 0 = by row length,
+                              // 4..32 = fixed, -1 = one thread per scalar row (reference)
   void release();
 };
 
@@ -161,6 +163,7 @@ struct AmgParams {
   int coord_dim = 0;
   double mdrop = 1e-3;
   bool use_graph = true;
+  int spmv_group = 0;         // Bsr::group of every level's A, P and R
 };
 
 // Build a hierarchy for the block matrix A (FP64 values, block size br) with
@@ -188,6 +191,14 @@ enum { RED_PARTIALS = 1024 };   // partial buffer length needed by the reduction
 // BSR SpMV y = alpha A x + beta y (FP64 or FP32 values / vectors)
 void bsr_spmv(const Bsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
 void bsr_spmv_f(const Bsr& A, const float* x, float* y, float alpha, float beta, cudaStream_t s);
+// r = rhs - A x (square blocks)
+template <class T>
+void bsr_resid(const Bsr& A, const T* rhs, const T* x, T* r, cudaStream_t s);
+// one Chebyshev step: d = cd d + cr dinv (rhs - A xin); xout = xin + d (zero_x: xin = d = 0)
+template <class T>
+void bsr_cheb(const Bsr& A, const T* dinv, const T* rhs, const T* xin, T* xout, T* d, T cd, T cr,
+              bool zero_x, cudaStream_t s);
+int bsr_group(const Bsr& A);
 
 // ------------------------------------------------------------ FE kernels ---
 struct Material {

@@ -201,6 +201,7 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   ap.coords = P->xyz;
   ap.coord_dim = P->dim;
   ap.mixed = o.precision == PFF_PREC_MIXED;
+  ap.spmv_group = o.spmv_group;
   const auto m = P->mesh();
   const int64_t n = P->n_nodes;
   const int ns = n_slots(P->dim);
