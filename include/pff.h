@@ -89,8 +89,9 @@ typedef struct pff_options {
                            membership has |indicator| <= tol_change G_c/eps (such an index is
                            a tie: both memberships satisfy the complementarity test); 1e-9 */
   int spmv_group;       /* lanes per block row in the AMG hierarchy's block-sparse kernels:
-                           0 = chosen per matrix from its mean row length (default),
-                           4, 8, 16 or 32 = fixed, -1 = one thread per scalar row (reference) */
+                           0 = timed per matrix at hierarchy build (default; the choice is
+                           cached per block shape and size class), 1, 2, 4, 8, 16 or 32 =
+                           fixed, -1 = one thread per scalar row (reference) */
   int reserved;
 } pff_options;
 

@@ -1374,7 +1374,16 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
   dfree(sc.red);
   cudaFreeHost(sc.h_err);
   cudaFreeHost(sc.h_red);
-  for (auto& L : amg.lev) L.A.group = L.P.group = L.R.group = prm.spmv_group;
+  for (auto& L : amg.lev) {
+    L.A.group = L.P.group = L.R.group = prm.spmv_group;
+    if (prm.spmv_group == 0) {
+      // the finest operator is applied through its stencil when L.stencil is set;
+      // its BSR copy is timed all the same (it is cheap and rarely used)
+      bsr_autotune(L.A, amg.mixed, s);
+      bsr_autotune(L.P, amg.mixed, s);
+      bsr_autotune(L.R, amg.mixed, s);
+    }
+  }
   amg.built = 1;
   if (verbose()) {
     std::fprintf(stderr, "[pff] AMG (%s): %zu levels + coarse %d\n", amg.mixed ? "fp32" : "fp64",

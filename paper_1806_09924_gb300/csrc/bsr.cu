@@ -3,16 +3,22 @@
 // and restrictions are block-sparse).
 //
 // A group of G lanes (G | 32) works on one block row.  Per pass the group
-// takes G consecutive blocks of the row: their values, which are contiguous in
-// memory, are read by the whole group with unit stride into shared memory, and
-// lane j then multiplies block j with its gathered x block.  The G partial row
-// sums are combined with xor shuffles inside the group, and lanes 0..BR-1 run
-// the epilogue of the block row's BR scalar rows:
+// takes G consecutive blocks of the row: for G >= 4 their values, which are
+// contiguous in memory, are read by the whole group with unit stride into
+// shared memory, and lane j then multiplies block j with its gathered x block
+// (G = 1, 2 suit rows of one or two blocks: each lane reads its own blocks).
+// The G partial row sums are combined with xor shuffles inside the group, and
+// lanes 0..BR-1 run the epilogue of the block row's BR scalar rows:
 //   OP_SPMV   y = alpha A x + beta y
 //   OP_RESID  y = rhs - A x
 //   OP_CHEB   one Chebyshev step: d = cd d + cr D^-1 (rhs - A x); xout = x + d
 // The row-per-thread kernels (one scalar row per thread, uncoalesced value
 // reads) stay available as the reference variant (Bsr::group = -1).
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "pff_internal.h"
 
 namespace pff {
@@ -42,7 +48,8 @@ __global__ void __launch_bounds__(threads_for(BR * BC))
   constexpr int BB = BR * BC;
   constexpr int NT = threads_for(BB);
   constexpr int NG = NT / G;
-  __shared__ T sv[BB > 1 ? NT * BB : 1];
+  constexpr bool STAGE = BB > 1 && G >= 4;
+  __shared__ T sv[STAGE ? NT * BB : 1];
   const int grp = threadIdx.x / G, lane = threadIdx.x % G;
   const unsigned gmask = G == 32 ? 0xffffffffu
                                  : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
@@ -56,10 +63,10 @@ __global__ void __launch_bounds__(threads_for(BR * BC))
     k0 = p.rp[I];
     k1 = p.rp[I + 1];
   }
-  T* my = sv + (BB > 1 ? grp * G * BB : 0);
+  T* my = sv + (STAGE ? grp * G * BB : 0);
   for (int kb = k0; kb < k1; kb += G) {   // trip count is uniform within a group
     const int nb = min(G, k1 - kb);
-    if constexpr (BB > 1) {
+    if constexpr (STAGE) {
       const T* src = p.val + (int64_t)kb * BB;
       for (int e = lane; e < nb * BB; e += G) my[e] = src[e];
       __syncwarp(gmask);
@@ -70,13 +77,13 @@ __global__ void __launch_bounds__(threads_for(BR * BC))
       T xv[BC];
 #pragma unroll
       for (int cc = 0; cc < BC; ++cc) xv[cc] = xx[cc];
-      const T* v = BB > 1 ? my + lane * BB : p.val + kb + lane;
+      const T* v = STAGE ? my + lane * BB : p.val + (int64_t)(kb + lane) * BB;
 #pragma unroll
       for (int a = 0; a < BR; ++a)
 #pragma unroll
         for (int cc = 0; cc < BC; ++cc) s[a] += v[a * BC + cc] * xv[cc];
     }
-    if constexpr (BB > 1) __syncwarp(gmask);
+    if constexpr (STAGE) __syncwarp(gmask);
   }
   // every lane of the warp reaches the shuffles (no early return above)
 #pragma unroll
@@ -106,6 +113,8 @@ bool launch_g(int G, const VecArgs<T>& a, cudaStream_t s) {
   constexpr int NT = threads_for(BR * BC);
   const unsigned grid = (unsigned)((a.nrows + NT / G - 1) / (NT / G));
   switch (G) {
+    case 1: k_bsr_vec<T, BR, BC, 1, OP><<<grid, NT, 0, s>>>(a); return true;
+    case 2: k_bsr_vec<T, BR, BC, 2, OP><<<grid, NT, 0, s>>>(a); return true;
     case 4: k_bsr_vec<T, BR, BC, 4, OP><<<grid, NT, 0, s>>>(a); return true;
     case 8: k_bsr_vec<T, BR, BC, 8, OP><<<grid, NT, 0, s>>>(a); return true;
     case 16: k_bsr_vec<T, BR, BC, 16, OP><<<grid, NT, 0, s>>>(a); return true;
@@ -198,6 +207,67 @@ const T* values(const Bsr& A) {
 }
 
 }  // namespace
+
+// ------------------------------------------------------------ autotune ---
+// The lane-group width of each hierarchy matrix is picked by timing every
+// candidate on that matrix once; the winner is remembered per (element size,
+// block shape, log2 rows, half-log2 mean row length), so the hierarchies
+// rebuilt at later loading steps reuse it without timing.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tune;
+
+template <class T>
+int tune_one(const Bsr& A, cudaStream_t s) {
+  const double avg = A.nrows > 0 ? (double)A.nnzb / A.nrows : 1.0;
+  const auto key = std::make_tuple((int)sizeof(T), A.br * 10 + A.bc,
+                                   (int)std::floor(std::log2(std::max(1, A.nrows))),
+                                   (int)std::lround(2.0 * std::log2(std::max(1.0, avg))), 0);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) return it->second;
+  }
+  const int64_t nx = (int64_t)A.ncols * A.bc, ny = (int64_t)A.nrows * A.br;
+  T* x = dalloc<T>(nx);
+  T* y = dalloc<T>(ny);
+  PFF_CUDA(cudaMemsetAsync(x, 0, sizeof(T) * nx, s));
+  cudaEvent_t e0, e1;
+  PFF_CUDA(cudaEventCreate(&e0));
+  PFF_CUDA(cudaEventCreate(&e1));
+  VecArgs<T> a{A.nrows, A.rowptr, A.col, values<T>(A), x, y, nullptr, nullptr, nullptr, T(1), T(0)};
+  int best = 4;
+  float best_ms = 1e30f;
+  for (int G : {1, 2, 4, 8, 16, 32}) {
+    count_launch(4);
+    if (!launch_shape<T, OP_SPMV>(A.br, A.bc, G, a, s)) break;   // shape without vector kernels
+    PFF_CUDA(cudaEventRecord(e0, s));
+    for (int r = 0; r < 3; ++r) launch_shape<T, OP_SPMV>(A.br, A.bc, G, a, s);
+    PFF_CUDA(cudaEventRecord(e1, s));
+    PFF_CUDA(cudaEventSynchronize(e1));
+    PFF_LAUNCH("spmv autotune");
+    float ms = 0.f;
+    PFF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = G;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  PFF_CUDA(cudaStreamSynchronize(s));
+  dfree(x);
+  dfree(y);
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = best;
+  return best;
+}
+}  // namespace
+
+void bsr_autotune(Bsr& A, bool f32, cudaStream_t s) {
+  if (A.nrows == 0 || A.nnzb == 0) return;
+  A.group = f32 ? tune_one<float>(A, s) : tune_one<double>(A, s);
+}
 
 int bsr_group(const Bsr& A) {
   if (A.group != 0) return A.group;

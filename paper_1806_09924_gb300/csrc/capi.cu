@@ -144,6 +144,7 @@ void release(pff_problem* P) {
   for (double* p : dbl) dfree(p);
   dfree(P->Kuu_f);
   dfree(P->Kpp_f);
+  dfree(P->gs_part);
   dfree(P->active);
   dfree(P->active_prev);
   dfree(P->raw_prev);
@@ -212,9 +213,9 @@ pff_options resolve_options(const pff_options* opts) {
   need(o.cheb_degree >= 1, "cheb_degree must be >= 1");
   need(o.max_newton >= 0 && o.max_halvings >= 0, "negative iteration limit");
   need(o.tol_change >= 0.0 && o.tol_active >= 0.0, "negative active-set band");
-  need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 4 || o.spmv_group == 8 ||
-           o.spmv_group == 16 || o.spmv_group == 32,
-       "spmv_group must be 0, -1, 4, 8, 16 or 32");
+  need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 1 || o.spmv_group == 2 ||
+           o.spmv_group == 4 || o.spmv_group == 8 || o.spmv_group == 16 || o.spmv_group == 32,
+       "spmv_group must be 0, -1, 1, 2, 4, 8, 16 or 32");
   return o;
 }
 }  // namespace

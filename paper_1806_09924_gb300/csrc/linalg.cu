@@ -115,6 +115,118 @@ __global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int nv,
   w[i] += sign * a;
 }
 
+// ------------------------------------------------ Gram-Schmidt (mixed) ---
+// GB300 executes FP64 arithmetic at a small fraction of its FP32 rate, which
+// puts an FP64 multiply-add per streamed double below the HBM roofline.  The
+// mixed-precision Krylov path therefore takes its projection coefficients and
+// norms from an FP32 view of the FP64 data (the high word re-biased with
+// integer operations), and keeps FP64 arithmetic only for the update
+// w <- w - V h, whose coefficients h are the ones stored in the Hessenberg
+// matrix, so the Arnoldi relation holds to FP64 rounding.
+
+// FP32 view of a double from its high word: sign, exponent re-biased, 20 mantissa
+// bits (relative error < 2^-20).  |x| < 2^-126 gives 0, |x| >= 2^128 gives inf.
+__device__ __forceinline__ float f32_view(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x);
+  const unsigned a = hw & 0x7fffffffu;
+  unsigned f = a >= (1151u << 20) ? 0x7f800000u : ((a - (896u << 20)) << 3);
+  f = a >= (897u << 20) ? f : 0u;
+  return __uint_as_float(f | (hw & 0x80000000u));
+}
+
+template <int K>
+__device__ __forceinline__ void block_sum_f(float (&v)[K], float (*sh)[K]) {
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+#pragma unroll
+  for (int c = 0; c < K; ++c) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[c] += __shfl_down_sync(0xffffffffu, v[c], o);
+    if (l == 0) sh[w][c] = v[c];
+  }
+  __syncthreads();
+  if (threadIdx.x < K) {
+    float r = 0.f;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) r += sh[i][threadIdx.x];
+    v[0] = r;   // thread c holds the block sum of value c
+  }
+  __syncthreads();
+}
+
+constexpr int GS_CH = 8;
+
+// block b owns rows [b R, b R + R): it stages the FP32 view of w there in shared
+// memory, then sweeps the basis vectors GS_CH at a time.
+// part[k g + b] = block partial of <V_k, w> (k < nv); part[nv g + b] = of ||w||^2
+__global__ void __launch_bounds__(RB) k_gs_dot(const double* __restrict__ V, int64_t ld, int nv,
+                                                const double* __restrict__ w, int64_t n, int R,
+                                                float* __restrict__ part) {
+  extern __shared__ float swf[];
+  __shared__ float red[RB / 32][GS_CH];
+  const int g = gridDim.x, b = blockIdx.x;
+  const int64_t r0 = (int64_t)b * R;
+  const int len = (int)std::max<int64_t>(0, std::min<int64_t>(R, n - r0));
+  float nrm[GS_CH] = {};
+  for (int i = threadIdx.x; i < len; i += RB) {
+    const float f = f32_view(w[r0 + i]);
+    swf[i] = f;
+    nrm[0] += f * f;
+  }
+  block_sum_f<GS_CH>(nrm, red);   // also orders the shared-memory stores before the reads
+  if (threadIdx.x == 0) part[(int64_t)nv * g + b] = nrm[0];
+  for (int k0 = 0; k0 < nv; k0 += GS_CH) {
+    float acc[GS_CH] = {};
+    const double* Vk = V + (int64_t)k0 * ld + r0;
+    const int kc = min(GS_CH, nv - k0);
+    for (int i = threadIdx.x; i < len; i += RB) {
+      const float wf = swf[i];
+#pragma unroll
+      for (int c = 0; c < GS_CH; ++c)
+        if (c < kc) acc[c] += f32_view(Vk[(int64_t)c * ld + i]) * wf;
+    }
+    block_sum_f<GS_CH>(acc, red);
+    if (threadIdx.x < kc) part[(int64_t)(k0 + threadIdx.x) * g + b] = acc[0];
+  }
+}
+
+// w <- w - sum_k h_k V_k in FP64; part[b] = block partial of ||w_new||^2 (FP32 view)
+__global__ void __launch_bounds__(RB) k_gs_axpy(const double* __restrict__ V, int64_t ld, int nv,
+                                                 const double* __restrict__ h, double* __restrict__ w,
+                                                 int64_t n, float* __restrict__ part) {
+  __shared__ double sh[64];
+  __shared__ float red[RB / 32][1];
+  if (threadIdx.x < nv) sh[threadIdx.x] = h[threadIdx.x];
+  __syncthreads();
+  float nrm[1] = {0.f};
+  for (int64_t i = (int64_t)blockIdx.x * RB + threadIdx.x; i < n; i += (int64_t)gridDim.x * RB) {
+    double a = w[i];
+    int k = 0;
+    for (; k + 4 <= nv; k += 4) {
+      const double v0 = V[(int64_t)k * ld + i], v1 = V[(int64_t)(k + 1) * ld + i];
+      const double v2 = V[(int64_t)(k + 2) * ld + i], v3 = V[(int64_t)(k + 3) * ld + i];
+      a = fma(-sh[k], v0, a);
+      a = fma(-sh[k + 1], v1, a);
+      a = fma(-sh[k + 2], v2, a);
+      a = fma(-sh[k + 3], v3, a);
+    }
+    for (; k < nv; ++k) a = fma(-sh[k], V[(int64_t)k * ld + i], a);
+    w[i] = a;
+    const float f = f32_view(a);
+    nrm[0] += f * f;
+  }
+  block_sum_f<1>(nrm, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = nrm[0];
+}
+
+// out[b] = sum of the g FP32 partials of row b, accumulated in FP64
+__global__ void k_gs_final(const float* __restrict__ part, int g, double* __restrict__ out) {
+  __shared__ double sh[32];
+  const float* p = part + (int64_t)blockIdx.x * g;
+  double a = 0.0;
+  for (int k = threadIdx.x; k < g; k += blockDim.x) a += (double)p[k];
+  a = block_sum(a, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = a;
+}
+
 // -------------------------------------------------------------------- scan --
 constexpr int SB = 1024;
 
@@ -202,6 +314,48 @@ void multi_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double
   ProfScope ps("multi_axpy", 8.0 * n * (nv + 2.0), s);
   k_multi_axpy<<<grid_for(n, 256), 256, 0, s>>>(V, ld, nv, h, w, n, sign);
   PFF_LAUNCH("multi_axpy");
+}
+
+int sm_count() {
+  static int n = 0;
+  if (n == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0)
+      n = 132;
+  }
+  return n;
+}
+
+int gs_grid(int64_t n, int* rows_per_block) {
+  // eight resident blocks per SM, more when a block's rows would overflow the
+  // staging buffer (GS_MAX_ROWS floats of shared memory)
+  int64_t g = std::max<int64_t>(8LL * sm_count(), (n + GS_MAX_ROWS - 1) / GS_MAX_ROWS);
+  g = std::max<int64_t>(1, std::min<int64_t>(g, n));
+  *rows_per_block = (int)((n + g - 1) / g);
+  return (int)((n + *rows_per_block - 1) / *rows_per_block);
+}
+
+void gs_dot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, float* part,
+                double* out, cudaStream_t s) {
+  int R = 0;
+  const int g = gs_grid(n, &R);
+  if (R > GS_MAX_ROWS || g > GS_MAX_BLOCKS || nv > 64)
+    fail(PFF_ERR_INVALID_ARG, "mixed Gram-Schmidt: system or basis too large");
+  ProfScope ps("gs_dot", 8.0 * n * (nv + 1.0), s, 2);
+  k_gs_dot<<<g, RB, sizeof(float) * R, s>>>(V, ld, nv, w, n, R, part);
+  k_gs_final<<<nv + 1, RB, 0, s>>>(part, g, out);
+  PFF_LAUNCH("gs_dot");
+}
+
+void gs_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n,
+                 float* part, double* nrm2, cudaStream_t s) {
+  if (nv > 64) fail(PFF_ERR_INVALID_ARG, "mixed Gram-Schmidt: basis too large");
+  const int g = (int)std::min<int64_t>(8LL * sm_count(), std::max<int64_t>(1, (n + RB - 1) / RB));
+  ProfScope ps("gs_axpy", 8.0 * n * (nv + 2.0), s, 2);
+  k_gs_axpy<<<g, RB, 0, s>>>(V, ld, nv, h, w, n, part);
+  k_gs_final<<<1, RB, 0, s>>>(part, g, nrm2);
+  PFF_LAUNCH("gs_axpy");
 }
 
 void exclusive_scan_int(const int* in, int* out, int n, int* total_host, cudaStream_t s) {

@@ -110,7 +110,7 @@ struct Bsr {
   double* val = nullptr;      // nnzb * br * bc, block row-major
   float* valf = nullptr;      // FP32 copy (mixed precision)
   int group = 0;              // lanes per block row of the vector kernels: 0 = by row length,
-                              // 4..32 = fixed, -1 = one thread per scalar row (reference)
+                              // 1..32 = fixed, -1 = one thread per scalar row (reference)
   void release();
 };
 
@@ -182,11 +182,21 @@ void nrm_inf_dev(const double* x, int64_t n, double* out, double* partials, cuda
 void multidot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* out,
                   double* partials, cudaStream_t s);
 // w -= sum_k h[k] V_k   (h on device)
+// Gram-Schmidt with FP32-view coefficients (mixed precision): out[k] = <V_k, w>
+// (k < nv), out[nv] = ||w||^2; part holds (nv + 1) * GS_MAX_BLOCKS floats
+void gs_dot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, float* part,
+                double* out, cudaStream_t s);
+// w <- w - V h in FP64; *nrm2 = ||w_new||^2 (FP32 view); part holds GS_MAX_BLOCKS floats
+void gs_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n,
+                 float* part, double* nrm2, cudaStream_t s);
+int sm_count();
 void multi_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n,
                     double sign, cudaStream_t s);
 void exclusive_scan_int(const int* in, int* out, int n, int* total_host, cudaStream_t s);
 
 enum { RED_PARTIALS = 1024 };   // partial buffer length needed by the reductions
+// mixed-precision Gram-Schmidt: rows staged per block, blocks per pass
+enum { GS_MAX_ROWS = 8192, GS_MAX_BLOCKS = 4096 };
 
 // BSR SpMV y = alpha A x + beta y (FP64 or FP32 values / vectors)
 void bsr_spmv(const Bsr& A, const double* x, double* y, double alpha, double beta, cudaStream_t s);
@@ -199,6 +209,9 @@ template <class T>
 void bsr_cheb(const Bsr& A, const T* dinv, const T* rhs, const T* xin, T* xout, T* d, T cd, T cr,
               bool zero_x, cudaStream_t s);
 int bsr_group(const Bsr& A);
+// time the lane-group widths of the vector kernels on A (FP32 or FP64 values)
+// and store the fastest in A.group (cached per matrix class)
+void bsr_autotune(Bsr& A, bool f32, cudaStream_t s);
 
 // ------------------------------------------------------------ FE kernels ---
 struct Material {
@@ -330,6 +343,7 @@ struct pff_problem {
   // Krylov workspace
   int krylov_m = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *tmp = nullptr;
+  float* gs_part = nullptr;   // partial sums of the mixed-precision Gram-Schmidt
   double* h_host = nullptr;
 
   // Newton step state

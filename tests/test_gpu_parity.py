@@ -286,7 +286,7 @@ def test_block_sparse_kernel_variants_agree(dim, shape, seed, precision):
     rng = np.random.default_rng(seed)
     r = torch.tensor(rng.standard_normal(P.n_dofs), device="cuda")
     out = {}
-    for g in (-1, 0, 4, 8, 16, 32):
+    for g in (-1, 0, 1, 2, 4, 8, 16, 32):
         # a small coarse level gives several block-sparse levels on these meshes
         P.precond_setup(pff.options(precision=prec, spmv_group=g, amg_coarse_max=24))
         z = torch.empty_like(r)
@@ -294,19 +294,24 @@ def test_block_sparse_kernel_variants_agree(dim, shape, seed, precision):
         torch.cuda.synchronize()
         out[g] = z.cpu().numpy()
     tol = 1e-12 if precision == "fp64" else 1e-5
-    for g in (0, 4, 8, 16, 32):
+    for g in (0, 1, 2, 4, 8, 16, 32):
         assert rel(out[g], out[-1]) <= tol, (g, rel(out[g], out[-1]))
     with pytest.raises(RuntimeError):
         P.precond_setup(pff.options(spmv_group=3))
     P.close()
 
 
-def test_linear_solve_matches_direct_solve():
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_linear_solve_matches_direct_solve(precision):
+    """FGMRES to 1e-12 against a sparse direct solve of the reduced system; in
+    mixed precision the preconditioner runs in FP32 and the Gram-Schmidt
+    coefficients come from FP32 views, the Arnoldi update stays FP64."""
     P, mesh, prm, state = make_case(2, (30, 26), 41, p=1e-3)
     act = torch.empty(mesh.n_nodes, dtype=torch.uint8, device="cuda")
     P.active_set_dev(1.0, act, None)
     P.assemble()
-    opts = pff.options(tol_linear=1e-12)
+    prec = pff.PFF_PREC_FP64 if precision == "fp64" else pff.PFF_PREC_MIXED
+    opts = pff.options(tol_linear=1e-12, precision=prec, krylov_restart=20)
     P.precond_setup(opts)
     a = act.cpu().numpy().astype(bool)
     d, n = 2, mesh.n_nodes
