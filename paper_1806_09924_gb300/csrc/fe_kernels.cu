@@ -859,9 +859,51 @@ __global__ void k_rigid_modes(MeshDev m, int64_t n, double* __restrict__ B) {
 
 // ------------------------------------------- stencil smoother (AMG level 0) --
 // The finest AMG level of each block is the assembled node stencil itself
-// (Kuu with B = d, Kpp with B = 1, slot-major).  One Chebyshev step, fused with
-// the operator apply:  res = dinv .* (rhs - K x_in),  d = cd d + cr res,
-// x_out = x_in + d.  With zero_x the iterate starts at 0 (no apply).
+// (Kuu with B = d, Kpp with B = 1, slot-major).  acc = K x over the 3^D
+// neighbours of node i, without branches: a neighbour outside the mesh is
+// replaced by node i itself and its product selected away, so every load is
+// in bounds and independent of the others, and all of them can be in flight
+// together (node indices fit in 32 bits).
+template <class T, int D, int B>
+__device__ __forceinline__ void stencil_apply(const MeshDev& m, int64_t n, int i,
+                                              const T* __restrict__ K, const T* __restrict__ x,
+                                              T (&acc)[B]) {
+  constexpr int NS = D == 2 ? 9 : 27;
+  const int n0 = m.nn[0], n1 = m.nn[1];
+  const int ix = i % n0;
+  const int r = i / n0;
+  const int iy = D == 2 ? r : r % n1;
+  const int iz = D == 2 ? 0 : r / n1;
+  const bool lo[3] = {ix > 0, iy > 0, iz > 0};
+  const bool hi[3] = {ix < n0 - 1, iy < n1 - 1, D == 3 && iz < m.nn[2] - 1};
+#pragma unroll
+  for (int a = 0; a < B; ++a) acc[a] = T(0);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = D == 3 ? s / 9 - 1 : 0;
+    const bool ok = (ox < 0 ? lo[0] : ox > 0 ? hi[0] : true) &&
+                    (oy < 0 ? lo[1] : oy > 0 ? hi[1] : true) &&
+                    (oz < 0 ? lo[2] : oz > 0 ? hi[2] : true);
+    const int j = ok ? i + ox + oy * n0 + oz * n0 * n1 : i;
+    T xj[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const T v = x[(int64_t)j * B + c];
+      xj[c] = ok ? v : T(0);
+    }
+#pragma unroll
+    for (int a = 0; a < B; ++a)
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const T k = K[((int64_t)(s * B + a) * B + c) * n + i];
+        acc[a] += (ok ? k : T(0)) * xj[c];
+      }
+  }
+}
+
+// One Chebyshev step fused with the operator apply:
+// res = dinv .* (rhs - K x_in),  d = cd d + cr res,  x_out = x_in + d.
+// With zero_x the iterate starts at 0 (no apply).
 template <class T, int D, int B>
 __global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
                                                       const T* __restrict__ K,
@@ -870,31 +912,18 @@ __global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
                                                       const T* __restrict__ xin,
                                                       T* __restrict__ xout, T* __restrict__ d,
                                                       T cd, T cr, int zero_x) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  constexpr int NS = D == 2 ? 9 : 27;
   T acc[B];
+  if (zero_x) {
 #pragma unroll
-  for (int a = 0; a < B; ++a) acc[a] = T(0);
-  if (!zero_x) {
-    int idx[3];
-    node_index<D>(i, m, idx);
-#pragma unroll
-    for (int s = 0; s < NS; ++s) {
-      const int64_t j = neighbour<D>(idx, s, m);
-      if (j < 0) continue;
-      T xj[B];
-#pragma unroll
-      for (int c = 0; c < B; ++c) xj[c] = xin[j * B + c];
-#pragma unroll
-      for (int a = 0; a < B; ++a)
-#pragma unroll
-        for (int c = 0; c < B; ++c) acc[a] += K[((int64_t)(s * B + a) * B + c) * n + i] * xj[c];
-    }
+    for (int a = 0; a < B; ++a) acc[a] = T(0);
+  } else {
+    stencil_apply<T, D, B>(m, n, i, K, xin, acc);
   }
 #pragma unroll
   for (int a = 0; a < B; ++a) {
-    const int64_t r = i * B + a;
+    const int64_t r = (int64_t)i * B + a;
     const T res = dinv[r] * (rhs[r] - acc[a]);
     const T dn = (zero_x ? T(0) : cd * d[r]) + cr * res;
     d[r] = dn;
@@ -909,28 +938,12 @@ __global__ void __launch_bounds__(256) k_stencil_resid(MeshDev m, int64_t n,
                                                        const T* __restrict__ rhs,
                                                        const T* __restrict__ x,
                                                        T* __restrict__ r) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  constexpr int NS = D == 2 ? 9 : 27;
-  int idx[3];
-  node_index<D>(i, m, idx);
   T acc[B];
+  stencil_apply<T, D, B>(m, n, i, K, x, acc);
 #pragma unroll
-  for (int a = 0; a < B; ++a) acc[a] = T(0);
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const int64_t j = neighbour<D>(idx, s, m);
-    if (j < 0) continue;
-    T xj[B];
-#pragma unroll
-    for (int c = 0; c < B; ++c) xj[c] = x[j * B + c];
-#pragma unroll
-    for (int a = 0; a < B; ++a)
-#pragma unroll
-      for (int c = 0; c < B; ++c) acc[a] += K[((int64_t)(s * B + a) * B + c) * n + i] * xj[c];
-  }
-#pragma unroll
-  for (int a = 0; a < B; ++a) r[i * B + a] = rhs[i * B + a] - acc[a];
+  for (int a = 0; a < B; ++a) r[(int64_t)i * B + a] = rhs[(int64_t)i * B + a] - acc[a];
 }
 
 // inverse diagonal of a node stencil (block size B, centre slot c0)

@@ -228,12 +228,12 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     P->amg_u_valid = true;
   }
   // Phase-field block: rebuild at the start of a loading step and whenever the
-  // active set moved by more than 1 % of the nodes (or every 5 iterations);
+  // active set moved by more than 0.1 % of the nodes (or every 5 iterations);
   // otherwise keep the hierarchy and refresh only the finest level's stencil
   // values and diagonal.  FGMRES converges to its tolerance either way: a
   // stale coarse space costs iterations, not accuracy.
   const bool rebuild = !allow_reuse || !P->amg_p.built || P->amg_p.mixed != ap.mixed || P->k == 0 ||
-                       P->phi_amg_changes > n / 100 || P->phi_amg_age >= 5 || P->amg_p.lev.empty();
+                       P->phi_amg_changes > n / 1000 || P->phi_amg_age >= 5 || P->amg_p.lev.empty();
   if (rebuild) {
     ProfScope ps("amg_setup_phi", 0.0, P->stream, 0);
     launch_stencil_to_bsr(m, n, 1, P->Kpp, P->App, P->stream);
