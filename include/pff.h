@@ -92,7 +92,11 @@ typedef struct pff_options {
                            0 = timed per matrix at hierarchy build (default; the choice is
                            cached per block shape and size class), 1, 2, 4, 8, 16 or 32 =
                            fixed, -1 = one thread per scalar row (reference) */
-  int reserved;
+  int amg_reuse;        /* 1: a displacement hierarchy carries over to the next loading step
+                           while phi~ moved by at most amg_reuse_tol (max norm) since its
+                           build; 0: rebuilt every loading step; 1 */
+  double amg_reuse_tol; /* see amg_reuse; 0.05 */
+  int reserved[2];
 } pff_options;
 
 /* Per loading step (or per Newton iteration for pff_newton_step) report. */
@@ -110,6 +114,8 @@ typedef struct pff_step_report {
   double rho0;          /* scaled reduced residual (inf-norm) at the first iteration */
   double rho;           /* ... at the last iteration */
   double time_ms;       /* wall time of the step */
+  int amg_builds_u;     /* displacement hierarchies built during the step (0: carried over) */
+  int amg_builds_phi;   /* phase-field hierarchies built during the step */
 } pff_step_report;
 
 void pff_default_options(pff_options* opts);

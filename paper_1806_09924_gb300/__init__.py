@@ -46,7 +46,8 @@ class PffOptions(ctypes.Structure):
         ("amg_coarse_max", ctypes.c_int), ("apply_variant", ctypes.c_int), ("precond", ctypes.c_int),
         ("cheb_ratio", ctypes.c_double), ("tol_active", ctypes.c_double),
         ("atol_newton", ctypes.c_double), ("tol_change", ctypes.c_double),
-        ("spmv_group", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("spmv_group", ctypes.c_int), ("amg_reuse", ctypes.c_int), ("amg_reuse_tol", ctypes.c_double),
+        ("reserved", ctypes.c_int * 2),
     ]
 
 
@@ -56,7 +57,7 @@ class PffStepReport(ctypes.Structure):
         ("krylov_its", ctypes.c_int), ("krylov_its_max", ctypes.c_int), ("active", ctypes.c_int),
         ("changed", ctypes.c_int), ("locked", ctypes.c_int), ("ties", ctypes.c_int),
         ("linesearch_fails", ctypes.c_int), ("rho0", ctypes.c_double), ("rho", ctypes.c_double),
-        ("time_ms", ctypes.c_double),
+        ("time_ms", ctypes.c_double), ("amg_builds_u", ctypes.c_int), ("amg_builds_phi", ctypes.c_int),
     ]
 
     def as_dict(self):

@@ -24,6 +24,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <memory>
 
 #include "pff_internal.h"
 
@@ -700,26 +701,37 @@ __global__ void k_dinv_spmv(int n, int b, const int* __restrict__ rp, const int*
 }
 
 // y = D^-1/2 A D^-1/2 x (D = scalar diagonal, dinv = 1/D or 0)
-__global__ void k_sym_spmv(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
-                           const double* __restrict__ val, const double* __restrict__ dinv,
-                           const double* __restrict__ x, double* __restrict__ y) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= (int64_t)n * b) return;
-  const int I = (int)(r / b), a = (int)(r % b);
-  double s = 0.0;
-  for (int k = rp[I]; k < rp[I + 1]; ++k) {
-    const double* v = val + ((int64_t)k * b + a) * b;
-    const int64_t j0 = (int64_t)col[k] * b;
-    for (int c = 0; c < b; ++c) s += v[c] * sqrt(dinv[j0 + c]) * x[j0 + c];
-  }
-  y[r] = sqrt(dinv[r]) * s;
-}
-
-// Lanczos three-term update w -= alpha v + beta v_prev
-__global__ void k_lanczos(int64_t n, double* __restrict__ w, const double* __restrict__ v,
-                          const double* __restrict__ vp, double alpha, double beta) {
+// Lanczos recurrence on S = D^-1/2 A D^-1/2 with every scalar kept on the device:
+// al[j] = <S v_j, v_j>, nb2[j] = ||w_j||^2, beta_j = sqrt(nb2[j])
+__global__ void k_lz_sqrt(int64_t n, const double* __restrict__ dinv, double* __restrict__ dh) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) w[i] -= alpha * v[i] + beta * vp[i];
+  if (i < n) dh[i] = sqrt(dinv[i]);
+}
+// w = dh .* y
+__global__ void k_lz_scale(int64_t n, const double* __restrict__ dh, const double* __restrict__ y,
+                           double* __restrict__ w) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) w[i] = dh[i] * y[i];
+}
+// w -= al[j] v + beta_{j-1} vp   (no vp term at j = 0)
+__global__ void k_lz_orth(int64_t n, double* __restrict__ w, const double* __restrict__ v,
+                          const double* __restrict__ vp, const double* __restrict__ al,
+                          const double* __restrict__ nb2, int j) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double beta = j > 0 ? sqrt(fmax(nb2[j - 1], 0.0)) : 0.0;
+  w[i] -= al[j] * v[i] + (j > 0 ? beta * vp[i] : 0.0);
+}
+// v_next = w / ||w|| (0 after a breakdown), t = dh .* v_next
+__global__ void k_lz_next(int64_t n, const double* __restrict__ w, const double* __restrict__ nb2,
+                          int j, const double* __restrict__ dh, double* __restrict__ vn,
+                          double* __restrict__ t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double q = nb2[j] > 0.0 ? 1.0 / sqrt(nb2[j]) : 0.0;
+  const double x = w[i] * q;
+  vn[i] = x;
+  t[i] = dh[i] * x;
 }
 
 __global__ void k_hash_vec(int64_t n, double* __restrict__ x) {
@@ -946,48 +958,55 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
 // on the clustered spectra of graded meshes.
 double estimate_lmax(const Bsr& A, const double* dinv, cudaStream_t s, double* partials,
                      double* dred, double* hred) {
+  (void)hred;
   const int64_t n = (int64_t)A.nrows * A.br;
+  const int steps = (int)std::min<int64_t>(30, n);
+  const unsigned g = grid_for(n, 256);
   double* v = dalloc<double>(n);
   double* vp = dalloc<double>(n);
   double* w = dalloc<double>(n);
+  double* t = dalloc<double>(n);
+  double* y = dalloc<double>(n);
+  double* dh = dalloc<double>(n);
+  double* al = dalloc<double>(2 * steps);
+  double* nb2 = al + steps;
   PFF_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * n, s));
-  count_launch();
-  k_hash_vec<<<grid_for(n, 256), 256, 0, s>>>(n, v);
-  dot_dev(v, v, n, dred, partials, s);
-  count_launch();
-  k_scale<<<grid_for(n, 256), 256, 0, s>>>(n, v, dred);
-  std::vector<double> al, be;
-  double beta = 0.0;
-  const int steps = (int)std::min<int64_t>(30, n);
+  count_launch(3);
+  k_lz_sqrt<<<g, 256, 0, s>>>(n, dinv, dh);
+  k_hash_vec<<<g, 256, 0, s>>>(n, w);
+  dot_dev(w, w, n, dred, partials, s);
+  k_lz_next<<<g, 256, 0, s>>>(n, w, dred, 0, dh, v, t);   // v_0 = w / ||w||, t = dh .* v_0
   for (int j = 0; j < steps; ++j) {
-    count_launch();
-    k_sym_spmv<<<grid_for(n, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr, A.col, A.val, dinv, v, w);
-    dot_dev(w, v, n, dred, partials, s);
-    PFF_CUDA(cudaMemcpyAsync(hred, dred, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PFF_CUDA(cudaStreamSynchronize(s));
-    const double alpha = *hred;
-    al.push_back(alpha);
-    count_launch();
-    k_lanczos<<<grid_for(n, 256), 256, 0, s>>>(n, w, v, vp, alpha, beta);
-    dot_dev(w, w, n, dred, partials, s);
-    PFF_CUDA(cudaMemcpyAsync(hred, dred, sizeof(double), cudaMemcpyDeviceToHost, s));
-    PFF_CUDA(cudaStreamSynchronize(s));
-    const double bn = std::sqrt(std::max(*hred, 0.0));
-    if (!(bn > 1e-14 * std::fabs(alpha)) || j + 1 == steps) break;
-    be.push_back(bn);
-    std::swap(vp, v);    // v_prev <- v
-    count_launch();
-    k_scale<<<grid_for(n, 256), 256, 0, s>>>(n, w, dred);   // w / ||w||
-    std::swap(v, w);     // v <- w / ||w||
-    beta = bn;
+    bsr_spmv(A, t, y, 1.0, 0.0, s);                        // y = A D^-1/2 v_j
+    count_launch(3);
+    k_lz_scale<<<g, 256, 0, s>>>(n, dh, y, w);             // w = S v_j
+    dot_dev(w, v, n, al + j, partials, s);
+    k_lz_orth<<<g, 256, 0, s>>>(n, w, v, vp, al, nb2, j);
+    dot_dev(w, w, n, nb2 + j, partials, s);
+    k_lz_next<<<g, 256, 0, s>>>(n, w, nb2, j, dh, vp, t);  // v_{j+1} into the v_{j-1} buffer
+    std::swap(v, vp);
   }
-  be.resize(al.size() > 0 ? al.size() - 1 : 0);
-  const double lam = al.empty() ? 1.0 : tridiag_max_eig(al, be);
+  std::vector<double> h(2 * steps);
+  PFF_CUDA(cudaMemcpyAsync(h.data(), al, sizeof(double) * 2 * steps, cudaMemcpyDeviceToHost, s));
+  PFF_CUDA(cudaStreamSynchronize(s));
+  PFF_LAUNCH("lmax");
+  // tridiagonal T_m up to the first breakdown (beta_j ~ 0: invariant subspace found)
+  std::vector<double> a, b;
+  for (int j = 0; j < steps; ++j) {
+    a.push_back(h[j]);
+    const double bn = std::sqrt(std::max(h[steps + j], 0.0));
+    if (!(bn > 1e-14 * std::fabs(h[j])) || j + 1 == steps) break;
+    b.push_back(bn);
+  }
+  const double lam = a.empty() ? 1.0 : tridiag_max_eig(a, b);
   dfree(v);
   dfree(vp);
   dfree(w);
-  PFF_LAUNCH("lmax");
-  return lam > 0.0 ? lam : 1.0;
+  dfree(t);
+  dfree(y);
+  dfree(dh);
+  dfree(al);
+  return std::isfinite(lam) && lam > 0.0 ? lam : 1.0;
 }
 
 // C = X * Y (BSR)
@@ -1107,8 +1126,22 @@ void Amg::release() {
   built = 0;
 }
 
+// named set-up phase for the per-kernel profile (no kernels of its own)
+struct Phase {
+  std::unique_ptr<ProfScope> p;
+  cudaStream_t s;
+  explicit Phase(cudaStream_t st) : s(st) {}
+  void start(const char* name) {
+    p.reset();
+    p.reset(new ProfScope(name, 0.0, s, 0));
+  }
+  void stop() { p.reset(); }
+};
+
 void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgParams& prm,
                cudaStream_t s) {
+  Phase ph(s);
+  ph.start("setup_copy");
   amg.release();
   amg.mixed = prm.mixed;
   amg.cheb_degree = prm.cheb_degree;
@@ -1140,6 +1173,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     const bool too_big = n > 8 * prm.coarse_max;
     if (n <= prm.coarse_max || (level >= prm.max_levels && !too_big)) {
       // coarsest level: dense inverse
+      ph.start("setup_coarse_inverse");
       amg.nc = n;
       double* Dm = dalloc<double>((size_t)n * n);
       amg.cinv = dalloc<double>((size_t)n * n);
@@ -1161,6 +1195,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
       A.release();
       break;
     }
+    ph.start("setup_strength");
     AmgLevel L;
     L.A = A;   // takes ownership
     L.n = n;
@@ -1190,6 +1225,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     k_symmetrize<<<grid_for(nb, 256), 256, 0, s>>>(nb, A.rowptr, A.col, s0, strong);
     PFF_LAUNCH("strength");
     // MIS(2)
+    ph.start("setup_mis2");
     int* state = dalloc<int>(nb);
     uint8_t* iso = dalloc<uint8_t>(nb);
     unsigned long long* M1 = dalloc<unsigned long long>(nb);
@@ -1214,6 +1250,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
       if (rounds > 200) fail(PFF_ERR_CAPACITY, "AMG MIS(2) did not terminate");
     }
     // aggregates
+    ph.start("setup_aggregate");
     int* flag = dalloc<int>(nb + 1);
     int* rootid = dalloc<int>(nb + 1);
     count_launch();
@@ -1276,6 +1313,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     count_launch();
     k_sort_segments<<<grid_for(nagg, 128), 128, 0, s>>>(nagg, off, members, nullptr);
     // tentative prolongator + coarse near-null space
+    ph.start("setup_tentative");
     double* Qn = dalloc<double>((size_t)nb * br * nns);
     double* Bc = dalloc<double>((size_t)nagg * nns * nns);
     count_launch();
@@ -1292,7 +1330,9 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
       PFF_LAUNCH("centroids");
     }
     // smoothed prolongator
+    ph.start("setup_lmax");
     L.lmax = estimate_lmax(L.A, L.dinv, s, partials, sc.red, sc.h_red);
+    ph.start("setup_prolongator");
     const double omega = 4.0 / (3.0 * L.lmax);
     Bsr& P = L.P;
     P.nrows = nb;
@@ -1315,6 +1355,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     check_err(sc, s, "prolongator");
     transpose(P, L.R, s);
     // Galerkin product
+    ph.start("setup_galerkin");
     Bsr AP, Ac;
     spgemm(L.A, P, AP, sc.err, s);
     spgemm(L.R, AP, Ac, sc.err, s);
@@ -1324,6 +1365,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     PFF_LAUNCH("fix_diag");
     AP.release();
     // work vectors and FP32 copies
+    ph.start("setup_vectors");
     L.x = dalloc<double>(n);
     L.b = dalloc<double>(n);
     L.r = dalloc<double>(n);
@@ -1374,6 +1416,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
   dfree(sc.red);
   cudaFreeHost(sc.h_err);
   cudaFreeHost(sc.h_red);
+  ph.start("setup_autotune");
   for (auto& L : amg.lev) {
     L.A.group = L.P.group = L.R.group = prm.spmv_group;
     if (prm.spmv_group == 0) {
@@ -1384,6 +1427,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
       bsr_autotune(L.R, amg.mixed, s);
     }
   }
+  ph.stop();
   amg.built = 1;
   if (verbose()) {
     std::fprintf(stderr, "[pff] AMG (%s): %zu levels + coarse %d\n", amg.mixed ? "fp32" : "fp64",

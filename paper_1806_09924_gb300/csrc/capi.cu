@@ -145,6 +145,7 @@ void release(pff_problem* P) {
   dfree(P->Kuu_f);
   dfree(P->Kpp_f);
   dfree(P->gs_part);
+  dfree(P->phit_built);
   dfree(P->active);
   dfree(P->active_prev);
   dfree(P->raw_prev);
@@ -213,6 +214,7 @@ pff_options resolve_options(const pff_options* opts) {
   need(o.cheb_degree >= 1, "cheb_degree must be >= 1");
   need(o.max_newton >= 0 && o.max_halvings >= 0, "negative iteration limit");
   need(o.tol_change >= 0.0 && o.tol_active >= 0.0, "negative active-set band");
+  need(o.amg_reuse_tol >= 0.0, "negative amg_reuse_tol");
   need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 1 || o.spmv_group == 2 ||
            o.spmv_group == 4 || o.spmv_group == 8 || o.spmv_group == 16 || o.spmv_group == 32,
        "spmv_group must be 0, -1, 1, 2, 4, 8, 16 or 32");
@@ -244,6 +246,8 @@ void pff_default_options(pff_options* o) {
   o->tol_active = 1e-10;
   o->atol_newton = 1e-14;
   o->tol_change = 1e-9;
+  o->amg_reuse = 1;
+  o->amg_reuse_tol = 0.05;
 }
 
 const char* pff_last_error(void) { return pff::g_msg.c_str(); }

@@ -334,7 +334,10 @@ struct pff_problem {
   double* Bu = nullptr;   // rigid-body modes
   double* Bp = nullptr;   // constants
   pff::Amg amg_u, amg_p;
-  bool amg_u_valid = false;
+  bool amg_u_valid = false;      // false: the displacement hierarchy must be rebuilt
+  bool amg_u_check = false;      // a new loading step: compare phi~ with phit_built
+  double* phit_built = nullptr;  // phi~ the displacement hierarchy was built from
+  int amg_u_age = 0;             // loading steps the displacement hierarchy was reused for
   // the phase-field hierarchy is reused while the active set barely moves
   int64_t phi_amg_changes = 0;   // active-set changes since the last build
   int phi_amg_age = 0;           // Newton iterations since the last build

@@ -192,6 +192,26 @@ void apply_jacobian(pff_problem* P, int variant, const double* x, double* y, con
   }
 }
 
+__global__ void k_abs_diff(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
+                           double* __restrict__ out) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = fabs(a[i] - b[i]);
+}
+
+// max_i |a_i - b_i| (device vectors of length n <= n_dofs)
+static double max_abs_diff(pff_problem* P, const double* a, const double* b, int64_t n) {
+  double* t = P->tmp ? P->tmp : dalloc<double>(n);
+  count_launch();
+  k_abs_diff<<<grid_for(n, 256), 256, 0, P->stream>>>(n, a, b, t);
+  PFF_LAUNCH("abs_diff");
+  nrm_inf_dev(t, n, P->d_scalars, P->partials, P->stream);
+  PFF_CUDA(cudaMemcpyAsync(P->h_scalars, P->d_scalars, sizeof(double), cudaMemcpyDeviceToHost,
+                           P->stream));
+  PFF_CUDA(cudaStreamSynchronize(P->stream));
+  if (!P->tmp) dfree(t);
+  return P->h_scalars[0];
+}
+
 void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   P->precision = o.precision;
   if (o.precond == PFF_PC_JACOBI) return;
@@ -220,12 +240,42 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
       L0.stf = Kf;
     }
   };
-  if (!P->amg_u_valid || P->amg_u.mixed != ap.mixed) {
+  // Displacement block: M_uu depends on phi~ alone, and the aggregates on the
+  // node coordinates alone.  A hierarchy carries over to the next loading step
+  // while phi~ moved by at most amg_reuse_tol at every node (and for at most
+  // 8 loading steps); the finest level then smooths on the new stencil with
+  // its new diagonal, the coarse levels keep the Galerkin operators of the
+  // build.  FGMRES is flexible, so a stale coarse space costs iterations only.
+  bool reuse_u = P->amg_u_valid && P->amg_u.mixed == ap.mixed && !P->amg_u.lev.empty();
+  if (reuse_u && P->amg_u_check) {
+    reuse_u = o.amg_reuse != 0 && P->phit_built != nullptr && P->amg_u_age < 8;
+    if (reuse_u) {
+      const double dphi = max_abs_diff(P, P->phit, P->phit_built, n);
+      reuse_u = dphi <= o.amg_reuse_tol;
+      if (verbose())
+        std::fprintf(stderr, "[pff] phi~ moved by %.3e since the displacement AMG build: %s\n",
+                     dphi, reuse_u ? "reuse" : "rebuild");
+    }
+    if (reuse_u) {
+      AmgLevel& L0 = P->amg_u.lev[0];
+      launch_stencil_dinv(m, n, P->dim, P->Kuu, L0.dinv, ap.mixed ? L0.dinvf : nullptr, P->stream);
+      use_stencil(P->amg_u, P->Kuu, P->Kuu_f, (int64_t)ns * P->dim * P->dim * n);
+      P->amg_u_age += 1;
+    }
+    P->amg_u_check = false;
+  }
+  if (!reuse_u) {
     ProfScope ps("amg_setup_u", 0.0, P->stream, 0);   // wall time of the build (syncs inside)
     launch_stencil_to_bsr(m, n, P->dim, P->Kuu, P->Auu, P->stream);
     amg_build(P->amg_u, P->Auu, P->Bu, P->dim == 2 ? 3 : 6, ap, P->stream);
     use_stencil(P->amg_u, P->Kuu, P->Kuu_f, (int64_t)ns * P->dim * P->dim * n);
+    if (!P->phit_built) P->phit_built = dalloc<double>(n);
+    PFF_CUDA(cudaMemcpyAsync(P->phit_built, P->phit, sizeof(double) * n, cudaMemcpyDeviceToDevice,
+                             P->stream));
+    P->amg_u_age = 0;
+    P->amg_u_check = false;
     P->amg_u_valid = true;
+    P->cur.amg_builds_u += 1;
   }
   // Phase-field block: rebuild at the start of a loading step and whenever the
   // active set moved by more than 0.1 % of the nodes (or every 5 iterations);
@@ -238,6 +288,7 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     ProfScope ps("amg_setup_phi", 0.0, P->stream, 0);
     launch_stencil_to_bsr(m, n, 1, P->Kpp, P->App, P->stream);
     amg_build(P->amg_p, P->App, P->Bp, 1, ap, P->stream);
+    P->cur.amg_builds_phi += 1;
     P->phi_amg_changes = 0;
     P->phi_amg_age = 0;
   } else {
@@ -409,7 +460,7 @@ void begin_loading_step(pff_problem* P, double p) {
                    P->stream);
   P->uu_assembled = false;
   P->phi_assembled = false;
-  P->amg_u_valid = false;
+  P->amg_u_check = true;   // the displacement hierarchy may carry over (precond_setup decides)
   // M_uu and S depend on phi~ only
   launch_assemble_uu(P->mesh(), P->mat, P->n_nodes, P->phit, P->Kuu, P->stream);
   launch_scaling(P->mesh(), P->mat, P->n_nodes, P->Kuu, P->S, P->Sinv, P->stream);

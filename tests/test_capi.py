@@ -41,19 +41,32 @@ def test_binding_declares_every_symbol():
 
 
 def test_struct_layout_matches_header(tmp_path):
+    """Every field of the binding's structs sits at the header's offset."""
     import paper_1806_09924_gb300 as pff
+    structs = {"pff_options": pff.PffOptions, "pff_step_report": pff.PffStepReport}
+    lines = []
+    for cname, cls in structs.items():
+        lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
+        for f, _ in cls._fields_:
+            lines.append(f'printf("{cname} {f} %zu\\n", offsetof({cname}, {f}));')
     src = tmp_path / "sz.c"
-    src.write_text('#include "pff.h"\n#include <stdio.h>\n#include <stddef.h>\n'
-                   'int main(void){printf("%zu %zu %zu %zu\\n", sizeof(pff_options), sizeof(pff_step_report),'
-                   ' offsetof(pff_options, precond), offsetof(pff_step_report, time_ms));return 0;}\n')
+    src.write_text('#include "pff.h"\n#include <stdio.h>\n#include <stddef.h>\nint main(void){'
+                   + "".join(lines) + "return 0;}\n")
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
-    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()
-    so, sr, off_pc, off_t = map(int, out)
-    assert so == ctypes.sizeof(pff.PffOptions)
-    assert sr == ctypes.sizeof(pff.PffStepReport)
-    assert off_pc == pff.PffOptions.precond.offset
-    assert off_t == pff.PffStepReport.time_ms.offset
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    seen = 0
+    for line in out:
+        if not line.strip():
+            continue
+        cname, field, value = line.split()
+        cls = structs[cname]
+        if field == "size":
+            assert int(value) == ctypes.sizeof(cls), cname
+        else:
+            assert int(value) == getattr(cls, field).offset, (cname, field)
+        seen += 1
+    assert seen == sum(len(c._fields_) + 1 for c in structs.values())
 
 
 def test_defaults_and_argument_errors_without_gpu(lib):
@@ -62,6 +75,7 @@ def test_defaults_and_argument_errors_without_gpu(lib):
     assert o.tol_linear == 1e-8 and o.c == 0.1 and o.amg_theta == 0.25 and o.precision == pff.PFF_PREC_FP64
     assert o.tol_active == 1e-10 and o.tol_change == 1e-9 and o.atol_newton == 1e-14
     assert o.krylov_restart == 40 and o.max_newton == 50
+    assert o.spmv_group == 0 and o.amg_reuse == 1 and o.amg_reuse_tol == 0.05
     h = ctypes.c_void_p()
     nc = (ctypes.c_int32 * 3)(4, 4, 4)
     # invalid dimension is rejected before any device work

@@ -212,6 +212,24 @@ def test_graded_ramp_parity(precision):
     P.close()
 
 
+def test_hierarchy_reuse_across_loading_steps():
+    """A displacement hierarchy carried over between loading steps (phi~ barely
+    moves in the ramp) changes the preconditioner, not the converged solution."""
+    w = W.scaled_workload(W.config(1), 96)
+    out = {}
+    for reuse in (0, 1):
+        P = pff.problem_from_workload(w)
+        reps = P.solve_loading_steps(w.pressures, pff.options(precision=1, amg_reuse=reuse))
+        assert all(r["converged"] == 1 for r in reps)
+        u, phi, act = P.get_solution()
+        out[reuse] = (u, phi, act, [r["amg_builds_u"] for r in reps])
+        P.close()
+    assert out[0][3] == [1] * len(w.pressures)
+    assert out[1][3][0] == 1 and sum(out[1][3]) < len(w.pressures)
+    assert rel(out[1][0], out[0][0]) <= 1e-9
+    assert rel(out[1][1], out[0][1]) <= 1e-9
+
+
 def test_newton_solution_parity_3d():
     w = W.scaled_workload(W.config(2), 12)
     mesh, st, oreps = _oracle_solution(w, [1e-3])
