@@ -88,10 +88,12 @@ typedef struct pff_options {
   double tol_change;    /* the active set counts as unchanged when every index that changed
                            membership has |indicator| <= tol_change G_c/eps (such an index is
                            a tie: both memberships satisfy the complementarity test); 1e-9 */
-  int spmv_group;       /* lanes per block row in the AMG hierarchy's block-sparse kernels:
+  int spmv_group;       /* block-sparse kernel of the AMG hierarchy: lanes per block row of
+                           the vector-CSR kernels, 1, 2, 4, 8, 16 or 32; 64 = SELL-32 layout
+                           (one thread per block row, FP32 hierarchies; FP64 ones fall back
+                           to vector-CSR); -1 = one thread per scalar row (reference);
                            0 = timed per matrix at hierarchy build (default; the choice is
-                           cached per block shape and size class), 1, 2, 4, 8, 16 or 32 =
-                           fixed, -1 = one thread per scalar row (reference) */
+                           cached per block shape and size class) */
   int amg_reuse;        /* 1: a displacement hierarchy carries over to the next loading step
                            while phi~ moved by at most amg_reuse_tol (max norm) since its
                            build; 0: rebuilt every loading step; 1 */

@@ -1419,6 +1419,11 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
   ph.start("setup_autotune");
   for (auto& L : amg.lev) {
     L.A.group = L.P.group = L.R.group = prm.spmv_group;
+    if (prm.spmv_group == BSR_SELL && amg.mixed) {
+      bsr_make_sell(L.A, s);
+      bsr_make_sell(L.P, s);
+      bsr_make_sell(L.R, s);
+    }
     if (prm.spmv_group == 0) {
       // the finest operator is applied through its stencil when L.stencil is set;
       // its BSR copy is timed all the same (it is cheap and rarely used)

@@ -12,9 +12,16 @@
 //   OP_SPMV   y = alpha A x + beta y
 //   OP_RESID  y = rhs - A x
 //   OP_CHEB   one Chebyshev step: d = cd d + cr D^-1 (rhs - A x); xout = x + d
-// The row-per-thread kernels (one scalar row per thread, uncoalesced value
-// reads) stay available as the reference variant (Bsr::group = -1).
+// The SELL-32 kernels keep one thread per block row: the blocks of 32
+// consecutive rows are stored entry-major (block k of the 32 rows, then block
+// k + 1, ...), so every value and column load of a warp reads 128 contiguous
+// bytes, and no shuffles or staging are needed; a row shorter than its slice's
+// longest row simply stops early (the padding is never read).
+// The row-per-thread kernels on the plain BSR arrays (one scalar row per
+// thread, uncoalesced value reads) stay available as the reference variant
+// (Bsr::group = -1).
 #include <cmath>
+#include <cstdio>
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -144,6 +151,107 @@ bool launch_shape(int br, int bc, int G, const VecArgs<T>& a, cudaStream_t s) {
   }
 }
 
+// ------------------------------------------------------------ SELL-32 ---
+struct SellArgs {
+  int nrows;
+  const int* __restrict__ rp;     // BSR row pointers: the row lengths
+  const int* __restrict__ off;    // slice offsets (entry columns)
+  const int* __restrict__ scol;
+  const float* __restrict__ sval;
+  const float* __restrict__ x;
+  float* y;
+  const float* __restrict__ rhs;
+  const float* __restrict__ dinv;
+  float* d;
+  float alpha, beta;
+};
+
+template <int BR, int BC, int OP>
+__global__ void __launch_bounds__(256) k_sell(SellArgs p) {
+  constexpr int BB = BR * BC;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= p.nrows) return;
+  const int l = row & 31;
+  const int64_t base = p.off[row >> 5];
+  const int len = p.rp[row + 1] - p.rp[row];
+  const int* cp = p.scol + base * 32 + l;
+  const float* vp = p.sval + base * BB * 32 + l;
+  float s[BR];
+#pragma unroll
+  for (int a = 0; a < BR; ++a) s[a] = 0.f;
+#pragma unroll 2
+  for (int k = 0; k < len; ++k) {
+    const int c = cp[k * 32];
+    float xv[BC];
+#pragma unroll
+    for (int cc = 0; cc < BC; ++cc) xv[cc] = p.x[(int64_t)c * BC + cc];
+#pragma unroll
+    for (int a = 0; a < BR; ++a)
+#pragma unroll
+      for (int cc = 0; cc < BC; ++cc) s[a] += vp[(k * BB + a * BC + cc) * 32] * xv[cc];
+  }
+#pragma unroll
+  for (int a = 0; a < BR; ++a) {
+    const int64_t r = (int64_t)row * BR + a;
+    if constexpr (OP == OP_SPMV) {
+      p.y[r] = p.beta == 0.f ? p.alpha * s[a] : p.alpha * s[a] + p.beta * p.y[r];
+    } else if constexpr (OP == OP_RESID) {
+      p.y[r] = p.rhs[r] - s[a];
+    } else {
+      const float res = p.dinv[r] * (p.rhs[r] - s[a]);
+      const float dn = p.alpha * p.d[r] + p.beta * res;
+      p.d[r] = dn;
+      p.y[r] = p.x[r] + dn;
+    }
+  }
+}
+
+template <int OP>
+bool launch_sell(int br, int bc, const SellArgs& a, cudaStream_t s) {
+  const unsigned grid = (unsigned)((a.nrows + 255) / 256);
+  const int key = br * 10 + bc;
+  if constexpr (OP == OP_SPMV) {
+    switch (key) {
+      case 23: k_sell<2, 3, OP><<<grid, 256, 0, s>>>(a); return true;
+      case 32: k_sell<3, 2, OP><<<grid, 256, 0, s>>>(a); return true;
+      case 36: k_sell<3, 6, OP><<<grid, 256, 0, s>>>(a); return true;
+      case 63: k_sell<6, 3, OP><<<grid, 256, 0, s>>>(a); return true;
+      default: break;
+    }
+  }
+  switch (key) {
+    case 11: k_sell<1, 1, OP><<<grid, 256, 0, s>>>(a); return true;
+    case 22: k_sell<2, 2, OP><<<grid, 256, 0, s>>>(a); return true;
+    case 33: k_sell<3, 3, OP><<<grid, 256, 0, s>>>(a); return true;
+    case 66: k_sell<6, 6, OP><<<grid, 256, 0, s>>>(a); return true;
+    default: return false;
+  }
+}
+
+// longest row of each slice of 32 block rows
+__global__ void k_sell_len(int nrows, const int* __restrict__ rp, int* __restrict__ len) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  const int l = row < nrows ? rp[row + 1] - rp[row] : 0;
+  const int m = __reduce_max_sync(0xffffffffu, l);
+  if ((threadIdx.x & 31) == 0 && row < nrows) len[row >> 5] = m;
+}
+
+__global__ void k_sell_fill(int nrows, int bb, const int* __restrict__ rp,
+                            const int* __restrict__ col, const double* __restrict__ val,
+                            const int* __restrict__ off, int* __restrict__ scol,
+                            float* __restrict__ sval) {
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= nrows) return;
+  const int l = row & 31;
+  const int64_t base = off[row >> 5];
+  const int k0 = rp[row], len = rp[row + 1] - k0;
+  for (int k = 0; k < len; ++k) {
+    scol[(base + k) * 32 + l] = col[k0 + k];
+    for (int e = 0; e < bb; ++e)
+      sval[((base + k) * bb + e) * 32 + l] = (float)val[(int64_t)(k0 + k) * bb + e];
+  }
+}
+
 // ------------------------------------------- row-per-thread reference ---
 template <class T>
 __global__ void k_row_spmv(int nrows, int br, int bc, const int* __restrict__ rowptr,
@@ -208,6 +316,48 @@ const T* values(const Bsr& A) {
 
 }  // namespace
 
+void bsr_make_sell(Bsr& A, cudaStream_t s) {
+  dfree(A.sell_off);
+  dfree(A.sell_col);
+  dfree(A.sell_valf);
+  A.sell_off = A.sell_col = nullptr;
+  A.sell_valf = nullptr;
+  if (A.nrows == 0) return;
+  const int ns = (A.nrows + 31) / 32;
+  int* len = dalloc<int>(ns + 1);
+  A.sell_off = dalloc<int>(ns + 1);
+  count_launch();
+  k_sell_len<<<(ns * 32 + 255) / 256, 256, 0, s>>>(A.nrows, A.rowptr, len);
+  int cols = 0;
+  exclusive_scan_int(len, A.sell_off, ns, &cols, s);
+  const int64_t entries = (int64_t)cols * 32;
+  const int bb = A.br * A.bc;
+  A.sell_col = dalloc<int>(std::max<int64_t>(entries, 1));
+  A.sell_valf = dalloc<float>(std::max<int64_t>(entries * bb, 1));
+  count_launch();
+  k_sell_fill<<<grid_for(A.nrows, 256), 256, 0, s>>>(A.nrows, bb, A.rowptr, A.col, A.val,
+                                                     A.sell_off, A.sell_col, A.sell_valf);
+  PFF_LAUNCH("sell");
+  PFF_CUDA(cudaStreamSynchronize(s));
+  dfree(len);
+}
+
+namespace {
+// launch OP through the SELL copy (FP32 only); false when it cannot be used
+template <class T, int OP>
+bool sell_op(const Bsr& A, const T* x, T* y, const T* rhs, const T* dinv, T* d, T alpha, T beta,
+             cudaStream_t s) {
+  if constexpr (sizeof(T) != 4) {
+    return false;
+  } else {
+    if (!A.sell_valf) return false;
+    SellArgs a{A.nrows, A.rowptr, A.sell_off, A.sell_col, A.sell_valf, x, y, rhs, dinv, d,
+               alpha, beta};
+    return launch_sell<OP>(A.br, A.bc, a, s);
+  }
+}
+}  // namespace
+
 // ------------------------------------------------------------ autotune ---
 // The lane-group width of each hierarchy matrix is picked by timing every
 // candidate on that matrix once; the winner is remembered per (element size,
@@ -218,7 +368,7 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_tune;
 
 template <class T>
-int tune_one(const Bsr& A, cudaStream_t s) {
+int tune_one(Bsr& A, cudaStream_t s) {
   const double avg = A.nrows > 0 ? (double)A.nnzb / A.nrows : 1.0;
   const auto key = std::make_tuple((int)sizeof(T), A.br * 10 + A.bc,
                                    (int)std::floor(std::log2(std::max(1, A.nrows))),
@@ -226,7 +376,10 @@ int tune_one(const Bsr& A, cudaStream_t s) {
   {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     auto it = g_tune.find(key);
-    if (it != g_tune.end()) return it->second;
+    if (it != g_tune.end()) {
+      if (it->second == BSR_SELL) bsr_make_sell(A, s);
+      return it->second;
+    }
   }
   const int64_t nx = (int64_t)A.ncols * A.bc, ny = (int64_t)A.nrows * A.br;
   T* x = dalloc<T>(nx);
@@ -238,16 +391,26 @@ int tune_one(const Bsr& A, cudaStream_t s) {
   VecArgs<T> a{A.nrows, A.rowptr, A.col, values<T>(A), x, y, nullptr, nullptr, nullptr, T(1), T(0)};
   int best = 4;
   float best_ms = 1e30f;
-  for (int G : {1, 2, 4, 8, 16, 32}) {
+  if constexpr (sizeof(T) == 4) bsr_make_sell(A, s);
+  for (int G : {1, 2, 4, 8, 16, 32, (int)BSR_SELL}) {
+    auto run = [&]() {
+      return G == BSR_SELL ? sell_op<T, OP_SPMV>(A, x, y, (const T*)nullptr, (const T*)nullptr,
+                                                 (T*)nullptr, T(1), T(0), s)
+                           : launch_shape<T, OP_SPMV>(A.br, A.bc, G, a, s);
+    };
     count_launch(4);
-    if (!launch_shape<T, OP_SPMV>(A.br, A.bc, G, a, s)) break;   // shape without vector kernels
+    if (!run()) continue;   // shape or precision without this variant
     PFF_CUDA(cudaEventRecord(e0, s));
-    for (int r = 0; r < 3; ++r) launch_shape<T, OP_SPMV>(A.br, A.bc, G, a, s);
+    for (int r = 0; r < 3; ++r) run();
     PFF_CUDA(cudaEventRecord(e1, s));
     PFF_CUDA(cudaEventSynchronize(e1));
     PFF_LAUNCH("spmv autotune");
     float ms = 0.f;
     PFF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (verbose())
+      std::fprintf(stderr, "[pff] spmv tune %dx%d rows %d nnzb %lld variant %d: %.2f us %.0f GB/s\n",
+                   A.br, A.bc, A.nrows, (long long)A.nnzb, G, 1e3 * ms / 3,
+                   bsr_bytes(A, sizeof(T), false) / (ms / 3 * 1e-3) * 1e-9);
     if (ms < best_ms) {
       best_ms = ms;
       best = G;
@@ -258,6 +421,13 @@ int tune_one(const Bsr& A, cudaStream_t s) {
   PFF_CUDA(cudaStreamSynchronize(s));
   dfree(x);
   dfree(y);
+  if (best != BSR_SELL) {   // keep the sliced copy only where it is used
+    dfree(A.sell_off);
+    dfree(A.sell_col);
+    dfree(A.sell_valf);
+    A.sell_off = A.sell_col = nullptr;
+    A.sell_valf = nullptr;
+  }
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best;
   return best;
@@ -269,14 +439,17 @@ void bsr_autotune(Bsr& A, bool f32, cudaStream_t s) {
   A.group = f32 ? tune_one<float>(A, s) : tune_one<double>(A, s);
 }
 
-int bsr_group(const Bsr& A) {
-  if (A.group != 0) return A.group;
-  // one pass over an average row: the smallest power of two >= mean blocks per row
+namespace {
+// one pass over an average row: the smallest power of two >= mean blocks per row
+int group_by_length(const Bsr& A) {
   const double avg = A.nrows > 0 ? (double)A.nnzb / A.nrows : 1.0;
   int g = 4;
   while (g < 32 && g < avg) g *= 2;
   return g;
 }
+}  // namespace
+
+int bsr_group(const Bsr& A) { return A.group != 0 ? A.group : group_by_length(A); }
 
 double bsr_bytes(const Bsr& A, int elem, bool beta) {
   return (double)A.nnzb * (A.br * A.bc * (double)elem + 4.0) + 4.0 * (A.nrows + 1.0) +
@@ -288,7 +461,13 @@ void bsr_spmv_t(const Bsr& A, const T* x, T* y, T alpha, T beta, cudaStream_t s)
   const int64_t rows = (int64_t)A.nrows * A.br;
   if (rows == 0) return;
   ProfScope ps(sizeof(T) == 8 ? "spmv_f64" : "spmv_f32", bsr_bytes(A, sizeof(T), beta != T(0)), s);
-  const int G = bsr_group(A);
+  int G = bsr_group(A);
+  if (G == BSR_SELL && sell_op<T, OP_SPMV>(A, x, y, (const T*)nullptr, (const T*)nullptr,
+                                           (T*)nullptr, alpha, beta, s)) {
+    PFF_LAUNCH("bsr_spmv");
+    return;
+  }
+  if (G == BSR_SELL) G = group_by_length(A);
   VecArgs<T> a{A.nrows, A.rowptr, A.col, values<T>(A), x, y, nullptr, nullptr, nullptr, alpha, beta};
   if (G < 0 || !launch_shape<T, OP_SPMV>(A.br, A.bc, G, a, s))
     k_row_spmv<T><<<grid_for(rows, 256), 256, 0, s>>>(A.nrows, A.br, A.bc, A.rowptr, A.col,
@@ -311,7 +490,13 @@ void bsr_resid(const Bsr& A, const T* rhs, const T* x, T* r, cudaStream_t s) {
   ProfScope ps(sizeof(T) == 8 ? "resid_f64" : "resid_f32",
                (double)A.nnzb * (A.br * A.bc * (double)sizeof(T) + 4.0) + 4.0 * (A.nrows + 1.0) +
                    3.0 * sizeof(T) * (double)rows, s);
-  const int G = bsr_group(A);
+  int G = bsr_group(A);
+  if (G == BSR_SELL && A.br == A.bc &&
+      sell_op<T, OP_RESID>(A, x, r, rhs, (const T*)nullptr, (T*)nullptr, T(0), T(0), s)) {
+    PFF_LAUNCH("bsr_resid");
+    return;
+  }
+  if (G == BSR_SELL) G = group_by_length(A);
   VecArgs<T> a{A.nrows, A.rowptr, A.col, values<T>(A), x, r, rhs, nullptr, nullptr, T(0), T(0)};
   if (G < 0 || A.br != A.bc || !launch_shape<T, OP_RESID>(A.br, A.bc, G, a, s))
     k_row_resid<T><<<grid_for(rows, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr, A.col,
@@ -328,7 +513,13 @@ void bsr_cheb(const Bsr& A, const T* dinv, const T* rhs, const T* xin, T* xout, 
   const double nvec = (double)rows * sizeof(T);
   ProfScope ps(sizeof(T) == 8 ? "cheb_f64" : "cheb_f32",
                (zero_x ? 0.0 : mat_b) + nvec * (zero_x ? 4.0 : 6.0), s);
-  const int G = bsr_group(A);
+  int G = bsr_group(A);
+  if (!zero_x && G == BSR_SELL && A.br == A.bc &&
+      sell_op<T, OP_CHEB>(A, xin, xout, rhs, dinv, d, cd, cr, s)) {
+    PFF_LAUNCH("bsr_cheb");
+    return;
+  }
+  if (G == BSR_SELL) G = group_by_length(A);
   VecArgs<T> a{A.nrows, A.rowptr, A.col, values<T>(A), xin, xout, rhs, dinv, d, cd, cr};
   if (zero_x || G < 0 || A.br != A.bc || !launch_shape<T, OP_CHEB>(A.br, A.bc, G, a, s))
     k_row_cheb<T><<<grid_for(rows, 256), 256, 0, s>>>(A.nrows, A.br, A.rowptr, A.col, values<T>(A),

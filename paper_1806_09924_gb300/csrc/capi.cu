@@ -216,8 +216,9 @@ pff_options resolve_options(const pff_options* opts) {
   need(o.tol_change >= 0.0 && o.tol_active >= 0.0, "negative active-set band");
   need(o.amg_reuse_tol >= 0.0, "negative amg_reuse_tol");
   need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 1 || o.spmv_group == 2 ||
-           o.spmv_group == 4 || o.spmv_group == 8 || o.spmv_group == 16 || o.spmv_group == 32,
-       "spmv_group must be 0, -1, 1, 2, 4, 8, 16 or 32");
+           o.spmv_group == 4 || o.spmv_group == 8 || o.spmv_group == 16 || o.spmv_group == 32 ||
+           o.spmv_group == 64,
+       "spmv_group must be 0, -1, 1, 2, 4, 8, 16, 32 or 64");
   return o;
 }
 }  // namespace

@@ -380,6 +380,11 @@ void Bsr::release() {
   dfree(col);
   dfree(val);
   dfree(valf);
+  dfree(sell_off);
+  dfree(sell_col);
+  dfree(sell_valf);
+  sell_off = sell_col = nullptr;
+  sell_valf = nullptr;
   rowptr = nullptr;
   col = nullptr;
   val = nullptr;

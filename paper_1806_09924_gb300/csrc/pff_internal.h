@@ -110,7 +110,14 @@ struct Bsr {
   double* val = nullptr;      // nnzb * br * bc, block row-major
   float* valf = nullptr;      // FP32 copy (mixed precision)
   int group = 0;              // lanes per block row of the vector kernels: 0 = by row length,
-                              // 1..32 = fixed, -1 = one thread per scalar row (reference)
+                              // 1..32 = fixed, -1 = one thread per scalar row (reference),
+                              // BSR_SELL = the sliced copy below (FP32 values)
+  // SELL-32 copy: slices of 32 block rows; slice s holds sell_off[s+1] - sell_off[s]
+  // entry columns of 32 blocks (its longest row); block k of row 32 s + l sits at entry
+  // (sell_off[s] + k) * 32 + l, its element e at value (((sell_off[s] + k) * bb + e) * 32 + l)
+  int* sell_off = nullptr;
+  int* sell_col = nullptr;
+  float* sell_valf = nullptr;
   void release();
 };
 
@@ -209,6 +216,11 @@ template <class T>
 void bsr_cheb(const Bsr& A, const T* dinv, const T* rhs, const T* xin, T* xout, T* d, T cd, T cr,
               bool zero_x, cudaStream_t s);
 int bsr_group(const Bsr& A);
+// algorithmic bytes of one SpMV with A (elem-byte values; beta: y is read too)
+double bsr_bytes(const Bsr& A, int elem, bool beta);
+enum { BSR_SELL = 64 };
+// build (or rebuild) the SELL-32 copy of A's FP32 values
+void bsr_make_sell(Bsr& A, cudaStream_t s);
 // time the lane-group widths of the vector kernels on A (FP32 or FP64 values)
 // and store the fastest in A.group (cached per matrix class)
 void bsr_autotune(Bsr& A, bool f32, cudaStream_t s);

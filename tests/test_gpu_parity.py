@@ -293,9 +293,10 @@ def test_preconditioner_is_a_convergent_linear_map():
 @pytest.mark.parametrize("dim,shape,seed", [(2, (48, 40), 51), (3, (14, 12, 10), 52)])
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_block_sparse_kernel_variants_agree(dim, shape, seed, precision):
-    """Every lane-group width of the vector block-sparse kernels (SpMV, residual,
-    Chebyshev step on the coarse levels and transfers) gives the V-cycle of the
-    row-per-thread reference kernels, up to the summation order."""
+    """Every lane-group width of the vector block-sparse kernels and the SELL-32
+    layout (SpMV, residual, Chebyshev step on the coarse levels and transfers)
+    give the V-cycle of the row-per-thread reference kernels, up to the
+    summation order."""
     P, mesh, prm, state = make_case(dim, shape, seed, p=1e-3)
     act = torch.empty(mesh.n_nodes, dtype=torch.uint8, device="cuda")
     P.active_set_dev(1.0, act, None)
@@ -304,7 +305,7 @@ def test_block_sparse_kernel_variants_agree(dim, shape, seed, precision):
     rng = np.random.default_rng(seed)
     r = torch.tensor(rng.standard_normal(P.n_dofs), device="cuda")
     out = {}
-    for g in (-1, 0, 1, 2, 4, 8, 16, 32):
+    for g in (-1, 0, 1, 2, 4, 8, 16, 32, 64):
         # a small coarse level gives several block-sparse levels on these meshes
         P.precond_setup(pff.options(precision=prec, spmv_group=g, amg_coarse_max=24))
         z = torch.empty_like(r)
@@ -312,7 +313,7 @@ def test_block_sparse_kernel_variants_agree(dim, shape, seed, precision):
         torch.cuda.synchronize()
         out[g] = z.cpu().numpy()
     tol = 1e-12 if precision == "fp64" else 1e-5
-    for g in (0, 1, 2, 4, 8, 16, 32):
+    for g in (0, 1, 2, 4, 8, 16, 32, 64):
         assert rel(out[g], out[-1]) <= tol, (g, rel(out[g], out[-1]))
     with pytest.raises(RuntimeError):
         P.precond_setup(pff.options(spmv_group=3))
