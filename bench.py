@@ -16,6 +16,10 @@ cpu_baseline / --impl reference = the CPU oracle (oracle/) on a bounded sample
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        [--cells C]   (same recipe at C x C cells: small cases for profiler captures)
+       [--workload batched [--instances 256] [--workers 8]]
+              256 independent 2d instances (32^2..512^2) through the batch executor
+       [--workload served [--requests 12] [--load 1.0] [--budget-gb 150] [--workers 8]]
+              a Poisson stream of mixed 2d / 3d 10-step requests through the server
 Multi-GPU runs (torchrun) are independent replicas: each rank solves its own
 copy of the workload; value sums the ranks' work over the slowest rank's time.
 """
@@ -371,6 +375,168 @@ def gpu_arm(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------- batched / served modes ----
+def _gpu_id(torch, local_rank):
+    try:
+        return "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
+    except Exception:
+        return str(local_rank)
+
+
+def batched_arm(args, rank, world, local_rank):
+    """256 independent 2d instances (32^2..512^2, one loading step each) solved
+    concurrently by the batch executor; the one-at-a-time solve of the same
+    instances is timed beside it."""
+    import torch
+    import paper_1806_09924_gb300 as pff
+    import workloads as W
+    torch.cuda.set_device(local_rank)
+    inst = W.batched_instances(args.instances)
+    # weak scaling over ranks: rank r takes every world-th instance
+    inst = inst[rank::world]
+    probs = [pff.problem_from_workload(w) for w in inst]
+    opts = pff.options(precision=pff.PFF_PREC_MIXED)
+    scheds = [w.pressures for w in inst]
+    dofs = sum(w.n_dofs * len(w.pressures) for w in inst)
+
+    def reset():
+        for P, w in zip(probs, inst):
+            P.set_crack(w.l0)
+        torch.cuda.synchronize()
+
+    def run(workers):
+        reset()
+        t0 = time.perf_counter()
+        reports, status = pff.batch_solve(probs, scheds, opts, workers=workers)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        if any(s != 0 for s in status):
+            raise RuntimeError(f"batch solve failed: {status}")
+        return dt, reports
+
+    for _ in range(args.warmup):
+        run(args.workers)
+    sampler = ClockSampler(_gpu_id(torch, local_rank))
+    sampler.start()
+    launches0 = pff.launch_count()
+    times = []
+    for _ in range(args.steps):
+        dt, reports = run(args.workers)
+        times.append(dt)
+    launches = pff.launch_count() - launches0
+    clocks = sampler.stop()
+    seq, _ = run(1)          # one at a time, same instances (untimed in value)
+    total = sum(times)
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([total], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    for P in probs:
+        P.close()
+    if rank != 0:
+        return 0
+    value = dofs * world * args.steps / total
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": "batched_sneddon2d_256", "instances": len(inst) * world,
+                   "cells": "32^2..512^2 (seed 1806)", "loading_steps_per_instance": 1,
+                   "n_dofs_total": dofs * world, "workers": args.workers,
+                   "parallelism": f"instances sharded over {world} rank(s)",
+                   "l2": "instances total several GB, > L2"},
+        "solves_per_s": len(inst) * world * args.steps / total,
+        "one_at_a_time": {"value": dofs / seq, "unit": UNIT, "s": seq},
+        "speedup_vs_one_at_a_time": seq * args.steps / total,
+        "newton_its_total": sum(r[0]["newton_its"] for r in reports),
+        "krylov_its_total": sum(r[0]["krylov_its"] for r in reports),
+        "gpu_launches": int(launches), "clocks": clocks,
+        "timing": "host wall clock around the synchronous batch call, state reset before",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def served_arm(args, rank, world, local_rank):
+    """Poisson stream of mixed 2d / 3d requests (10-step ramps) through the
+    request server under a device-memory budget; p50 / p99 latency and
+    throughput, next to the plain FP64 one-at-a-time GPU path on the same
+    requests (which also sets the arrival rate)."""
+    import numpy as np
+    import torch
+    import paper_1806_09924_gb300 as pff
+    import workloads as W
+    torch.cuda.set_device(local_rank)
+    if rank != 0:
+        return 0
+    reqs = W.served_requests(args.requests, steps=10)
+    budget = int(args.budget_gb * (1 << 30))
+    cod_x = [0.0]
+
+    def closed_loop(opts, workers):
+        S = pff.Server(budget, workers, opts)
+        t0 = time.perf_counter()
+        ids = [S.submit(w, cod_x=cod_x) for w, _ in reqs]
+        res = [S.wait(i) for i in ids]
+        dt = time.perf_counter() - t0
+        S.close()
+        if any(r["status"] != 0 for r in res):
+            raise RuntimeError("a request failed")
+        return dt, res
+
+    # plain FP64 one-at-a-time GPU path: service rate mu
+    base_s, base = closed_loop(pff.options(precision=pff.PFF_PREC_FP64), 1)
+    mu = len(reqs) / base_s
+    lam = args.load * mu
+    sampler = ClockSampler(_gpu_id(torch, local_rank))
+    sampler.start()
+    launches0 = pff.launch_count()
+    S = pff.Server(budget, args.workers, pff.options(precision=pff.PFF_PREC_MIXED))
+    arrivals = np.cumsum([g for _, g in reqs]) / lam
+    t0 = time.perf_counter()
+    ids = []
+    for (w, _), ta in zip(reqs, arrivals):
+        delay = ta - (time.perf_counter() - t0)
+        if delay > 0:
+            time.sleep(delay)
+        ids.append(S.submit(w, cod_x=cod_x))
+    res = [S.wait(i) for i in ids]
+    makespan = time.perf_counter() - t0
+    stats = S.stats()
+    S.close()
+    launches = pff.launch_count() - launches0
+    clocks = sampler.stop()
+    if any(r["status"] != 0 for r in res):
+        raise RuntimeError("a request failed")
+    lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
+    steps = sum(len(w.pressures) for w, _ in reqs)
+    dofs = sum(w.n_dofs * len(w.pressures) for w, _ in reqs)
+    base_lat = np.array([r["t_finish"] - r["t_submit"] for r in base])
+    line = {
+        "metric": METRIC, "value": dofs / makespan, "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": 1e3 * makespan, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": "served_mixed_2d3d", "requests": len(reqs),
+                   "mix": f"{sum(1 for w, _ in reqs if w.dim == 2)} 2d (64^2..1024^2 graded), "
+                          f"{sum(1 for w, _ in reqs if w.dim == 3)} 3d (32^3..128^3 graded), seed 1807",
+                   "loading_steps_per_request": 10, "arrivals": "Poisson",
+                   "rate_per_s": lam, "load_vs_fp64_service_rate": args.load,
+                   "budget_gb": args.budget_gb, "workers": args.workers},
+        "solves_per_s": steps / makespan,
+        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                      "mean": float(lat.mean())},
+        "fp64_one_at_a_time": {"value": dofs / base_s, "unit": UNIT, "solves_per_s": steps / base_s,
+                               "service_rate_per_s": mu,
+                               "latency_s_closed_loop": {"p50": float(np.percentile(base_lat, 50)),
+                                                         "p99": float(np.percentile(base_lat, 99))}},
+        "server": stats, "gpu_launches": int(launches), "clocks": clocks,
+        "timing": "host wall clock from the first arrival to the last completion",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -381,12 +547,35 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cells", type=int, default=0,
                     help="run the same recipe at this many cells per axis (profiling captures)")
+    ap.add_argument("--workload", default="graded2d", choices=["graded2d", "batched", "served"],
+                    help="graded2d: the 1024^2 graded ramp (default line); batched: 256 independent "
+                         "instances; served: a Poisson request stream")
+    ap.add_argument("--instances", type=int, default=256)
+    ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--requests", type=int, default=12)
+    ap.add_argument("--load", type=float, default=1.0,
+                    help="served: arrival rate as a multiple of the FP64 one-at-a-time service rate")
+    ap.add_argument("--budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
+        if args.workload != "graded2d":
+            if rank == 0:
+                print(json.dumps({"impl": "reference", "unavailable":
+                                  "the reference arm times the oracle on the graded 2d workload only"}))
+            return 0
         return reference_arm(args, rank, world)
+    if args.workload == "batched":
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local_rank)
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        return batched_arm(args, rank, world, local_rank)
+    if args.workload == "served":
+        return served_arm(args, rank, world, local_rank)
     return gpu_arm(args, rank, world, local_rank)
 
 

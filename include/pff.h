@@ -256,6 +256,102 @@ int pff_set_state_dev(pff_problem* prob, const double* u_dev, const double* phi_
 int pff_eval_tcv_cod_noalloc(pff_problem* prob, int n_pts, const double* pts, double* tcv,
                              double* cod);
 
+/* Batched solves (many independent problems) ------------------------------
+ * The paper solves one problem at a time; these entry points have no
+ * counterpart there.  They exist because small instances (a few thousand to a
+ * few hundred thousand DoFs) leave most of the GPU idle: their kernels are
+ * launch- and latency-bound.  Running many of them at once lets their kernels
+ * overlap on the device.
+ *
+ * pff_batch_solve solves the loading-step schedules of n independent problems
+ * with n_workers host threads (0: one per problem, at most 16).  Each worker
+ * owns a non-blocking CUDA stream; it takes the next unsolved problem (largest
+ * first), moves it onto its stream for the duration of the call (the
+ * problem's own stream is restored afterwards) and solves it exactly as
+ * pff_solve_loading_steps would, so every problem reaches the result it reaches
+ * alone, up to the summation order of the autotuned sparse kernels.
+ * problems[i] must be distinct.  n_steps[i] pressures are read from
+ * schedules[i] (host); reports[i] (host, caller-owned, n_steps[i] entries) and
+ * status[i] (may be NULL) receive the outcome of problem i.  Returns PFF_OK when
+ * every problem converged, else the first nonzero status (all problems are
+ * still attempted). */
+int pff_batch_solve(int n, pff_problem* const* problems, const int* n_steps,
+                    const double* const* schedules, const pff_options* opts,
+                    pff_step_report* const* reports, int n_workers, int* status);
+
+/* Request server (continuous batching) --------------------------------------
+ * Also without counterpart in the paper.  A server owns n_workers host
+ * threads and streams and a device-memory budget.  Submitted requests wait in
+ * FIFO order; the head of the queue is admitted as soon as a worker is free and
+ * its memory estimate (pff_request_bytes) fits into what the running requests
+ * leave of the budget (a request larger than the whole budget is admitted
+ * alone).  An admitted request builds its problem on the worker's stream,
+ * solves its pressure schedule, evaluates TCV and the requested COD points,
+ * optionally copies its solution to the host, and frees its device memory;
+ * requests that arrive meanwhile are admitted as memory and workers free up,
+ * so the kernels of all running requests overlap on the GPU. */
+typedef struct pff_server pff_server;
+
+typedef struct pff_request {
+  int dim;                        /* 2 or 3 */
+  int32_t n_cells[3];             /* cells per axis */
+  const double* axis_coords[3];   /* host, n_cells[a] + 1 increasing values each; copied */
+  double E, nu, Gc, kappa, eps;   /* material (pff_set_material) */
+  double l0;                      /* crack half-length (2d) / radius (3d) (pff_set_crack) */
+  int n_steps;                    /* loading steps */
+  const double* schedule;         /* host, n_steps pressures; copied */
+  int n_cod;                      /* COD points, may be 0 */
+  const double* cod_x;            /* host, n_cod abscissae; copied */
+  int keep_solution;              /* 1: keep u, phi, active on the host (pff_server_solution) */
+  int reserved;
+} pff_request;
+
+typedef struct pff_request_result {
+  int status;            /* PFF_OK or the error code of the request */
+  int done;              /* 1 once finished (successfully or not) */
+  int newton_its;        /* summed over the loading steps */
+  int krylov_its;        /* summed over the loading steps */
+  int converged_steps;   /* loading steps that met the stopping test */
+  int reserved;
+  int64_t n_dofs;
+  int64_t bytes;         /* admission estimate */
+  double t_submit;       /* seconds since the server was created */
+  double t_admit;
+  double t_finish;
+  double tcv;
+} pff_request_result;
+
+typedef struct pff_server_stats {
+  int64_t budget_bytes;
+  int64_t reserved_bytes;       /* estimates of the running requests */
+  int64_t peak_reserved_bytes;  /* never above the budget unless one request exceeds it alone */
+  int queued, running, finished;
+  int max_running;              /* most requests running at once */
+} pff_server_stats;
+
+/* Device bytes reserved for a problem of this size by the admission test. */
+int64_t pff_request_bytes(int dim, const int32_t* n_cells);
+
+int pff_server_create(int64_t budget_bytes, int n_workers, const pff_options* opts,
+                      pff_server** out);
+/* Queue a request (its arrays are copied); *id identifies it. */
+int pff_server_submit(pff_server* srv, const pff_request* req, int64_t* id);
+/* Non-blocking state of a request (res->done = 0 while queued or running). */
+int pff_server_result(pff_server* srv, int64_t id, pff_request_result* res);
+/* Wait up to timeout_s seconds (< 0: no limit) for a request to finish;
+ * PFF_ERR_TIMEOUT if it has not. */
+int pff_server_wait(pff_server* srv, int64_t id, double timeout_s, pff_request_result* res);
+/* COD values of a finished request (n_cod doubles, host). */
+int pff_server_cod(pff_server* srv, int64_t id, double* cod);
+/* Solution of a finished request submitted with keep_solution = 1 (host
+ * buffers as for pff_get_solution; any may be NULL). */
+int pff_server_solution(pff_server* srv, int64_t id, double* u, double* phi, uint8_t* active);
+/* Forget a finished request (its host copies are freed). */
+int pff_server_release(pff_server* srv, int64_t id);
+int pff_server_stats_get(pff_server* srv, pff_server_stats* st);
+/* Stop admitting, drop queued requests, wait for the running ones, free all. */
+void pff_server_destroy(pff_server* srv);
+
 /* Instrumentation (process-wide, all problems) ----------------------------- */
 
 /* Enable (1) or disable (0) per-kernel timing and reset its totals.  When

@@ -64,6 +64,41 @@ class PffStepReport(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class PffRequest(ctypes.Structure):
+    _fields_ = [
+        ("dim", ctypes.c_int), ("n_cells", ctypes.c_int32 * 3),
+        ("axis_coords", ctypes.POINTER(ctypes.c_double) * 3),
+        ("E", ctypes.c_double), ("nu", ctypes.c_double), ("Gc", ctypes.c_double),
+        ("kappa", ctypes.c_double), ("eps", ctypes.c_double), ("l0", ctypes.c_double),
+        ("n_steps", ctypes.c_int), ("schedule", ctypes.POINTER(ctypes.c_double)),
+        ("n_cod", ctypes.c_int), ("cod_x", ctypes.POINTER(ctypes.c_double)),
+        ("keep_solution", ctypes.c_int), ("reserved", ctypes.c_int),
+    ]
+
+
+class PffRequestResult(ctypes.Structure):
+    _fields_ = [
+        ("status", ctypes.c_int), ("done", ctypes.c_int), ("newton_its", ctypes.c_int),
+        ("krylov_its", ctypes.c_int), ("converged_steps", ctypes.c_int), ("reserved", ctypes.c_int),
+        ("n_dofs", ctypes.c_int64), ("bytes", ctypes.c_int64), ("t_submit", ctypes.c_double),
+        ("t_admit", ctypes.c_double), ("t_finish", ctypes.c_double), ("tcv", ctypes.c_double),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "reserved"}
+
+
+class PffServerStats(ctypes.Structure):
+    _fields_ = [
+        ("budget_bytes", ctypes.c_int64), ("reserved_bytes", ctypes.c_int64),
+        ("peak_reserved_bytes", ctypes.c_int64), ("queued", ctypes.c_int), ("running", ctypes.c_int),
+        ("finished", ctypes.c_int), ("max_running", ctypes.c_int),
+    ]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 class PffError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"pff error {code}: {msg}")
@@ -105,6 +140,22 @@ _SIGS = {
     "pff_profile_report": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "pff_launch_count": (ctypes.c_longlong, []),
     "pff_eval_tcv_cod_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "pff_batch_solve": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(_D), ctypes.POINTER(PffOptions),
+                                       ctypes.POINTER(ctypes.POINTER(PffStepReport)), ctypes.c_int,
+                                       ctypes.POINTER(ctypes.c_int)]),
+    "pff_request_bytes": (ctypes.c_int64, [ctypes.c_int, ctypes.POINTER(ctypes.c_int32)]),
+    "pff_server_create": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int, ctypes.POINTER(PffOptions),
+                                         ctypes.POINTER(_P)]),
+    "pff_server_submit": (ctypes.c_int, [_P, ctypes.POINTER(PffRequest), ctypes.POINTER(ctypes.c_int64)]),
+    "pff_server_result": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(PffRequestResult)]),
+    "pff_server_wait": (ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_double,
+                                       ctypes.POINTER(PffRequestResult)]),
+    "pff_server_cod": (ctypes.c_int, [_P, ctypes.c_int64, _P]),
+    "pff_server_solution": (ctypes.c_int, [_P, ctypes.c_int64, _P, _P, _P]),
+    "pff_server_release": (ctypes.c_int, [_P, ctypes.c_int64]),
+    "pff_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(PffServerStats)]),
+    "pff_server_destroy": (None, [_P]),
 }
 
 PFF_NOALLOC_MAX_POINTS = 1024
@@ -328,6 +379,115 @@ def profile_report() -> dict:
 def launch_count() -> int:
     """Kernels launched by the library since it was loaded."""
     return int(load_library().pff_launch_count())
+
+
+def batch_solve(problems, schedules, opts: Optional[PffOptions] = None, workers: int = 0):
+    """Solve independent problems concurrently (pff_batch_solve).
+
+    Returns (reports, status): reports[i] is the list of step-report dicts of
+    problems[i], status[i] its return code."""
+    lib = load_library()
+    n = len(problems)
+    o = opts if opts is not None else options()
+    scheds = [np.ascontiguousarray(s, dtype=np.float64).reshape(-1) for s in schedules]
+    reps = [(PffStepReport * max(len(s), 1))() for s in scheds]
+    handles = (_P * max(n, 1))(*[p.handle for p in problems])
+    steps = (ctypes.c_int * max(n, 1))(*[len(s) for s in scheds])
+    sp = (_D * max(n, 1))(*[s.ctypes.data_as(_D) for s in scheds])
+    rp = (ctypes.POINTER(PffStepReport) * max(n, 1))(
+        *[ctypes.cast(r, ctypes.POINTER(PffStepReport)) for r in reps])
+    st = (ctypes.c_int * max(n, 1))()
+    lib.pff_batch_solve(n, handles, steps, sp, ctypes.byref(o), rp, int(workers), st)
+    return ([[reps[i][k].as_dict() for k in range(len(scheds[i]))] for i in range(n)],
+            [st[i] for i in range(n)])
+
+
+def request_bytes(dim: int, n_cells) -> int:
+    """Device bytes the server's admission test reserves for a problem of this size."""
+    nc = (ctypes.c_int32 * 3)(*(list(n_cells) + [1] * (3 - len(n_cells))))
+    return int(load_library().pff_request_bytes(int(dim), nc))
+
+
+class Server:
+    """Continuous-batching request server (pff_server_*): a device-memory budget,
+    worker threads with their own streams, FIFO admission."""
+
+    def __init__(self, budget_bytes: int, workers: int, opts: Optional[PffOptions] = None):
+        lib = load_library()
+        self._lib = lib
+        o = opts if opts is not None else options()
+        h = _P()
+        _check(lib.pff_server_create(int(budget_bytes), int(workers), ctypes.byref(o), ctypes.byref(h)))
+        self._h = h
+        self._meta = {}
+
+    def submit(self, w, pressures=None, cod_x=(), keep_solution: bool = False) -> int:
+        """Queue a request for ``workloads.Workload`` w (its mesh, material, crack and,
+        unless given, its pressure schedule)."""
+        coords = [np.ascontiguousarray(c, dtype=np.float64) for c in w.coords]
+        sched = np.ascontiguousarray(w.pressures if pressures is None else pressures, dtype=np.float64)
+        cx = np.ascontiguousarray(cod_x, dtype=np.float64).reshape(-1)
+        r = PffRequest()
+        r.dim = w.dim
+        for a in range(w.dim):
+            r.n_cells[a] = len(coords[a]) - 1
+            r.axis_coords[a] = coords[a].ctypes.data_as(_D)
+        r.E, r.nu, r.Gc, r.kappa, r.eps, r.l0 = w.E, w.nu, w.Gc, w.kappa, w.eps, w.l0
+        r.n_steps = len(sched)
+        r.schedule = sched.ctypes.data_as(_D)
+        r.n_cod = len(cx)
+        r.cod_x = cx.ctypes.data_as(_D)
+        r.keep_solution = 1 if keep_solution else 0
+        rid = ctypes.c_int64()
+        _check(self._lib.pff_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)))
+        nn = int(np.prod([len(c) for c in coords]))
+        self._meta[rid.value] = (w.dim, nn, len(cx))
+        return rid.value
+
+    def result(self, rid: int) -> dict:
+        res = PffRequestResult()
+        _check(self._lib.pff_server_result(self._h, rid, ctypes.byref(res)))
+        return res.as_dict()
+
+    def wait(self, rid: int, timeout: float = -1.0) -> dict:
+        res = PffRequestResult()
+        _check(self._lib.pff_server_wait(self._h, rid, float(timeout), ctypes.byref(res)))
+        return res.as_dict()
+
+    def cod(self, rid: int) -> np.ndarray:
+        out = np.zeros(self._meta[rid][2])
+        _check(self._lib.pff_server_cod(self._h, rid, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def solution(self, rid: int):
+        d, nn, _ = self._meta[rid]
+        u = np.zeros((nn, d))
+        phi = np.zeros(nn)
+        act = np.zeros(nn, dtype=np.uint8)
+        _check(self._lib.pff_server_solution(self._h, rid, u.ctypes.data_as(ctypes.c_void_p),
+                                             phi.ctypes.data_as(ctypes.c_void_p),
+                                             act.ctypes.data_as(ctypes.c_void_p)))
+        return u, phi, act
+
+    def release(self, rid: int):
+        _check(self._lib.pff_server_release(self._h, rid))
+        self._meta.pop(rid, None)
+
+    def stats(self) -> dict:
+        st = PffServerStats()
+        _check(self._lib.pff_server_stats_get(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pff_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def problem_from_workload(w, crack: bool = True) -> Problem:

@@ -258,9 +258,24 @@ int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_c
   API_BEGIN
   need(out != nullptr, "out is NULL");
   *out = nullptr;
+  *out = pff::create_problem(dim, n_cells, axis_coords, nullptr);
+  API_END
+}
+
+}  // extern "C"
+
+namespace pff {
+// A problem whose set-up work and device memory are ordered on stream s (the
+// stream-ordered pool when s is not the legacy default stream, so that
+// creating and destroying problems does not synchronize the device while other
+// problems solve); pff_create_mesh uses the legacy default stream.
+pff_problem* create_problem(int dim, const int32_t* n_cells, const double* const* axis_coords,
+                            cudaStream_t stream) {
   need(dim == 2 || dim == 3, "dim must be 2 or 3");
   need(n_cells && axis_coords, "n_cells / axis_coords is NULL");
   auto* P = new pff_problem();
+  P->stream = stream;
+  AllocStream alloc_scope(stream);
   try {
     P->dim = dim;
     int64_t nn = 1, nc = 1;
@@ -283,7 +298,8 @@ int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_c
     const int64_t n = nn, N = P->n_dofs;
     for (int a = 0; a < dim; ++a) {
       P->X[a] = pff::dalloc<double>(P->nn[a]);
-      PFF_CUDA(cudaMemcpy(P->X[a], P->hX[a].data(), sizeof(double) * P->nn[a], cudaMemcpyHostToDevice));
+      PFF_CUDA(cudaMemcpyAsync(P->X[a], P->hX[a].data(), sizeof(double) * P->nn[a],
+                               cudaMemcpyHostToDevice, P->stream));
     }
     using pff::dalloc;
     P->u = dalloc<double>(n * dim);
@@ -319,17 +335,21 @@ int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_c
     P->dUA = dalloc<double>(N);
     P->Ftrial = dalloc<double>(N);
     P->tmp = dalloc<double>(N);
-    PFF_CUDA(cudaMemset(P->u, 0, sizeof(double) * n * dim));
-    PFF_CUDA(cudaMemset(P->active, 0, n));
-    PFF_CUDA(cudaMemset(P->raw_prev, 0, n));
-    PFF_CUDA(cudaMemset(P->locked, 0, n));
-    PFF_CUDA(cudaMemset(P->toggles, 0, sizeof(int) * n));
+    PFF_CUDA(cudaMemsetAsync(P->u, 0, sizeof(double) * n * dim, P->stream));
+    PFF_CUDA(cudaMemsetAsync(P->active, 0, n, P->stream));
+    PFF_CUDA(cudaMemsetAsync(P->raw_prev, 0, n, P->stream));
+    PFF_CUDA(cudaMemsetAsync(P->locked, 0, n, P->stream));
+    PFF_CUDA(cudaMemsetAsync(P->toggles, 0, sizeof(int) * n, P->stream));
     std::vector<double> ones((size_t)n, 1.0);
-    PFF_CUDA(cudaMemcpy(P->phi, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    PFF_CUDA(cudaMemcpy(P->phi_old, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
-    PFF_CUDA(cudaMemcpy(P->phi_prev, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    PFF_CUDA(cudaMemcpyAsync(P->phi, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice,
+                             P->stream));
+    PFF_CUDA(cudaMemcpyAsync(P->phi_old, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice,
+                             P->stream));
+    PFF_CUDA(cudaMemcpyAsync(P->phi_prev, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice,
+                             P->stream));
     P->Bp = dalloc<double>(n);
-    PFF_CUDA(cudaMemcpy(P->Bp, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice));
+    PFF_CUDA(cudaMemcpyAsync(P->Bp, ones.data(), sizeof(double) * n, cudaMemcpyHostToDevice,
+                             P->stream));
     const auto m = P->mesh();
     pff::launch_lumped_mass(m, n, P->mass, P->stream);
     P->Bu = dalloc<double>((size_t)n * dim * (dim == 2 ? 3 : 6));
@@ -344,13 +364,16 @@ int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_c
     refresh_phi_tilde(P);
     sync(P);
   } catch (...) {
+    cudaStreamSynchronize(P->stream);
     release(P);
     delete P;
     throw;
   }
-  *out = P;
-  API_END
+  return P;
 }
+}  // namespace pff
+
+extern "C" {
 
 int pff_set_material(pff_problem* P, double E, double nu, double Gc, double kappa, double eps) {
   API_BEGIN
@@ -566,7 +589,11 @@ int pff_get_sizes(const pff_problem* P, int* dim, int64_t* n_nodes, int64_t* n_d
 void pff_destroy(pff_problem* P) {
   if (!P) return;
   cudaStreamSynchronize(P->stream);
-  release(P);
+  {
+    pff::AllocStream alloc_scope(P->stream);   // pool memory goes back on the problem's stream
+    release(P);
+  }
+  cudaStreamSynchronize(P->stream);
   delete P;
 }
 

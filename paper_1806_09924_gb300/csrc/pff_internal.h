@@ -389,6 +389,9 @@ void begin_loading_step(pff_problem* P, double p);
 int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep);
 void end_loading_step(pff_problem* P);
 void compute_residual(pff_problem* P, const double* u, const double* phi, double* F);
+// a problem created with its set-up work and memory ordered on `stream`
+pff_problem* create_problem(int dim, const int32_t* n_cells, const double* const* axis_coords,
+                            cudaStream_t stream);
 void compute_active_set(pff_problem* P, double c_rel, double tol_active, double tol_change,
                         int lock_after, bool track);
 void assemble_all(pff_problem* P);

@@ -43,7 +43,9 @@ def test_binding_declares_every_symbol():
 def test_struct_layout_matches_header(tmp_path):
     """Every field of the binding's structs sits at the header's offset."""
     import paper_1806_09924_gb300 as pff
-    structs = {"pff_options": pff.PffOptions, "pff_step_report": pff.PffStepReport}
+    structs = {"pff_options": pff.PffOptions, "pff_step_report": pff.PffStepReport,
+               "pff_request": pff.PffRequest, "pff_request_result": pff.PffRequestResult,
+               "pff_server_stats": pff.PffServerStats}
     lines = []
     for cname, cls in structs.items():
         lines.append(f'printf("{cname} size %zu\\n", sizeof({cname}));')
@@ -84,3 +86,45 @@ def test_defaults_and_argument_errors_without_gpu(lib):
     assert b"dim" in lib.pff_last_error()
     assert lib.pff_set_pressure(None, 1e-3) == pff.PFF_ERR_INVALID_ARG
     assert lib.pff_newton_step(None, None, None) == pff.PFF_ERR_INVALID_ARG
+
+
+def test_server_host_logic_without_gpu(lib):
+    """Argument checks, the admission estimate and the request queue need no GPU
+    (workers that cannot get a stream leave the queue untouched)."""
+    import paper_1806_09924_gb300 as pff
+    b2 = pff.request_bytes(2, [64, 64])
+    assert 0 < b2 < pff.request_bytes(2, [128, 128]) < pff.request_bytes(2, [256, 256])
+    # per DoF a 3d problem needs more (27-point stencils)
+    assert (pff.request_bytes(3, [96, 96, 96]) / (4 * 97 ** 3)
+            > pff.request_bytes(2, [1024, 1024]) / (3 * 1025 ** 2))
+    assert lib.pff_request_bytes(4, (ctypes.c_int32 * 3)(2, 2, 2)) == -1
+    h = ctypes.c_void_p()
+    assert lib.pff_server_create(0, 1, None, ctypes.byref(h)) == pff.PFF_ERR_INVALID_ARG
+    assert lib.pff_server_create(1 << 30, 0, None, ctypes.byref(h)) == pff.PFF_ERR_INVALID_ARG
+    if torch_gpu():
+        return
+    S = pff.Server(1 << 30, 2)
+    bad = pff.PffRequest()
+    bad.dim = 5
+    rid = ctypes.c_int64()
+    assert lib.pff_server_submit(S._h, ctypes.byref(bad), ctypes.byref(rid)) == pff.PFF_ERR_INVALID_ARG
+    import workloads as W
+    w = W.config(0)
+    r = S.submit(w)
+    res = S.result(r)
+    assert res["done"] == 0 and res["n_dofs"] == w.n_dofs and res["bytes"] == pff.request_bytes(2, [128, 128])
+    with pytest.raises(pff.PffError):
+        S.wait(r, timeout=0.05)
+    with pytest.raises(pff.PffError):
+        S.release(r)          # not finished
+    st = S.stats()
+    assert st["queued"] == 1 and st["running"] == 0 and st["finished"] == 0
+    S.close()                 # drops the queued request
+
+
+def torch_gpu():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:
+        return False
