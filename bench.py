@@ -169,27 +169,23 @@ class ClockSampler:
 
 
 # -------------------------------------------------------------- GPU arm ----
-def _kernel_hash():
-    h = hashlib.sha256()
-    csrc = os.path.join(ROOT, "paper_1806_09924_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
-        with open(os.path.join(csrc, f), "rb") as fh:
-            h.update(fh.read())
-    return h.hexdigest()[:16]
+def _source_hash(rel_path: str) -> str:
+    with open(os.path.join(ROOT, rel_path), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
 def _traffic_for(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it is current."""
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
+    when the source file of the kernel changed since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
-            d = json.load(f)
+            e = json.load(f).get(kernel)
+        if not e or e.get("source_sha256") != _source_hash(e["source"]):
+            return None
+        return e.get("dram_bytes_per_launch_full_size")
     except Exception:
         return None
-    e = d.get(kernel)
-    if not e or e.get("source_hash") != _kernel_hash():
-        return None
-    return e.get("dram_bytes_per_launch_full_size")
 
 
 def gpu_arm(args, rank, world, local_rank):
@@ -487,6 +483,8 @@ def served_arm(args, rank, world, local_rank):
 
     # plain FP64 one-at-a-time GPU path: service rate mu
     base_s, base = closed_loop(pff.options(precision=pff.PFF_PREC_FP64), 1)
+    # the served form with every request queued at once (throughput bound)
+    mixed_s, _ = closed_loop(pff.options(precision=pff.PFF_PREC_MIXED), args.workers)
     mu = len(reqs) / base_s
     lam = args.load * mu
     sampler = ClockSampler(_gpu_id(torch, local_rank))
@@ -526,6 +524,8 @@ def served_arm(args, rank, world, local_rank):
         "solves_per_s": steps / makespan,
         "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                       "mean": float(lat.mean())},
+        "closed_loop_mixed": {"value": dofs / mixed_s, "unit": UNIT, "solves_per_s": steps / mixed_s,
+                              "note": "all requests queued at t = 0, same server"},
         "fp64_one_at_a_time": {"value": dofs / base_s, "unit": UNIT, "solves_per_s": steps / base_s,
                                "service_rate_per_s": mu,
                                "latency_s_closed_loop": {"p50": float(np.percentile(base_lat, 50)),

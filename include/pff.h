@@ -374,6 +374,11 @@ int pff_profile_report(char* buf, int buflen);
 /* Number of kernels launched by the library since it was loaded. */
 long long pff_launch_count(void);
 
+/* Device bytes the library holds now and at most since the last reset (all
+ * problems and servers of the process; reset_peak = 1 restarts the peak from
+ * the current value). */
+int pff_memory_usage(int64_t* current, int64_t* peak, int reset_peak);
+
 #ifdef __cplusplus
 }
 #endif

@@ -156,6 +156,8 @@ _SIGS = {
     "pff_server_release": (ctypes.c_int, [_P, ctypes.c_int64]),
     "pff_server_stats_get": (ctypes.c_int, [_P, ctypes.POINTER(PffServerStats)]),
     "pff_server_destroy": (None, [_P]),
+    "pff_memory_usage": (ctypes.c_int, [ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64),
+                                        ctypes.c_int]),
 }
 
 PFF_NOALLOC_MAX_POINTS = 1024
@@ -400,6 +402,13 @@ def batch_solve(problems, schedules, opts: Optional[PffOptions] = None, workers:
     lib.pff_batch_solve(n, handles, steps, sp, ctypes.byref(o), rp, int(workers), st)
     return ([[reps[i][k].as_dict() for k in range(len(scheds[i]))] for i in range(n)],
             [st[i] for i in range(n)])
+
+
+def memory_usage(reset_peak: bool = False):
+    """(current, peak) device bytes held by the library (all problems)."""
+    cur, peak = ctypes.c_int64(), ctypes.c_int64()
+    _check(load_library().pff_memory_usage(ctypes.byref(cur), ctypes.byref(peak), 1 if reset_peak else 0))
+    return cur.value, peak.value
 
 
 def request_bytes(dim: int, n_cells) -> int:

@@ -6,6 +6,7 @@
 #include <cstring>
 #include <mutex>
 #include <stdexcept>
+#include <unordered_map>
 #include <unordered_set>
 
 #include "pff_internal.h"
@@ -38,6 +39,14 @@ namespace {
 thread_local cudaStream_t t_alloc_stream = nullptr;
 std::mutex g_async_mu;
 std::unordered_set<void*> g_async_ptrs;
+std::unordered_map<void*, size_t> g_sizes;   // every live allocation and its size
+int64_t g_bytes = 0, g_peak = 0;
+
+void account(void* p, size_t bytes) {   // g_async_mu held
+  g_sizes[p] = bytes;
+  g_bytes += (int64_t)bytes;
+  g_peak = std::max(g_peak, g_bytes);
+}
 bool g_pool_ready[64] = {false};
 
 void prepare_pool() {
@@ -64,9 +73,16 @@ void* dmalloc(size_t bytes) {
     std::lock_guard<std::mutex> g(g_async_mu);
     prepare_pool();
     e = cudaMallocAsync(&p, bytes ? bytes : 16, t_alloc_stream);
-    if (e == cudaSuccess) g_async_ptrs.insert(p);
+    if (e == cudaSuccess) {
+      g_async_ptrs.insert(p);
+      account(p, bytes);
+    }
   } else {
     e = cudaMalloc(&p, bytes ? bytes : 16);
+    if (e == cudaSuccess) {
+      std::lock_guard<std::mutex> g(g_async_mu);
+      account(p, bytes);
+    }
   }
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -80,6 +96,11 @@ void dfree(void* p) {
   if (!p) return;
   {
     std::lock_guard<std::mutex> g(g_async_mu);
+    auto sz = g_sizes.find(p);
+    if (sz != g_sizes.end()) {
+      g_bytes -= (int64_t)sz->second;
+      g_sizes.erase(sz);
+    }
     auto it = g_async_ptrs.find(p);
     if (it != g_async_ptrs.end()) {
       g_async_ptrs.erase(it);
@@ -252,6 +273,14 @@ void pff_default_options(pff_options* o) {
 }
 
 const char* pff_last_error(void) { return pff::g_msg.c_str(); }
+
+int pff_memory_usage(int64_t* current, int64_t* peak, int reset_peak) {
+  std::lock_guard<std::mutex> g(pff::g_async_mu);
+  if (current) *current = pff::g_bytes;
+  if (peak) *peak = pff::g_peak;
+  if (reset_peak) pff::g_peak = pff::g_bytes;
+  return PFF_OK;
+}
 
 int pff_create_mesh(int dim, const int32_t* n_cells, const double* const* axis_coords,
                     pff_problem** out) {

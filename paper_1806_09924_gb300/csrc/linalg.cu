@@ -327,10 +327,24 @@ int sm_count() {
   return n;
 }
 
+// resident blocks per SM of a kernel (registers and shared memory permitting)
+template <class K>
+int resident_blocks(K kernel, size_t smem) {
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, kernel, RB, smem) != cudaSuccess || b < 1) {
+    cudaGetLastError();
+    b = 4;
+  }
+  return b;
+}
+
 int gs_grid(int64_t n, int* rows_per_block) {
-  // eight resident blocks per SM, more when a block's rows would overflow the
-  // staging buffer (GS_MAX_ROWS floats of shared memory)
-  int64_t g = std::max<int64_t>(8LL * sm_count(), (n + GS_MAX_ROWS - 1) / GS_MAX_ROWS);
+  // one full wave (every SM holding as many blocks as fit), more blocks when a
+  // block's rows would overflow the staging buffer (GS_MAX_ROWS floats)
+  static int waves_blocks = 0;
+  if (waves_blocks == 0)
+    waves_blocks = sm_count() * resident_blocks(k_gs_dot, sizeof(float) * (GS_MAX_ROWS / 2));
+  int64_t g = std::max<int64_t>(waves_blocks, (n + GS_MAX_ROWS - 1) / GS_MAX_ROWS);
   g = std::max<int64_t>(1, std::min<int64_t>(g, n));
   *rows_per_block = (int)((n + g - 1) / g);
   return (int)((n + *rows_per_block - 1) / *rows_per_block);
@@ -351,7 +365,9 @@ void gs_dot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n,
 void gs_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n,
                  float* part, double* nrm2, cudaStream_t s) {
   if (nv > 64) fail(PFF_ERR_INVALID_ARG, "mixed Gram-Schmidt: basis too large");
-  const int g = (int)std::min<int64_t>(8LL * sm_count(), std::max<int64_t>(1, (n + RB - 1) / RB));
+  static int wave = 0;
+  if (wave == 0) wave = sm_count() * resident_blocks(k_gs_axpy, 0);
+  const int g = (int)std::min<int64_t>(wave, std::max<int64_t>(1, (n + RB - 1) / RB));
   ProfScope ps("gs_axpy", 8.0 * n * (nv + 2.0), s, 2);
   k_gs_axpy<<<g, RB, 0, s>>>(V, ld, nv, h, w, n, part);
   k_gs_final<<<1, RB, 0, s>>>(part, g, nrm2);
