@@ -98,7 +98,10 @@ typedef struct pff_options {
                            while phi~ moved by at most amg_reuse_tol (max norm) since its
                            build; 0: rebuilt every loading step; 1 */
   double amg_reuse_tol; /* see amg_reuse; 0.05 */
-  int reserved[2];
+  int precond_overlap;  /* 1: the displacement and phase-field V-cycles of the block
+                           preconditioner run concurrently on two streams; 0: one after the
+                           other; 1 */
+  int reserved;
 } pff_options;
 
 /* Per loading step (or per Newton iteration for pff_newton_step) report. */

@@ -167,6 +167,14 @@ void release(pff_problem* P) {
   dfree(P->Kpp_f);
   dfree(P->gs_part);
   dfree(P->phit_built);
+  if (P->side) {
+    cudaStreamSynchronize(P->side);
+    cudaStreamDestroy(P->side);
+    P->side = nullptr;
+  }
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
+  P->ev_fork = P->ev_join = nullptr;
   dfree(P->active);
   dfree(P->active_prev);
   dfree(P->raw_prev);
@@ -270,6 +278,7 @@ void pff_default_options(pff_options* o) {
   o->tol_change = 1e-9;
   o->amg_reuse = 1;
   o->amg_reuse_tol = 0.05;
+  o->precond_overlap = 1;
 }
 
 const char* pff_last_error(void) { return pff::g_msg.c_str(); }

@@ -315,6 +315,11 @@ struct pff_problem {
   double* X[3] = {nullptr, nullptr, nullptr};
   pff::Material mat{1.0, 0.2, 1.0, 1e-10, 0.0625, 0.0, 0.0, 0.0};
   cudaStream_t stream = nullptr;
+  // second stream of the block preconditioner: the phase-field V-cycle runs on
+  // it while the displacement V-cycle runs on `stream` (fork / join by events)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool overlap = true;
 
   // state (device)
   double *u = nullptr, *phi = nullptr, *phi_old = nullptr, *phi_prev = nullptr, *phit = nullptr;

@@ -214,6 +214,7 @@ static double max_abs_diff(pff_problem* P, const double* a, const double* b, int
 
 void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   P->precision = o.precision;
+  P->overlap = o.precond_overlap != 0;
   if (o.precond == PFF_PC_JACOBI) return;
   AmgParams ap;
   ap.theta = o.amg_theta;
@@ -307,8 +308,24 @@ void precond_apply(pff_problem* P, const double* r, double* z) {
     k_mul<<<grid_for(N, 256), 256, 0, P->stream>>>(N, P->op_S ? P->op_S : P->S, r, P->tmp);
   }
   PFF_LAUNCH("precond scale");
-  amg_vcycle(P->amg_u, P->tmp, z, P->stream);
-  amg_vcycle(P->amg_p, P->tmp + nu, z + nu, P->stream);
+  if (P->overlap) {
+    // the two diagonal blocks are independent: their V-cycles (whose coarse
+    // levels are latency-bound) overlap on two streams
+    if (!P->side) {
+      PFF_CUDA(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+      PFF_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+      PFF_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+    }
+    PFF_CUDA(cudaEventRecord(P->ev_fork, P->stream));
+    PFF_CUDA(cudaStreamWaitEvent(P->side, P->ev_fork, 0));
+    amg_vcycle(P->amg_p, P->tmp + nu, z + nu, P->side);
+    amg_vcycle(P->amg_u, P->tmp, z, P->stream);
+    PFF_CUDA(cudaEventRecord(P->ev_join, P->side));
+    PFF_CUDA(cudaStreamWaitEvent(P->stream, P->ev_join, 0));
+  } else {
+    amg_vcycle(P->amg_u, P->tmp, z, P->stream);
+    amg_vcycle(P->amg_p, P->tmp + nu, z + nu, P->stream);
+  }
 }
 
 static void precond(pff_problem* P, const pff_options& o, const double* r, double* z) {

@@ -320,6 +320,25 @@ def test_block_sparse_kernel_variants_agree(dim, shape, seed, precision):
     P.close()
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_concurrent_block_vcycles_equal_sequential(precision):
+    """The two diagonal blocks' V-cycles on two streams give the sequential result bit for bit."""
+    P, mesh, prm, state = make_case(2, (40, 36), 61, p=1e-3)
+    act = torch.empty(mesh.n_nodes, dtype=torch.uint8, device="cuda")
+    P.active_set_dev(1.0, act, None)
+    P.assemble()
+    r = torch.tensor(np.random.default_rng(5).standard_normal(P.n_dofs), device="cuda")
+    out = []
+    for ov in (0, 1):
+        P.precond_setup(pff.options(precision=precision, precond_overlap=ov, spmv_group=8))
+        z = torch.empty_like(r)
+        P.precond_apply_dev(r, z)
+        torch.cuda.synchronize()
+        out.append(z.cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+    P.close()
+
+
 @pytest.mark.parametrize("precision", ["fp64", "mixed"])
 def test_linear_solve_matches_direct_solve(precision):
     """FGMRES to 1e-12 against a sparse direct solve of the reduced system; in
