@@ -320,6 +320,28 @@ def test_block_sparse_kernel_variants_agree(dim, shape, seed, precision):
     P.close()
 
 
+@pytest.mark.parametrize("dim,shape,seed", [(2, (36, 22), 71), (3, (8, 6, 4), 72)])
+def test_mixed_vcycle_matches_fp64_vcycle(dim, shape, seed):
+    """The FP32 V-cycle (four-node stencil kernels, FP32 hierarchy copies) and the
+    FP64 V-cycle (separate one-node kernels) on the same hierarchy agree to FP32
+    accuracy; node counts that are not multiples of 4 exercise the ragged tail."""
+    P, mesh, prm, state = make_case(dim, shape, seed, p=1e-3)
+    assert mesh.n_nodes % 4 != 0
+    act = torch.empty(mesh.n_nodes, dtype=torch.uint8, device="cuda")
+    P.active_set_dev(1.0, act, None)
+    P.assemble()
+    r = torch.tensor(np.random.default_rng(seed).standard_normal(P.n_dofs), device="cuda")
+    out = []
+    for prec in (0, 1):
+        P.precond_setup(pff.options(precision=prec, amg_coarse_max=24))
+        z = torch.empty_like(r)
+        P.precond_apply_dev(r, z)
+        torch.cuda.synchronize()
+        out.append(z.cpu().numpy())
+    assert rel(out[1], out[0]) <= 1e-4, rel(out[1], out[0])
+    P.close()
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_concurrent_block_vcycles_equal_sequential(precision):
     """The two diagonal blocks' V-cycles on two streams give the sequential result bit for bit."""
