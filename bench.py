@@ -384,6 +384,22 @@ def gpu_arm(args, rank, world, local_rank):
     return 0
 
 
+# ------------------------------------------------------ multi-rank helpers ----
+def shard(items, rank: int, world: int):
+    """Weak scaling over ranks: rank r takes every world-th item (no data-path exchange)."""
+    return list(items)[rank::world]
+
+
+def reduce_across_ranks(value: float, op: str, dist=None, device="cpu") -> float:
+    """max / sum of a host scalar over the ranks of the default process group."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return float(value)
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 # ------------------------------------------------- batched / served modes ----
 def _gpu_id(torch, local_rank):
     try:
@@ -400,9 +416,7 @@ def batched_arm(args, rank, world, local_rank):
     import paper_1806_09924_gb300 as pff
     import workloads as W
     torch.cuda.set_device(local_rank)
-    inst = W.batched_instances(args.instances)
-    # weak scaling over ranks: rank r takes every world-th instance
-    inst = inst[rank::world]
+    inst = shard(W.batched_instances(args.instances), rank, world)
     probs = [pff.problem_from_workload(w) for w in inst]
     opts = pff.options(precision=pff.PFF_PREC_MIXED)
     scheds = [w.pressures for w in inst]
@@ -435,27 +449,27 @@ def batched_arm(args, rank, world, local_rank):
     launches = pff.launch_count() - launches0
     clocks = sampler.stop()
     seq, _ = run(1)          # one at a time, same instances (untimed in value)
-    total = sum(times)
+    dist = None
     if world > 1:
         import torch.distributed as dist
-        t = torch.tensor([total], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total = float(t.item())
+    total = reduce_across_ranks(sum(times), "max", dist, "cuda")
+    dofs_all = reduce_across_ranks(dofs, "sum", dist, "cuda")
+    n_all = int(reduce_across_ranks(len(inst), "sum", dist, "cuda"))
     for P in probs:
         P.close()
     if rank != 0:
         return 0
-    value = dofs * world * args.steps / total
+    value = dofs_all * args.steps / total
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
-        "config": {"workload": "batched_sneddon2d_256", "instances": len(inst) * world,
+        "config": {"workload": "batched_sneddon2d_256", "instances": n_all,
                    "cells": "32^2..512^2 (seed 1806)", "loading_steps_per_instance": 1,
-                   "n_dofs_total": dofs * world, "workers": args.workers,
+                   "n_dofs_total": dofs_all, "workers": args.workers,
                    "parallelism": f"instances sharded over {world} rank(s)",
                    "l2": "instances total several GB, > L2"},
-        "solves_per_s": len(inst) * world * args.steps / total,
+        "solves_per_s": n_all * args.steps / total,
         "one_at_a_time": {"value": dofs / seq, "unit": UNIT, "s": seq},
         "speedup_vs_one_at_a_time": seq * args.steps / total,
         "newton_its_total": sum(r[0]["newton_its"] for r in reports),
