@@ -861,7 +861,7 @@ void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* 
   // first step: d = r / theta
   if (L.stencil) {
     launch_stencil_cheb<T>(L.mesh, nb, b, stencil_vals<T>(L), dinvs<T>(L), rhs, cur, nxt, d, 0.0,
-                           1.0 / theta, zero_start ? 1 : 0, s);
+                           1.0 / theta, zero_start ? 1 : 0, s, sizeof(T) == 4 && L.stf_node_major);
   } else {
     bsr_cheb<T>(A, dinvs<T>(L), rhs, cur, nxt, d, T(0), T(1.0 / theta), zero_start, s);
   }
@@ -870,7 +870,7 @@ void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* 
     const double rn = 1.0 / (2.0 * sigma - rho);
     if (L.stencil) {
       launch_stencil_cheb<T>(L.mesh, nb, b, stencil_vals<T>(L), dinvs<T>(L), rhs, cur, nxt, d,
-                             rn * rho, 2.0 * rn / delta, 0, s);
+                             rn * rho, 2.0 * rn / delta, 0, s, sizeof(T) == 4 && L.stf_node_major);
     } else {
       bsr_cheb<T>(A, dinvs<T>(L), rhs, cur, nxt, d, T(rn * rho), T(2.0 * rn / delta), false, s);
     }
@@ -903,7 +903,8 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
   }
   const Bsr& A = L.A;
   if (L.stencil) {
-    launch_stencil_resid<T>(L.mesh, A.nrows, A.br, stencil_vals<T>(L), rhs, x, r, s);
+    launch_stencil_resid<T>(L.mesh, A.nrows, A.br, stencil_vals<T>(L), rhs, x, r, s,
+                            sizeof(T) == 4 && L.stf_node_major);
   } else {
     bsr_resid<T>(A, rhs, x, r, s);
   }

@@ -931,6 +931,84 @@ __global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
   }
 }
 
+// 2d displacement block in FP32 with the node-major layout Kq[(s n + i) * 4 + 2a + c]:
+// each node's 2x2 block of slot s is one 16-byte load, each neighbour's x one
+// 8-byte load.  RESID: r = rhs - K x; otherwise one Chebyshev step as above.
+template <bool RESID>
+__device__ __forceinline__ void stencil_q2(const MeshDev& m, int n, const float* __restrict__ Kq,
+                                           const float* __restrict__ dinv,
+                                           const float* __restrict__ rhs,
+                                           const float* __restrict__ xin, float* __restrict__ out,
+                                           float* __restrict__ d, float cd, float cr, int zero_x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float a0 = 0.f, a1 = 0.f;
+  if (RESID || !zero_x) {
+    const int n0 = m.nn[0];
+    const int ix = i % n0, iy = i / n0;
+    const bool lx = ix > 0, hx = ix < n0 - 1, ly = iy > 0, hy = iy < m.nn[1] - 1;
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+      const int ox = s % 3 - 1, oy = s / 3 - 1;
+      const bool ok = (ox < 0 ? lx : ox > 0 ? hx : true) && (oy < 0 ? ly : oy > 0 ? hy : true);
+      const int j = ok ? i + ox + oy * n0 : i;
+      const float2 x = reinterpret_cast<const float2*>(xin)[j];
+      const float4 k = reinterpret_cast<const float4*>(Kq)[(int64_t)s * n + i];
+      const float x0 = ok ? x.x : 0.f, x1 = ok ? x.y : 0.f;
+      a0 += k.x * x0 + k.y * x1;
+      a1 += k.z * x0 + k.w * x1;
+    }
+  }
+  const float2 b = reinterpret_cast<const float2*>(rhs)[i];
+  if constexpr (RESID) {
+    reinterpret_cast<float2*>(out)[i] = make_float2(b.x - a0, b.y - a1);
+  } else {
+    const float2 di = reinterpret_cast<const float2*>(dinv)[i];
+    float2 dn = make_float2(cr * di.x * (b.x - a0), cr * di.y * (b.y - a1));
+    float2 xo = dn;
+    if (!zero_x) {
+      const float2 dd = reinterpret_cast<const float2*>(d)[i];
+      const float2 xi = reinterpret_cast<const float2*>(xin)[i];
+      dn.x += cd * dd.x;
+      dn.y += cd * dd.y;
+      xo = make_float2(xi.x + dn.x, xi.y + dn.y);
+    }
+    reinterpret_cast<float2*>(d)[i] = dn;
+    reinterpret_cast<float2*>(out)[i] = xo;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_stencil_cheb_q2(MeshDev m, int n, const float* __restrict__ Kq,
+                                                         const float* __restrict__ dinv,
+                                                         const float* __restrict__ rhs,
+                                                         const float* __restrict__ xin,
+                                                         float* __restrict__ xout,
+                                                         float* __restrict__ d, float cd, float cr,
+                                                         int zero_x) {
+  stencil_q2<false>(m, n, Kq, dinv, rhs, xin, xout, d, cd, cr, zero_x);
+}
+
+__global__ void __launch_bounds__(256) k_stencil_resid_q2(MeshDev m, int n,
+                                                          const float* __restrict__ Kq,
+                                                          const float* __restrict__ rhs,
+                                                          const float* __restrict__ x,
+                                                          float* __restrict__ r) {
+  stencil_q2<true>(m, n, Kq, nullptr, rhs, x, r, nullptr, 0.f, 0.f, 0);
+}
+
+// node-major FP32 copy of the 2d displacement stencil (9 slots x 2 x 2)
+__global__ void k_stencil_to_q2(int64_t n, const double* __restrict__ K, float* __restrict__ Kq) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 9 * n) return;
+  const int64_t s = t / n, i = t - s * n;
+  float4 q;
+  q.x = (float)K[(s * 4 + 0) * n + i];
+  q.y = (float)K[(s * 4 + 1) * n + i];
+  q.z = (float)K[(s * 4 + 2) * n + i];
+  q.w = (float)K[(s * 4 + 3) * n + i];
+  reinterpret_cast<float4*>(Kq)[t] = q;
+}
+
 // r = rhs - K x
 template <class T, int D, int B>
 __global__ void __launch_bounds__(256) k_stencil_resid(MeshDev m, int64_t n,
@@ -1267,34 +1345,55 @@ void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s) 
 template <class T>
 void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T* dinv,
                          const T* rhs, const T* xin, T* xout, T* d, double cd, double cr,
-                         int zero_x, cudaStream_t s) {
+                         int zero_x, cudaStream_t s, bool node_major) {
   // stencil values (unless starting from zero), then dinv, rhs, x_in, x_out, d read + write
   const double bytes = sizeof(T) * (double)n *
                        ((zero_x ? 0.0 : NSd(m.dim) * b * b) + b * (zero_x ? 4.0 : 6.0));
   ProfScope ps(sizeof(T) == 8 ? "cheb0_f64" : "cheb0_f32", bytes, s);
+  if constexpr (sizeof(T) == 4) {
+    if (node_major && m.dim == 2 && b == 2) {
+      k_stencil_cheb_q2<<<grid_for(n, 256), 256, 0, s>>>(m, (int)n, K, dinv, rhs, xin, xout, d,
+                                                         (float)cd, (float)cr, zero_x);
+      PFF_LAUNCH("stencil_cheb");
+      return;
+    }
+  }
   STENCIL_DISPATCH(m.dim, b, k_stencil_cheb, m, n, K, dinv, rhs, xin, xout, d, (T)cd, (T)cr, zero_x);
   PFF_LAUNCH("stencil_cheb");
 }
 
 template <class T>
 void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const T* rhs, const T* x,
-                          T* r, cudaStream_t s) {
+                          T* r, cudaStream_t s, bool node_major) {
   const double bytes = sizeof(T) * (double)n * (NSd(m.dim) * b * b + 3.0 * b);
   ProfScope ps(sizeof(T) == 8 ? "resid0_f64" : "resid0_f32", bytes, s);
+  if constexpr (sizeof(T) == 4) {
+    if (node_major && m.dim == 2 && b == 2) {
+      k_stencil_resid_q2<<<grid_for(n, 256), 256, 0, s>>>(m, (int)n, K, rhs, x, r);
+      PFF_LAUNCH("stencil_resid");
+      return;
+    }
+  }
   STENCIL_DISPATCH(m.dim, b, k_stencil_resid, m, n, K, rhs, x, r);
   PFF_LAUNCH("stencil_resid");
 }
 
 template void launch_stencil_cheb<float>(const MeshDev&, int64_t, int, const float*, const float*,
                                          const float*, const float*, float*, float*, double, double,
-                                         int, cudaStream_t);
+                                         int, cudaStream_t, bool);
 template void launch_stencil_cheb<double>(const MeshDev&, int64_t, int, const double*,
                                           const double*, const double*, const double*, double*,
-                                          double*, double, double, int, cudaStream_t);
+                                          double*, double, double, int, cudaStream_t, bool);
 template void launch_stencil_resid<float>(const MeshDev&, int64_t, int, const float*, const float*,
-                                          const float*, float*, cudaStream_t);
+                                          const float*, float*, cudaStream_t, bool);
 template void launch_stencil_resid<double>(const MeshDev&, int64_t, int, const double*,
-                                           const double*, const double*, double*, cudaStream_t);
+                                           const double*, const double*, double*, cudaStream_t, bool);
+
+void stencil_to_node_major(const double* K, float* Kq, int64_t n, cudaStream_t s) {
+  ProfScope ps("to_f32", 48.0 * 9 * n, s);
+  k_stencil_to_q2<<<grid_for(9 * n, 256), 256, 0, s>>>(n, K, Kq);
+  PFF_LAUNCH("stencil_to_q2");
+}
 
 void launch_stencil_dinv(const MeshDev& m, int64_t n, int b, const double* K, double* dinv,
                          float* dinvf, cudaStream_t s) {

@@ -135,6 +135,7 @@ struct AmgLevel {
   MeshDev mesh{};
   const double* st = nullptr;
   const float* stf = nullptr;
+  bool stf_node_major = false;  // stf in the node-major 2d displacement layout
   // V-cycle work vectors (stored as doubles; FP32 cycles reinterpret them)
   double *x = nullptr, *b = nullptr, *r = nullptr, *d = nullptr, *t = nullptr;
 };
@@ -281,13 +282,17 @@ void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s);
 // node coordinates [n][dim]
 void launch_node_coords(const MeshDev& m, int64_t n, double* xyz, cudaStream_t s);
 // AMG finest level on the node stencil (T = float or double; b = dim or 1)
+// node_major: K is the FP32 node-major copy of a 2d displacement stencil
+// (stencil_to_node_major); otherwise slot-major with slot stride n
 template <class T>
 void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T* dinv,
                          const T* rhs, const T* xin, T* xout, T* d, double cd, double cr,
-                         int zero_x, cudaStream_t s);
+                         int zero_x, cudaStream_t s, bool node_major = false);
 template <class T>
 void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const T* rhs, const T* x,
-                          T* r, cudaStream_t s);
+                          T* r, cudaStream_t s, bool node_major = false);
+// FP32 node-major copy Kq[(s n + i) * 4 + 2a + c] of a 2d displacement stencil
+void stencil_to_node_major(const double* K, float* Kq, int64_t n, cudaStream_t s);
 void convert_d2f(const double* a, float* b, int64_t n, cudaStream_t s);
 // dinv (and its FP32 copy, may be null) = inverse diagonal of a node stencil
 void launch_stencil_dinv(const MeshDev& m, int64_t n, int b, const double* K, double* dinv,

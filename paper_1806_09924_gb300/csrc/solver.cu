@@ -237,7 +237,9 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     L0.st = K;
     if (ap.mixed) {
       if (!Kf) Kf = dalloc<float>(count);
-      convert_d2f(K, Kf, count, P->stream);
+      L0.stf_node_major = P->dim == 2 && count == (int64_t)ns * 4 * n;
+      if (L0.stf_node_major) stencil_to_node_major(K, Kf, n, P->stream);
+      else convert_d2f(K, Kf, count, P->stream);
       L0.stf = Kf;
     }
   };
