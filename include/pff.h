@@ -78,7 +78,9 @@ typedef struct pff_options {
   int max_krylov;       /* FGMRES iterations per linear solve; 600 */
   int cheb_degree;      /* Chebyshev smoother degree; 2 */
   double amg_theta;     /* strength threshold on the distance Laplacian of the mesh nodes
-                           (w_ij = 1/|x_i - x_j|^2 strong iff w_ij^2 >= theta^2 wmax_i wmax_j); 0.25 */
+                           (w_ij = 1/|x_i - x_j|^2 strong iff w_ij^2 >= theta^2 wmax_i wmax_j);
+                           0.06 (0 treats every coupling as strong and fails on graded
+                           meshes; 0.25 and above lose semi-coarsening efficiency) */
   int amg_coarse_max;   /* largest coarse level (scalar rows) solved directly; 320 */
   int apply_variant;    /* PFF_APPLY_*; PFF_APPLY_AUTO */
   int precond;          /* PFF_PC_*; PFF_PC_AMG */

@@ -268,7 +268,7 @@ void pff_default_options(pff_options* o) {
   o->krylov_restart = 40;
   o->max_krylov = 600;
   o->cheb_degree = 2;
-  o->amg_theta = 0.25;
+  o->amg_theta = 0.06;
   o->amg_coarse_max = 320;
   o->apply_variant = PFF_APPLY_AUTO;
   o->precond = PFF_PC_AMG;

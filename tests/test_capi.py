@@ -74,7 +74,7 @@ def test_struct_layout_matches_header(tmp_path):
 def test_defaults_and_argument_errors_without_gpu(lib):
     import paper_1806_09924_gb300 as pff
     o = pff.options()
-    assert o.tol_linear == 1e-8 and o.c == 0.1 and o.amg_theta == 0.25 and o.precision == pff.PFF_PREC_FP64
+    assert o.tol_linear == 1e-8 and o.c == 0.1 and o.amg_theta == 0.06 and o.precision == pff.PFF_PREC_FP64
     assert o.tol_active == 1e-10 and o.tol_change == 1e-9 and o.atol_newton == 1e-14
     assert o.krylov_restart == 40 and o.max_newton == 50
     assert o.spmv_group == 0 and o.amg_reuse == 1 and o.amg_reuse_tol == 0.05
