@@ -617,71 +617,72 @@ __global__ void k_densify(int n, int b, const int* __restrict__ rp, const int* _
 }
 
 // Gauss-Jordan inverse with partial pivoting, one block (n small)
-__global__ void k_gauss_jordan(int n, double* __restrict__ A, double* __restrict__ Inv,
-                               int* __restrict__ err) {
-  __shared__ int piv;
+// Gauss-Jordan with partial pivoting spread over the GPU: per pivot k one
+// block chooses the pivot row, swaps it into row k and scales it (k_gj_pivot),
+// then one block per row eliminates column k from it (k_gj_elim).
+__global__ void k_gj_identity(int n, double* __restrict__ Inv) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (int64_t)n * n) Inv[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+__global__ void k_gj_pivot(int n, int k, double* __restrict__ A, double* __restrict__ Inv,
+                           int* __restrict__ err) {
   __shared__ double pmax[256];
   __shared__ int pidx[256];
   const int t = threadIdx.x;
-  for (int e = t; e < n * n; e += blockDim.x) Inv[e] = (e / n == e % n) ? 1.0 : 0.0;
+  double best = -1.0;
+  int bi = k;
+  for (int r = k + t; r < n; r += blockDim.x) {
+    const double v = fabs(A[(int64_t)r * n + k]);
+    if (v > best) {
+      best = v;
+      bi = r;
+    }
+  }
+  pmax[t] = best;
+  pidx[t] = bi;
   __syncthreads();
-  for (int k = 0; k < n; ++k) {
-    double best = -1.0;
-    int bi = k;
-    for (int r = k + t; r < n; r += blockDim.x) {
-      const double v = fabs(A[(int64_t)r * n + k]);
-      if (v > best) {
-        best = v;
-        bi = r;
-      }
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {   // max, ties to the lower row
+    if (t < o && (pmax[t + o] > pmax[t] || (pmax[t + o] == pmax[t] && pidx[t + o] < pidx[t]))) {
+      pmax[t] = pmax[t + o];
+      pidx[t] = pidx[t + o];
     }
-    pmax[t] = best;
-    pidx[t] = bi;
-    __syncthreads();
-    if (t == 0) {
-      double b = -1.0;
-      int bb = k;
-      for (int j = 0; j < (int)blockDim.x; ++j)
-        if (pmax[j] > b || (pmax[j] == b && pidx[j] < bb)) {
-          b = pmax[j];
-          bb = pidx[j];
-        }
-      piv = bb;
-      if (!(b > 0.0)) atomicExch(err, 4);
-    }
-    __syncthreads();
-    const int p = piv;
-    if (p != k) {
-      for (int c = t; c < n; c += blockDim.x) {
-        double x = A[(int64_t)k * n + c];
-        A[(int64_t)k * n + c] = A[(int64_t)p * n + c];
-        A[(int64_t)p * n + c] = x;
-        x = Inv[(int64_t)k * n + c];
-        Inv[(int64_t)k * n + c] = Inv[(int64_t)p * n + c];
-        Inv[(int64_t)p * n + c] = x;
-      }
-    }
-    __syncthreads();
-    const double dk = A[(int64_t)k * n + k];
-    const double inv = dk != 0.0 ? 1.0 / dk : 0.0;
-    __syncthreads();
-    for (int c = t; c < n; c += blockDim.x) {
-      A[(int64_t)k * n + c] *= inv;
-      Inv[(int64_t)k * n + c] *= inv;
-    }
-    __syncthreads();
-    for (int e = t; e < n * n; e += blockDim.x) {
-      const int r = e / n, c = e % n;
-      if (r == k) continue;
-      const double f = A[(int64_t)r * n + k];
-      if (c != k) A[(int64_t)r * n + c] -= f * A[(int64_t)k * n + c];
-      Inv[(int64_t)r * n + c] -= f * Inv[(int64_t)k * n + c];
-    }
-    __syncthreads();
-    for (int r = t; r < n; r += blockDim.x)
-      if (r != k) A[(int64_t)r * n + k] = 0.0;
     __syncthreads();
   }
+  const int p = pidx[0];
+  if (t == 0 && !(pmax[0] > 0.0)) atomicExch(err, 4);
+  if (p != k) {
+    for (int c = t; c < n; c += blockDim.x) {
+      double x = A[(int64_t)k * n + c];
+      A[(int64_t)k * n + c] = A[(int64_t)p * n + c];
+      A[(int64_t)p * n + c] = x;
+      x = Inv[(int64_t)k * n + c];
+      Inv[(int64_t)k * n + c] = Inv[(int64_t)p * n + c];
+      Inv[(int64_t)p * n + c] = x;
+    }
+  }
+  __syncthreads();
+  const double dk = A[(int64_t)k * n + k];
+  const double inv = dk != 0.0 ? 1.0 / dk : 0.0;
+  __syncthreads();
+  for (int c = t; c < n; c += blockDim.x) {
+    A[(int64_t)k * n + c] *= inv;
+    Inv[(int64_t)k * n + c] *= inv;
+  }
+}
+
+// block r != k: row r -= A[r][k] * row k (row k is only read here)
+__global__ void k_gj_elim(int n, int k, double* __restrict__ A, double* __restrict__ Inv) {
+  const int r = blockIdx.x;
+  if (r == k) return;
+  const double f = A[(int64_t)r * n + k];
+  if (f == 0.0) return;
+  for (int c = k + 1 + threadIdx.x; c < n; c += blockDim.x)
+    A[(int64_t)r * n + c] -= f * A[(int64_t)k * n + c];
+  for (int c = threadIdx.x; c < n; c += blockDim.x)
+    Inv[(int64_t)r * n + c] -= f * Inv[(int64_t)k * n + c];
+  __syncthreads();
+  if (threadIdx.x == 0) A[(int64_t)r * n + k] = 0.0;
 }
 
 // power-iteration step: y = D^-1 A x
@@ -977,6 +978,30 @@ double estimate_lmax(const Bsr& A, const double* dinv, cudaStream_t s, double* p
   k_hash_vec<<<g, 256, 0, s>>>(n, w);
   dot_dev(w, w, n, dred, partials, s);
   k_lz_next<<<g, 256, 0, s>>>(n, w, dred, 0, dh, v, t);   // v_0 = w / ||w||, t = dh .* v_0
+  // largest Ritz value of T_m (m = done steps) up to the first breakdown
+  // (beta_j ~ 0: an invariant subspace was found); *broke tells whether it did
+  std::vector<double> h(2 * steps);
+  auto ritz = [&](int done, bool* broke) {
+    PFF_CUDA(cudaMemcpyAsync(h.data(), al, sizeof(double) * steps, cudaMemcpyDeviceToHost, s));
+    PFF_CUDA(cudaMemcpyAsync(h.data() + steps, nb2, sizeof(double) * steps, cudaMemcpyDeviceToHost, s));
+    PFF_CUDA(cudaStreamSynchronize(s));
+    std::vector<double> a, b;
+    *broke = false;
+    for (int j = 0; j < done; ++j) {
+      a.push_back(h[j]);
+      const double bn = std::sqrt(std::max(h[steps + j], 0.0));
+      if (!(bn > 1e-14 * std::fabs(h[j]))) {
+        *broke = true;
+        break;
+      }
+      if (j + 1 == done) break;
+      b.push_back(bn);
+    }
+    return a.empty() ? 1.0 : tridiag_max_eig(a, b);
+  };
+  // checkpoints: stop once the largest Ritz value moved by less than 1e-3
+  // relative over the last 6 steps (it increases monotonically toward lmax)
+  double lam = 0.0, prev = -1.0;
   for (int j = 0; j < steps; ++j) {
     bsr_spmv(A, t, y, 1.0, 0.0, s);                        // y = A D^-1/2 v_j
     count_launch(3);
@@ -986,20 +1011,15 @@ double estimate_lmax(const Bsr& A, const double* dinv, cudaStream_t s, double* p
     dot_dev(w, w, n, nb2 + j, partials, s);
     k_lz_next<<<g, 256, 0, s>>>(n, w, nb2, j, dh, vp, t);  // v_{j+1} into the v_{j-1} buffer
     std::swap(v, vp);
+    const int done = j + 1;
+    if (done == steps || (done >= 12 && done % 6 == 0)) {
+      bool broke = false;
+      lam = ritz(done, &broke);
+      if (broke || done == steps || (prev > 0.0 && lam - prev <= 1e-3 * lam)) break;
+      prev = lam;
+    }
   }
-  std::vector<double> h(2 * steps);
-  PFF_CUDA(cudaMemcpyAsync(h.data(), al, sizeof(double) * 2 * steps, cudaMemcpyDeviceToHost, s));
-  PFF_CUDA(cudaStreamSynchronize(s));
   PFF_LAUNCH("lmax");
-  // tridiagonal T_m up to the first breakdown (beta_j ~ 0: invariant subspace found)
-  std::vector<double> a, b;
-  for (int j = 0; j < steps; ++j) {
-    a.push_back(h[j]);
-    const double bn = std::sqrt(std::max(h[steps + j], 0.0));
-    if (!(bn > 1e-14 * std::fabs(h[j])) || j + 1 == steps) break;
-    b.push_back(bn);
-  }
-  const double lam = a.empty() ? 1.0 : tridiag_max_eig(a, b);
   dfree(v);
   dfree(vp);
   dfree(w);
@@ -1181,8 +1201,12 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
       PFF_CUDA(cudaMemsetAsync(Dm, 0, sizeof(double) * (size_t)n * n, s));
       count_launch();
       k_densify<<<grid_for(nb, 128), 128, 0, s>>>(nb, br, A.rowptr, A.col, A.val, Dm, n);
-      count_launch();
-      k_gauss_jordan<<<1, 256, 0, s>>>(n, Dm, amg.cinv, sc.err);
+      count_launch(1 + 2 * n);
+      k_gj_identity<<<grid_for((int64_t)n * n, 256), 256, 0, s>>>(n, amg.cinv);
+      for (int k = 0; k < n; ++k) {
+        k_gj_pivot<<<1, 256, 0, s>>>(n, k, Dm, amg.cinv, sc.err);
+        k_gj_elim<<<n, 128, 0, s>>>(n, k, Dm, amg.cinv);
+      }
       PFF_LAUNCH("coarse inverse");
       if (amg.mixed) {
         amg.cinvf = dalloc<float>((size_t)n * n);

@@ -151,6 +151,7 @@ void refresh_phi_tilde(pff_problem* P) {
   P->uu_assembled = false;
   P->phi_assembled = false;
   P->amg_u_valid = false;
+  P->amg_p_valid = false;
   P->in_step = false;
 }
 
@@ -167,6 +168,7 @@ void release(pff_problem* P) {
   dfree(P->Kpp_f);
   dfree(P->gs_part);
   dfree(P->phit_built);
+  dfree(P->active_built);
   if (P->side) {
     cudaStreamSynchronize(P->side);
     cudaStreamDestroy(P->side);
@@ -431,6 +433,7 @@ int pff_set_material(pff_problem* P, double E, double nu, double Gc, double kapp
   P->uu_assembled = false;
   P->phi_assembled = false;
   P->amg_u_valid = false;
+  P->amg_p_valid = false;
   P->in_step = false;
   API_END
 }
@@ -680,6 +683,7 @@ int pff_precond_setup(pff_problem* P, const pff_options* opts) {
   need(P->phi_assembled, "call pff_assemble first");
   const pff_options o = resolve_options(opts);
   P->amg_u_valid = false;
+  P->amg_p_valid = false;
   pff::precond_setup(P, o);
   sync(P);
   API_END

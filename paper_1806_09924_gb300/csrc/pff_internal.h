@@ -361,7 +361,8 @@ struct pff_problem {
   double* phit_built = nullptr;  // phi~ the displacement hierarchy was built from
   int amg_u_age = 0;             // loading steps the displacement hierarchy was reused for
   // the phase-field hierarchy is reused while the active set barely moves
-  int64_t phi_amg_changes = 0;   // active-set changes since the last build
+  bool amg_p_valid = false;      // false: the phase-field hierarchy must be rebuilt
+  uint8_t* active_built = nullptr;  // active set the phase-field hierarchy was built for
   int phi_amg_age = 0;           // Newton iterations since the last build
   int precision = PFF_PREC_FP64;
 

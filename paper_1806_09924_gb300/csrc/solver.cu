@@ -198,6 +198,26 @@ __global__ void k_abs_diff(int64_t n, const double* __restrict__ a, const double
   if (i < n) out[i] = fabs(a[i] - b[i]);
 }
 
+__global__ void k_count_diff(int64_t n, const uint8_t* __restrict__ a, const uint8_t* __restrict__ b,
+                             int* __restrict__ cnt) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const bool d = i < n && a[i] != b[i];
+  const unsigned m = __ballot_sync(0xffffffffu, d);
+  if ((threadIdx.x & 31) == 0 && m) atomicAdd(cnt, __popc(m));
+}
+
+// number of indices where two masks differ
+static int64_t count_diff(pff_problem* P, const uint8_t* a, const uint8_t* b, int64_t n) {
+  count_launch();
+  PFF_CUDA(cudaMemsetAsync(P->counters + 4, 0, sizeof(int), P->stream));
+  k_count_diff<<<grid_for(n, 256), 256, 0, P->stream>>>(n, a, b, P->counters + 4);
+  PFF_LAUNCH("count_diff");
+  PFF_CUDA(cudaMemcpyAsync(P->h_counters + 4, P->counters + 4, sizeof(int), cudaMemcpyDeviceToHost,
+                           P->stream));
+  PFF_CUDA(cudaStreamSynchronize(P->stream));
+  return P->h_counters[4];
+}
+
 // max_i |a_i - b_i| (device vectors of length n <= n_dofs)
 static double max_abs_diff(pff_problem* P, const double* a, const double* b, int64_t n) {
   double* t = P->tmp ? P->tmp : dalloc<double>(n);
@@ -280,19 +300,24 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     P->amg_u_valid = true;
     P->cur.amg_builds_u += 1;
   }
-  // Phase-field block: rebuild at the start of a loading step and whenever the
-  // active set moved by more than 0.1 % of the nodes (or every 5 iterations);
-  // otherwise keep the hierarchy and refresh only the finest level's stencil
-  // values and diagonal.  FGMRES converges to its tolerance either way: a
-  // stale coarse space costs iterations, not accuracy.
-  const bool rebuild = !allow_reuse || !P->amg_p.built || P->amg_p.mixed != ap.mixed || P->k == 0 ||
-                       P->phi_amg_changes > n / 1000 || P->phi_amg_age >= 5 || P->amg_p.lev.empty();
+  // Phase-field block: rebuild when the active set differs from the one the
+  // hierarchy was built for in more than 0.1 % of the nodes (also across
+  // loading steps), or after 8 Newton iterations; otherwise keep the hierarchy
+  // and refresh only the finest level's stencil values and diagonal.  FGMRES
+  // converges to its tolerance either way: a stale coarse space costs
+  // iterations, not accuracy.
+  bool rebuild = !allow_reuse || !P->amg_p_valid || !P->amg_p.built ||
+                 P->amg_p.mixed != ap.mixed || P->phi_amg_age >= 8 || P->amg_p.lev.empty() ||
+                 !P->active_built;
+  if (!rebuild) rebuild = count_diff(P, P->active, P->active_built, n) > n / 1000;
   if (rebuild) {
     ProfScope ps("amg_setup_phi", 0.0, P->stream, 0);
     launch_stencil_to_bsr(m, n, 1, P->Kpp, P->App, P->stream);
     amg_build(P->amg_p, P->App, P->Bp, 1, ap, P->stream);
     P->cur.amg_builds_phi += 1;
-    P->phi_amg_changes = 0;
+    if (!P->active_built) P->active_built = dalloc<uint8_t>(n);
+    PFF_CUDA(cudaMemcpyAsync(P->active_built, P->active, n, cudaMemcpyDeviceToDevice, P->stream));
+    P->amg_p_valid = true;
     P->phi_amg_age = 0;
   } else {
     AmgLevel& L0 = P->amg_p.lev[0];
@@ -579,7 +604,7 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   }
   // 4. reduced Jacobian and right-hand side
   assemble_all(P);
-  if (P->have_prev) P->phi_amg_changes += n_changed;
+
   precond_setup(P, o, true);
   // 5. linear solve on the scaled system.  The displacement and phase-field
   // blocks of S^-1 F~ differ by orders of magnitude (displacements vs. a
