@@ -702,42 +702,48 @@ __global__ void k_dinv_spmv(int n, int b, const int* __restrict__ rp, const int*
 }
 
 // y = D^-1/2 A D^-1/2 x (D = scalar diagonal, dinv = 1/D or 0)
-// Lanczos recurrence on S = D^-1/2 A D^-1/2 with every scalar kept on the device:
+// Lanczos recurrence on S = D^-1/2 A D^-1/2 with every scalar kept on the device
+// (FP64 scalars; vectors in T = double, or float for mixed-precision hierarchies):
 // al[j] = <S v_j, v_j>, nb2[j] = ||w_j||^2, beta_j = sqrt(nb2[j])
-__global__ void k_lz_sqrt(int64_t n, const double* __restrict__ dinv, double* __restrict__ dh) {
+template <class T>
+__global__ void k_lz_sqrt(int64_t n, const T* __restrict__ dinv, T* __restrict__ dh) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) dh[i] = sqrt(dinv[i]);
 }
 // w = dh .* y
-__global__ void k_lz_scale(int64_t n, const double* __restrict__ dh, const double* __restrict__ y,
-                           double* __restrict__ w) {
+template <class T>
+__global__ void k_lz_scale(int64_t n, const T* __restrict__ dh, const T* __restrict__ y,
+                           T* __restrict__ w) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) w[i] = dh[i] * y[i];
 }
 // w -= al[j] v + beta_{j-1} vp   (no vp term at j = 0)
-__global__ void k_lz_orth(int64_t n, double* __restrict__ w, const double* __restrict__ v,
-                          const double* __restrict__ vp, const double* __restrict__ al,
+template <class T>
+__global__ void k_lz_orth(int64_t n, T* __restrict__ w, const T* __restrict__ v,
+                          const T* __restrict__ vp, const double* __restrict__ al,
                           const double* __restrict__ nb2, int j) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double beta = j > 0 ? sqrt(fmax(nb2[j - 1], 0.0)) : 0.0;
-  w[i] -= al[j] * v[i] + (j > 0 ? beta * vp[i] : 0.0);
+  const T a = (T)al[j];
+  const T beta = j > 0 ? (T)sqrt(fmax(nb2[j - 1], 0.0)) : T(0);
+  w[i] -= a * v[i] + (j > 0 ? beta * vp[i] : T(0));
 }
 // v_next = w / ||w|| (0 after a breakdown), t = dh .* v_next
-__global__ void k_lz_next(int64_t n, const double* __restrict__ w, const double* __restrict__ nb2,
-                          int j, const double* __restrict__ dh, double* __restrict__ vn,
-                          double* __restrict__ t) {
+template <class T>
+__global__ void k_lz_next(int64_t n, const T* __restrict__ w, const double* __restrict__ nb2,
+                          int j, const T* __restrict__ dh, T* __restrict__ vn, T* __restrict__ t) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double q = nb2[j] > 0.0 ? 1.0 / sqrt(nb2[j]) : 0.0;
-  const double x = w[i] * q;
+  const T q = nb2[j] > 0.0 ? (T)(1.0 / sqrt(nb2[j])) : T(0);
+  const T x = w[i] * q;
   vn[i] = x;
   t[i] = dh[i] * x;
 }
 
-__global__ void k_hash_vec(int64_t n, double* __restrict__ x) {
+template <class T>
+__global__ void k_hash_vec(int64_t n, T* __restrict__ x) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) x[i] = (double)(hash32((uint32_t)i * 2654435761u + 12345u) & 0xffffff) / 16777216.0 + 0.1;
+  if (i < n) x[i] = (T)((double)(hash32((uint32_t)i * 2654435761u + 12345u) & 0xffffff) / 16777216.0 + 0.1);
 }
 
 __global__ void k_scale(int64_t n, double* __restrict__ x, const double* __restrict__ nrm2) {
@@ -958,26 +964,40 @@ double tridiag_max_eig(const std::vector<double>& a, const std::vector<double>& 
 // lambda_max(D^-1 A) by Lanczos on the similar symmetric matrix D^-1/2 A D^-1/2:
 // the extreme Ritz value converges from below much faster than power iteration
 // on the clustered spectra of graded meshes.
-double estimate_lmax(const Bsr& A, const double* dinv, cudaStream_t s, double* partials,
+void lz_dot(const double* x, const double* y, int64_t n, double* out, double* partials,
+            cudaStream_t s) {
+  dot_dev(x, y, n, out, partials, s);
+}
+void lz_dot(const float* x, const float* y, int64_t n, double* out, double* partials,
+            cudaStream_t s) {
+  dot_dev_f32(x, y, n, out, partials, s);
+}
+void lz_spmv(const Bsr& A, const double* x, double* y, cudaStream_t s) { bsr_spmv(A, x, y, 1.0, 0.0, s); }
+void lz_spmv(const Bsr& A, const float* x, float* y, cudaStream_t s) { bsr_spmv_f(A, x, y, 1.f, 0.f, s); }
+
+// T = float runs the recurrence on the FP32 copy of A (A.valf): the estimate
+// only sets the Chebyshev interval and the prolongator damping
+template <class T>
+double estimate_lmax(const Bsr& A, const T* dinv, cudaStream_t s, double* partials,
                      double* dred, double* hred) {
   (void)hred;
   const int64_t n = (int64_t)A.nrows * A.br;
   const int steps = (int)std::min<int64_t>(30, n);
   const unsigned g = grid_for(n, 256);
-  double* v = dalloc<double>(n);
-  double* vp = dalloc<double>(n);
-  double* w = dalloc<double>(n);
-  double* t = dalloc<double>(n);
-  double* y = dalloc<double>(n);
-  double* dh = dalloc<double>(n);
+  T* v = dalloc<T>(n);
+  T* vp = dalloc<T>(n);
+  T* w = dalloc<T>(n);
+  T* t = dalloc<T>(n);
+  T* y = dalloc<T>(n);
+  T* dh = dalloc<T>(n);
   double* al = dalloc<double>(2 * steps);
   double* nb2 = al + steps;
-  PFF_CUDA(cudaMemsetAsync(vp, 0, sizeof(double) * n, s));
+  PFF_CUDA(cudaMemsetAsync(vp, 0, sizeof(T) * n, s));
   count_launch(3);
-  k_lz_sqrt<<<g, 256, 0, s>>>(n, dinv, dh);
-  k_hash_vec<<<g, 256, 0, s>>>(n, w);
-  dot_dev(w, w, n, dred, partials, s);
-  k_lz_next<<<g, 256, 0, s>>>(n, w, dred, 0, dh, v, t);   // v_0 = w / ||w||, t = dh .* v_0
+  k_lz_sqrt<T><<<g, 256, 0, s>>>(n, dinv, dh);
+  k_hash_vec<T><<<g, 256, 0, s>>>(n, w);
+  lz_dot(w, w, n, dred, partials, s);
+  k_lz_next<T><<<g, 256, 0, s>>>(n, w, dred, 0, dh, v, t);   // v_0 = w / ||w||, t = dh .* v_0
   // largest Ritz value of T_m (m = done steps) up to the first breakdown
   // (beta_j ~ 0: an invariant subspace was found); *broke tells whether it did
   std::vector<double> h(2 * steps);
@@ -1003,13 +1023,13 @@ double estimate_lmax(const Bsr& A, const double* dinv, cudaStream_t s, double* p
   // relative over the last 6 steps (it increases monotonically toward lmax)
   double lam = 0.0, prev = -1.0;
   for (int j = 0; j < steps; ++j) {
-    bsr_spmv(A, t, y, 1.0, 0.0, s);                        // y = A D^-1/2 v_j
+    lz_spmv(A, t, y, s);                                      // y = A D^-1/2 v_j
     count_launch(3);
-    k_lz_scale<<<g, 256, 0, s>>>(n, dh, y, w);             // w = S v_j
-    dot_dev(w, v, n, al + j, partials, s);
-    k_lz_orth<<<g, 256, 0, s>>>(n, w, v, vp, al, nb2, j);
-    dot_dev(w, w, n, nb2 + j, partials, s);
-    k_lz_next<<<g, 256, 0, s>>>(n, w, nb2, j, dh, vp, t);  // v_{j+1} into the v_{j-1} buffer
+    k_lz_scale<T><<<g, 256, 0, s>>>(n, dh, y, w);             // w = S v_j
+    lz_dot(w, v, n, al + j, partials, s);
+    k_lz_orth<T><<<g, 256, 0, s>>>(n, w, v, vp, al, nb2, j);
+    lz_dot(w, w, n, nb2 + j, partials, s);
+    k_lz_next<T><<<g, 256, 0, s>>>(n, w, nb2, j, dh, vp, t);  // v_{j+1} into the v_{j-1} buffer
     std::swap(v, vp);
     const int done = j + 1;
     if (done == steps || (done >= 12 && done % 6 == 0)) {
@@ -1145,6 +1165,18 @@ void Amg::release() {
   cinvf = nullptr;
   cx = cb = nullptr;
   built = 0;
+}
+
+// lambda_max of D^-1 A for a level; mixed hierarchies first make the level's
+// FP32 copies (A.valf, dinvf), which the FP32 V-cycle needs anyway
+double level_lmax(Amg& amg, AmgLevel& L, cudaStream_t s, double* partials, SetupScratch& sc) {
+  if (!amg.mixed) return estimate_lmax<double>(L.A, L.dinv, s, partials, sc.red, sc.h_red);
+  const int64_t n = (int64_t)L.A.nrows * L.A.br;
+  make_float(L.A, s);
+  L.dinvf = dalloc<float>(n);
+  count_launch();
+  k_to_float<<<grid_for(n, 256), 256, 0, s>>>(n, L.dinv, L.dinvf);
+  return estimate_lmax<float>(L.A, L.dinvf, s, partials, sc.red, sc.h_red);
 }
 
 // named set-up phase for the per-kernel profile (no kernels of its own)
@@ -1293,18 +1325,12 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     if (nagg == 0 || (int64_t)nagg * nns > (int64_t)(0.9 * n) || level >= prm.max_levels) {
       // every row is isolated (identity / decoupled rows): smoothing is all there is
       L.terminal = true;
-      L.lmax = estimate_lmax(L.A, L.dinv, s, partials, sc.red, sc.h_red);
+      L.lmax = level_lmax(amg, L, s, partials, sc);
       L.x = dalloc<double>(n);
       L.b = dalloc<double>(n);
       L.r = dalloc<double>(n);
       L.d = dalloc<double>(n);
       L.t = dalloc<double>(n);
-      if (amg.mixed) {
-        make_float(L.A, s);
-        L.dinvf = dalloc<float>(n);
-        count_launch();
-        k_to_float<<<grid_for(n, 256), 256, 0, s>>>(n, L.dinv, L.dinvf);
-      }
       PFF_CUDA(cudaStreamSynchronize(s));
       dfree(dnorm);
       dfree(s0);
@@ -1356,7 +1382,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     }
     // smoothed prolongator
     ph.start("setup_lmax");
-    L.lmax = estimate_lmax(L.A, L.dinv, s, partials, sc.red, sc.h_red);
+    L.lmax = level_lmax(amg, L, s, partials, sc);
     ph.start("setup_prolongator");
     const double omega = 4.0 / (3.0 * L.lmax);
     Bsr& P = L.P;
@@ -1396,13 +1422,9 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     L.r = dalloc<double>(n);
     L.d = dalloc<double>(n);
     L.t = dalloc<double>(n);
-    if (amg.mixed) {
-      make_float(L.A, s);
+    if (amg.mixed) {   // (A and dinv were copied to FP32 for the eigenvalue estimate)
       make_float(L.P, s);
       make_float(L.R, s);
-      L.dinvf = dalloc<float>(n);
-      count_launch();
-      k_to_float<<<grid_for(n, 256), 256, 0, s>>>(n, L.dinv, L.dinvf);
     }
     PFF_CUDA(cudaStreamSynchronize(s));
     dfree(dnorm);

@@ -63,6 +63,18 @@ __global__ void k_dot(const double* __restrict__ x, const double* __restrict__ y
   if (threadIdx.x == 0) part[blockIdx.x] = a;
 }
 
+// FP32 vectors: products summed in FP32 per thread, blocks and partials in FP64
+__global__ void k_dot_f32(const float* __restrict__ x, const float* __restrict__ y, int64_t n,
+                          double* __restrict__ part) {
+  __shared__ double sh[32];
+  float a = 0.f;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (int64_t)gridDim.x * blockDim.x)
+    a += x[i] * y[i];
+  const double s = block_sum((double)a, sh);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 __global__ void k_nrm_inf(const double* __restrict__ x, int64_t n, double* __restrict__ part) {
   __shared__ double sh[32];
   double a = 0.0;
@@ -274,6 +286,15 @@ void dot_dev(const double* x, const double* y, int64_t n, double* out, double* p
   k_dot<<<g, RB, 0, s>>>(x, y, n, partials);
   k_final<<<1, RB, 0, s>>>(partials, g, 0, 0, out);
   PFF_LAUNCH("dot");
+}
+
+void dot_dev_f32(const float* x, const float* y, int64_t n, double* out, double* partials,
+                 cudaStream_t s) {
+  const int g = red_grid(n);
+  ProfScope ps("dot_f32", (x == y ? 4.0 : 8.0) * n, s, 2);
+  k_dot_f32<<<g, RB, 0, s>>>(x, y, n, partials);
+  k_final<<<1, RB, 0, s>>>(partials, g, 0, 0, out);
+  PFF_LAUNCH("dot_f32");
 }
 
 void nrm_inf_dev(const double* x, int64_t n, double* out, double* partials, cudaStream_t s) {

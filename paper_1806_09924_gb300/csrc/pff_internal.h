@@ -186,6 +186,9 @@ void amg_vcycle(Amg& amg, const double* r, double* z, cudaStream_t s);
 void dot_dev(const double* x, const double* y, int64_t n, double* out, double* partials,
              cudaStream_t s);
 void nrm_inf_dev(const double* x, int64_t n, double* out, double* partials, cudaStream_t s);
+// <x, y> of FP32 vectors (FP32 products per thread, FP64 sums beyond)
+void dot_dev_f32(const float* x, const float* y, int64_t n, double* out, double* partials,
+                 cudaStream_t s);
 // Fused: out[k] = <V_k, w> for k < nv (V stored as nv vectors of stride ld).
 void multidot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* out,
                   double* partials, cudaStream_t s);
