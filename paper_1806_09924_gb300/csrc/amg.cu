@@ -685,23 +685,6 @@ __global__ void k_gj_elim(int n, int k, double* __restrict__ A, double* __restri
   if (threadIdx.x == 0) A[(int64_t)r * n + k] = 0.0;
 }
 
-// power-iteration step: y = D^-1 A x
-__global__ void k_dinv_spmv(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
-                            const double* __restrict__ val, const double* __restrict__ dinv,
-                            const double* __restrict__ x, double* __restrict__ y) {
-  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= (int64_t)n * b) return;
-  const int I = (int)(r / b), a = (int)(r % b);
-  double s = 0.0;
-  for (int k = rp[I]; k < rp[I + 1]; ++k) {
-    const double* v = val + ((int64_t)k * b + a) * b;
-    const double* xx = x + (int64_t)col[k] * b;
-    for (int c = 0; c < b; ++c) s += v[c] * xx[c];
-  }
-  y[r] = dinv[r] * s;
-}
-
-// y = D^-1/2 A D^-1/2 x (D = scalar diagonal, dinv = 1/D or 0)
 // Lanczos recurrence on S = D^-1/2 A D^-1/2 with every scalar kept on the device
 // (FP64 scalars; vectors in T = double, or float for mixed-precision hierarchies):
 // al[j] = <S v_j, v_j>, nb2[j] = ||w_j||^2, beta_j = sqrt(nb2[j])
@@ -744,12 +727,6 @@ template <class T>
 __global__ void k_hash_vec(int64_t n, T* __restrict__ x) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) x[i] = (T)((double)(hash32((uint32_t)i * 2654435761u + 12345u) & 0xffffff) / 16777216.0 + 0.1);
-}
-
-__global__ void k_scale(int64_t n, double* __restrict__ x, const double* __restrict__ nrm2) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const double s = *nrm2 > 0.0 ? 1.0 / sqrt(*nrm2) : 0.0;
-  if (i < n) x[i] *= s;
 }
 
 __global__ void k_to_float(int64_t n, const double* __restrict__ a, float* __restrict__ b) {

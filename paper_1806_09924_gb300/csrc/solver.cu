@@ -73,13 +73,6 @@ __global__ void k_sub(int64_t n, const double* __restrict__ a, const double* __r
   if (i < n) c[i] = a[i] - b[i];
 }
 
-// lam_i = |F_phi,i / m_i|
-__global__ void k_lambda(int64_t n, int dim, const double* __restrict__ F,
-                         const double* __restrict__ mass, double* __restrict__ out) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = fabs(F[(int64_t)dim * n + i] / mass[i]);
-}
-
 __global__ void k_count_ties(int64_t n, const double* __restrict__ ind, double tau,
                              int* __restrict__ cnt) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
