@@ -59,6 +59,9 @@ extern "C" {
 
 #define PFF_PC_AMG 0     /* block-diagonal preconditioner, one SA-AMG V-cycle per block */
 #define PFF_PC_JACOBI 1  /* point Jacobi (diagnostics only) */
+#define PFF_PC_AMG_TRI 2 /* block lower-triangular: the phase-field V-cycle acts on
+                            r_phi - M_phi_u z_u (uses the M_phi_u coupling the
+                            block-diagonal form of Section 3.1 leaves out) */
 
 typedef struct pff_problem pff_problem;
 

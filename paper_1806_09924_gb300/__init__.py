@@ -35,6 +35,7 @@ PFF_APPLY_ASSEMBLED = 1
 PFF_APPLY_MATFREE = 2
 PFF_PC_AMG = 0
 PFF_PC_JACOBI = 1
+PFF_PC_AMG_TRI = 2
 
 
 class PffOptions(ctypes.Structure):

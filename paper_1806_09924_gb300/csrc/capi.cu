@@ -169,6 +169,7 @@ void release(pff_problem* P) {
   dfree(P->gs_part);
   dfree(P->phit_built);
   dfree(P->active_built);
+  dfree(P->pc_tmp);
   if (P->side) {
     cudaStreamSynchronize(P->side);
     cudaStreamDestroy(P->side);
@@ -246,6 +247,8 @@ pff_options resolve_options(const pff_options* opts) {
   need(o.max_newton >= 0 && o.max_halvings >= 0, "negative iteration limit");
   need(o.tol_change >= 0.0 && o.tol_active >= 0.0, "negative active-set band");
   need(o.amg_reuse_tol >= 0.0, "negative amg_reuse_tol");
+  need(o.precond == PFF_PC_AMG || o.precond == PFF_PC_JACOBI || o.precond == PFF_PC_AMG_TRI,
+       "unknown precond");
   need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 1 || o.spmv_group == 2 ||
            o.spmv_group == 4 || o.spmv_group == 8 || o.spmv_group == 16 || o.spmv_group == 32 ||
            o.spmv_group == 64,
@@ -706,7 +709,8 @@ int pff_linear_solve_dev(pff_problem* P, const pff_options* opts, const double* 
   pff::AllocStream alloc_scope(P->stream);
   need(P->phi_assembled, "call pff_assemble first");
   const pff_options o = resolve_options(opts);
-  if (o.precond == PFF_PC_AMG) need(P->amg_u.built && P->amg_p.built, "call pff_precond_setup first");
+  if (o.precond != PFF_PC_JACOBI)
+    need(P->amg_u.built && P->amg_p.built, "call pff_precond_setup first");
   if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
     P->apply_variant = o.apply_variant;
   const int64_t N = P->n_dofs;

@@ -373,6 +373,7 @@ struct pff_problem {
   int krylov_m = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *tmp = nullptr;
   float* gs_part = nullptr;   // partial sums of the mixed-precision Gram-Schmidt
+  double* pc_tmp = nullptr;   // work vector of the block lower-triangular preconditioner
   double* h_host = nullptr;
 
   // Newton step state

@@ -348,9 +348,39 @@ void precond_apply(pff_problem* P, const double* r, double* z) {
   }
 }
 
+__global__ void k_tri_rhs(int64_t n, const double* __restrict__ S, const double* __restrict__ y,
+                          double* __restrict__ t) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) t[i] -= S[i] * y[i];
+}
+
+// block lower-triangular form: z_u = V_u (S_u r_u), then
+// z_phi = V_phi (S_phi (r_phi - [S^-1 G~ (z_u, 0)]_phi)) -- the exact coupling
+// M_phi_u z_u of the reduced Jacobian, through the ordinary Jacobian apply
+static void precond_apply_tri(pff_problem* P, const double* r, double* z) {
+  const int64_t N = P->n_dofs, nu = (int64_t)P->dim * P->n_nodes, np = N - nu;
+  const double* S = P->op_S ? P->op_S : P->S;
+  if (!P->pc_tmp) P->pc_tmp = dalloc<double>(N);
+  {
+    ProfScope ps("vec_mul", 24.0 * N, P->stream);
+    k_mul<<<grid_for(N, 256), 256, 0, P->stream>>>(N, S, r, P->tmp);
+  }
+  amg_vcycle(P->amg_u, P->tmp, z, P->stream);
+  PFF_CUDA(cudaMemcpyAsync(P->pc_tmp, z, sizeof(double) * nu, cudaMemcpyDeviceToDevice, P->stream));
+  PFF_CUDA(cudaMemsetAsync(P->pc_tmp + nu, 0, sizeof(double) * np, P->stream));
+  apply_jacobian(P, P->apply_variant, P->pc_tmp, P->w, P->op_Sinv ? P->op_Sinv : P->Sinv);
+  {
+    ProfScope ps("vec_sub", 24.0 * np, P->stream);
+    k_tri_rhs<<<grid_for(np, 256), 256, 0, P->stream>>>(np, S + nu, P->w + nu, P->tmp + nu);
+  }
+  amg_vcycle(P->amg_p, P->tmp + nu, z + nu, P->stream);
+}
+
 static void precond(pff_problem* P, const pff_options& o, const double* r, double* z) {
   if (o.precond == PFF_PC_JACOBI) {
     PFF_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * P->n_dofs, cudaMemcpyDeviceToDevice, P->stream));
+  } else if (o.precond == PFF_PC_AMG_TRI) {
+    precond_apply_tri(P, r, z);   // uses P->w: free until the Jacobian apply that follows
   } else {
     precond_apply(P, r, z);
   }

@@ -407,3 +407,17 @@ def test_krylov_iterations_nearly_independent_of_h():
     assert max(per_newton) <= 60, per_newton
     assert max(per_newton) <= 1.5 * min(per_newton), per_newton
 
+
+def test_block_triangular_preconditioner_reaches_the_same_solution():
+    """PFF_PC_AMG_TRI (the phase-field V-cycle sees r_phi - M_phi_u z_u) changes
+    the path of FGMRES, not the converged Newton solution."""
+    w = W.scaled_workload(W.config(1), 64)
+    out = []
+    for pc in (pff.PFF_PC_AMG, pff.PFF_PC_AMG_TRI):
+        P = pff.problem_from_workload(w)
+        reps = P.solve_loading_steps(w.pressures[:3], pff.options(precision=1, precond=pc))
+        assert all(r["converged"] == 1 for r in reps)
+        out.append(P.get_solution())
+        P.close()
+    assert rel(out[1][0], out[0][0]) <= 1e-9 and rel(out[1][1], out[0][1]) <= 1e-9
+
