@@ -16,9 +16,9 @@ cpu_baseline / --impl reference = the CPU oracle (oracle/) on a bounded sample
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        [--cells C]   (same recipe at C x C cells: small cases for profiler captures)
-       [--workload batched [--instances 256] [--workers 8]]
+       [--workload batched [--instances 256] [--workers 16]]
               256 independent 2d instances (32^2..512^2) through the batch executor
-       [--workload served [--requests 12] [--load 1.0] [--budget-gb 150] [--workers 8]]
+       [--workload served [--requests 12] [--load 1.0] [--budget-gb 150] [--workers 16]]
               a Poisson stream of mixed 2d / 3d 10-step requests through the server
 Multi-GPU runs (torchrun) are independent replicas: each rank solves its own
 copy of the workload; value sums the ranks' work over the slowest rank's time.
@@ -578,7 +578,7 @@ def main():
                     help="graded2d: the 1024^2 graded ramp (default line); batched: 256 independent "
                          "instances; served: a Poisson request stream")
     ap.add_argument("--instances", type=int, default=256)
-    ap.add_argument("--workers", type=int, default=8)
+    ap.add_argument("--workers", type=int, default=16)
     ap.add_argument("--requests", type=int, default=12)
     ap.add_argument("--load", type=float, default=1.0,
                     help="served: arrival rate as a multiple of the FP64 one-at-a-time service rate")

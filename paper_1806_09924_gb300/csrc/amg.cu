@@ -22,6 +22,7 @@
 //   V-cycle: Chebyshev(D^-1 A) pre/post smoothing, restriction, coarse solve,
 //   prolongation; FP64 or FP32 (mixed precision) values and vectors.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdio>
 #include <memory>
@@ -823,7 +824,8 @@ void coarse_cycle(Amg& amg, T* cb, T* cx, cudaStream_t s) {
     if (!ok) amg.use_graph = false;
   }
   if (amg.graph) {
-    ProfScope ps("coarse_levels_graph", 0.0, s, amg.graph_kernels);
+    ProfScope ps(amg.lev[0].A.br > 1 ? "coarse_levels_graph_u" : "coarse_levels_graph_phi", 0.0, s,
+                 amg.graph_kernels);
     PFF_CUDA(cudaGraphLaunch(amg.graph, s));
   } else {
     vcycle_level<T>(amg, 1, cb, cx, s);
@@ -896,7 +898,7 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
   T* cb = last ? reinterpret_cast<T*>(amg.cb) : reinterpret_cast<T*>(amg.lev[l + 1].b);
   T* cx = last ? reinterpret_cast<T*>(amg.cx) : reinterpret_cast<T*>(amg.lev[l + 1].x);
   spmv_t<T>(L.R, r, cb, T(1), T(0), s);
-  if (l == 0 && amg.use_graph) coarse_cycle<T>(amg, cb, cx, s);
+  if (l == 0 && amg.use_graph && !amg.inline_levels) coarse_cycle<T>(amg, cb, cx, s);
   else vcycle_level<T>(amg, l + 1, cb, cx, s);
   spmv_t<T>(L.P, cx, x, T(1), T(1), s);
   smooth<T>(L, amg.cheb_degree, amg.cheb_ratio, rhs, x, t, d, false, s);
@@ -1458,6 +1460,8 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
   }
   ph.stop();
   amg.built = 1;
+  static std::atomic<uint64_t> builds{0};
+  amg.build_id = ++builds;
   if (verbose()) {
     std::fprintf(stderr, "[pff] AMG (%s): %zu levels + coarse %d\n", amg.mixed ? "fp32" : "fp64",
                  amg.lev.size(), amg.nc);

@@ -175,6 +175,10 @@ void release(pff_problem* P) {
     cudaStreamDestroy(P->side);
     P->side = nullptr;
   }
+  if (P->iter_graph) cudaGraphExecDestroy(P->iter_graph);
+  P->iter_graph = nullptr;
+  dfree(P->g_in);
+  dfree(P->g_out);
   if (P->ev_fork) cudaEventDestroy(P->ev_fork);
   if (P->ev_join) cudaEventDestroy(P->ev_join);
   P->ev_fork = P->ev_join = nullptr;
@@ -284,6 +288,7 @@ void pff_default_options(pff_options* o) {
   o->amg_reuse = 1;
   o->amg_reuse_tol = 0.05;
   o->precond_overlap = 1;
+  o->iter_graph = 1;
 }
 
 const char* pff_last_error(void) { return pff::g_msg.c_str(); }

@@ -150,8 +150,10 @@ struct Amg {
   int cheb_degree = 2;
   double cheb_ratio = 30.0;
   int built = 0;
+  uint64_t build_id = 0;      // distinct for every build (process-wide counter)
   // levels 1.. captured as one CUDA graph (see coarse_cycle in amg.cu)
   bool use_graph = true;
+  bool inline_levels = false; // run levels 1.. as ordinary launches (inside an outer capture)
   cudaGraphExec_t graph = nullptr;
   int graph_kernels = 0;
   cudaStream_t cap_stream = nullptr;
@@ -374,6 +376,12 @@ struct pff_problem {
   double *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *tmp = nullptr;
   float* gs_part = nullptr;   // partial sums of the mixed-precision Gram-Schmidt
   double* pc_tmp = nullptr;   // work vector of the block lower-triangular preconditioner
+  // one FGMRES iteration's device work (preconditioner + Jacobian apply) as a
+  // CUDA graph on fixed buffers, for problems small enough to be launch-bound
+  cudaGraphExec_t iter_graph = nullptr;
+  int iter_graph_kernels = 0;
+  double *g_in = nullptr, *g_out = nullptr;
+  uint64_t iter_key[8] = {0, 0, 0, 0, 0, 0, 0, 0};
   double* h_host = nullptr;
 
   // Newton step state

@@ -376,6 +376,74 @@ static void precond_apply_tri(pff_problem* P, const double* r, double* z) {
   amg_vcycle(P->amg_p, P->tmp + nu, z + nu, P->stream);
 }
 
+// The device work of one FGMRES iteration -- z = M v (preconditioner) and
+// w = S^-1 G~ z (Jacobian apply) -- captured once as a CUDA graph on the fixed
+// buffers g_in (v) and g_out (z), and recaptured whenever something it embeds
+// changes (a hierarchy build, the scaling vectors, the apply variant, the
+// precision or the stream overlap).  Small problems are launch-bound: the graph
+// turns about 25 launches per iteration into one.  Returns false when the
+// graph cannot be used (capture failed); the caller then launches directly.
+constexpr int64_t ITER_GRAPH_MAX_DOFS = 1000000;
+
+static bool iteration_graph(pff_problem* P, const pff_options& o) {
+  const uint64_t key[8] = {P->amg_u.build_id, P->amg_p.build_id,
+                           (uint64_t)(uintptr_t)(P->op_S ? P->op_S : P->S),
+                           (uint64_t)(uintptr_t)(P->op_Sinv ? P->op_Sinv : P->Sinv),
+                           (uint64_t)P->apply_variant, (uint64_t)P->precision,
+                           (uint64_t)P->overlap, (uint64_t)(uintptr_t)P->stream};
+  if (P->iter_graph && std::equal(key, key + 8, P->iter_key)) return true;
+  if (P->iter_graph) {
+    cudaGraphExecDestroy(P->iter_graph);
+    P->iter_graph = nullptr;
+  }
+  const int64_t N = P->n_dofs;
+  if (!P->g_in) P->g_in = dalloc<double>(N);
+  if (!P->g_out) P->g_out = dalloc<double>(N);
+  cudaStream_t s = P->stream;
+  if (!s) return false;   // the legacy default stream cannot be captured
+  if (P->overlap && !P->side) {
+    PFF_CUDA(cudaStreamCreateWithFlags(&P->side, cudaStreamNonBlocking));
+    PFF_CUDA(cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming));
+    PFF_CUDA(cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming));
+  }
+  bool ok = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+  cudaGraph_t g = nullptr;
+  if (ok) {
+    P->amg_u.inline_levels = P->amg_p.inline_levels = true;
+    set_capturing(true);
+    try {
+      precond_apply(P, P->g_in, P->g_out);
+      apply_jacobian(P, P->apply_variant, P->g_out, P->w, P->op_Sinv ? P->op_Sinv : P->Sinv);
+    } catch (...) {
+      ok = false;
+    }
+    set_capturing(false);
+    P->amg_u.inline_levels = P->amg_p.inline_levels = false;
+    if (cudaStreamEndCapture(s, &g) != cudaSuccess) ok = false;
+  }
+  if (ok && g) {
+    size_t nn = 0;
+    cudaGraphGetNodes(g, nullptr, &nn);
+    std::vector<cudaGraphNode_t> nodes(nn);
+    cudaGraphGetNodes(g, nodes.data(), &nn);
+    int kern = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kern;
+    }
+    P->iter_graph_kernels = kern;
+    if (cudaGraphInstantiate(&P->iter_graph, g, 0) != cudaSuccess) {
+      P->iter_graph = nullptr;
+      ok = false;
+    }
+  }
+  if (g) cudaGraphDestroy(g);
+  cudaGetLastError();
+  if (!ok) return false;
+  std::copy(key, key + 8, P->iter_key);
+  return true;
+}
+
 static void precond(pff_problem* P, const pff_options& o, const double* r, double* z) {
   if (o.precond == PFF_PC_JACOBI) {
     PFF_CUDA(cudaMemcpyAsync(z, r, sizeof(double) * P->n_dofs, cudaMemcpyDeviceToDevice, P->stream));
@@ -408,6 +476,7 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
   const unsigned g = grid_for(N, 256);
   const bool gs_mixed = P->precision == PFF_PREC_MIXED && m + 1 <= 64 &&
                         N <= (int64_t)GS_MAX_ROWS * GS_MAX_BLOCKS;
+  const bool use_iter_graph = o.precond == PFF_PC_AMG && N <= ITER_GRAPH_MAX_DOFS && o.iter_graph != 0;
   PFF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
   dot_dev(b, b, N, P->d_scalars, P->partials, s);
   const double beta0 = std::sqrt(fetch(P, P->d_scalars));
@@ -432,8 +501,17 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
     for (; j < m; ++j) {
       double* vj = V + (int64_t)j * N;
       double* zj = Z + (int64_t)j * N;
-      precond(P, o, vj, zj);
-      apply_jacobian(P, P->apply_variant, zj, w, P->op_Sinv ? P->op_Sinv : P->Sinv);
+      if (use_iter_graph && iteration_graph(P, o)) {
+        PFF_CUDA(cudaMemcpyAsync(P->g_in, vj, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+        {
+          ProfScope ps("iteration_graph", 0.0, s, P->iter_graph_kernels);
+          PFF_CUDA(cudaGraphLaunch(P->iter_graph, s));
+        }
+        PFF_CUDA(cudaMemcpyAsync(zj, P->g_out, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
+      } else {
+        precond(P, o, vj, zj);
+        apply_jacobian(P, P->apply_variant, zj, w, P->op_Sinv ? P->op_Sinv : P->Sinv);
+      }
       double hn = 0.0;
       if (gs_mixed) {
         // dh[0..j] = h, dh[j+1] = ||w||^2; dh[2(m+2)] = ||w - V h||^2

@@ -79,6 +79,26 @@ def test_batch_solve_matches_one_at_a_time_and_oracle():
         P.close()
 
 
+def test_iteration_graph_gives_the_direct_launch_result():
+    """On a non-default stream a small problem runs each FGMRES iteration's
+    preconditioner and Jacobian apply as one CUDA graph: the same kernels in the
+    same order, so the solution is bit-identical to ordinary launches."""
+    w = W.scaled_workload(W.config(1), 96)
+    stream = torch.cuda.Stream()
+    out = []
+    for g in (0, 1):
+        P = pff.problem_from_workload(w)
+        P.set_stream(stream)
+        reps = P.solve_loading_steps(w.pressures[:3], pff.options(precision=1, iter_graph=g))
+        assert all(r["converged"] == 1 for r in reps)
+        out.append((P.get_solution(), [r["krylov_its"] for r in reps]))
+        P.close()
+    (u0, phi0, a0), k0 = out[0]
+    (u1, phi1, a1), k1 = out[1]
+    assert k0 == k1
+    assert np.array_equal(u0, u1) and np.array_equal(phi0, phi1) and np.array_equal(a0, a1)
+
+
 def test_server_result_is_the_same_alone_and_in_the_mix():
     reqs = small_requests()
     opts = pff.options(precision=pff.PFF_PREC_MIXED)
