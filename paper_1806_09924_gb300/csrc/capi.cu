@@ -509,6 +509,7 @@ int pff_newton_step(pff_problem* P, const pff_options* opts, pff_step_report* re
   const pff_options o = resolve_options(opts);
   if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
     P->apply_variant = o.apply_variant;
+  P->apply_auto = o.apply_variant == PFF_APPLY_AUTO;
   const int rc = pff::newton_iteration(P, o, rep);
   if (rc != PFF_OK) {
     pff::set_error(rc, "Newton iteration failed");
@@ -533,6 +534,7 @@ int pff_solve_loading_steps(pff_problem* P, int n_steps, const double* p_schedul
   const pff_options o = resolve_options(opts);
   if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
     P->apply_variant = o.apply_variant;
+  P->apply_auto = o.apply_variant == PFF_APPLY_AUTO;
   int rc_all = PFF_OK;
   for (int st = 0; st < n_steps; ++st) {
     const auto t0 = std::chrono::steady_clock::now();
@@ -718,6 +720,7 @@ int pff_linear_solve_dev(pff_problem* P, const pff_options* opts, const double* 
     need(P->amg_u.built && P->amg_p.built, "call pff_precond_setup first");
   if (o.apply_variant == PFF_APPLY_MATFREE || o.apply_variant == PFF_APPLY_ASSEMBLED)
     P->apply_variant = o.apply_variant;
+  P->apply_auto = o.apply_variant == PFF_APPLY_AUTO;
   const int64_t N = P->n_dofs;
   pff::ensure_krylov(P, std::max(2, o.krylov_restart));
   // scaled right-hand side Sinv .* b into scratch, solution into x

@@ -391,6 +391,7 @@ struct pff_problem {
   int k = 0;
   double rho0 = 0.0;
   int apply_variant = PFF_APPLY_ASSEMBLED;
+  bool apply_auto = false;         // PFF_APPLY_AUTO requested: time both applies once
   bool apply_tuned = false;
   pff_step_report cur{};
 

@@ -19,6 +19,8 @@
 // S = diag(M_uu(phi~)) (+ diag G_c(M/eps + eps K) for phi) is fixed during a
 // loading step, so the reduced residual norms of different iterates compare.
 #include <algorithm>
+#include <mutex>
+#include <map>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -209,6 +211,53 @@ static int64_t count_diff(pff_problem* P, const uint8_t* a, const uint8_t* b, in
                            P->stream));
   PFF_CUDA(cudaStreamSynchronize(P->stream));
   return P->h_counters[4];
+}
+
+// PFF_APPLY_AUTO: the assembled-stencil and the matrix-free FP64 Jacobian apply
+// compute the same product; time each on this problem once (3 launches after a
+// warm one, CUDA events on the problem's stream) and keep the faster.  The
+// choice is remembered per (dimension, log2 node count) for later problems.
+static void choose_apply(pff_problem* P) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, int> cache;
+  const auto key = std::make_pair(P->dim, (int)std::log2((double)std::max<int64_t>(1, P->n_nodes)));
+  {
+    std::lock_guard<std::mutex> g(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) {
+      P->apply_variant = it->second;
+      P->apply_auto = false;
+      return;
+    }
+  }
+  cudaEvent_t e0, e1;
+  PFF_CUDA(cudaEventCreate(&e0));
+  PFF_CUDA(cudaEventCreate(&e1));
+  const double* Si = P->op_Sinv ? P->op_Sinv : P->Sinv;
+  float best_ms = 1e30f;
+  int best = PFF_APPLY_ASSEMBLED;
+  for (int v : {PFF_APPLY_ASSEMBLED, PFF_APPLY_MATFREE}) {
+    apply_jacobian(P, v, P->F, P->tmp, Si);
+    PFF_CUDA(cudaEventRecord(e0, P->stream));
+    for (int r = 0; r < 3; ++r) apply_jacobian(P, v, P->F, P->tmp, Si);
+    PFF_CUDA(cudaEventRecord(e1, P->stream));
+    PFF_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.f;
+    PFF_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    if (verbose())
+      std::fprintf(stderr, "[pff] Jacobian apply %s: %.1f us\n",
+                   v == PFF_APPLY_ASSEMBLED ? "assembled" : "matrix-free", 1e3 * ms / 3);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = v;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  P->apply_variant = best;
+  P->apply_auto = false;
+  std::lock_guard<std::mutex> g(mu);
+  cache[key] = best;
 }
 
 // max_i |a_i - b_i| (device vectors of length n <= n_dofs)
@@ -705,6 +754,7 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   }
   // 4. reduced Jacobian and right-hand side
   assemble_all(P);
+  if (P->apply_auto) choose_apply(P);
 
   precond_setup(P, o, true);
   // 5. linear solve on the scaled system.  The displacement and phase-field
