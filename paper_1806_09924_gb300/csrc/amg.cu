@@ -588,6 +588,150 @@ __global__ void k_mm_fill(int n, int xr, int xc, int yc, const int* __restrict__
   }
 }
 
+// ---- warp-per-row SpGEMM C = X Y (set-up Galerkin products) ---------------
+// One warp per row of X.  Symbolic: the candidate columns (columns of the Y
+// rows named by the row of X) go into a shared-memory hash set, which keeps
+// each column once whatever the insertion order.  Numeric: the unique columns
+// are compacted, sorted (bitonic, in shared memory) and written, and the block
+// products are added into the output row in the fixed order of the row of X
+// and the rows of Y, lanes splitting each block -- no atomics on values, so
+// the result is deterministic.  A row with more than MM_HS/2 unique columns
+// sets *overflow (the caller then uses the row-per-thread kernels).
+constexpr int MM_WS = 4;      // warps per block
+constexpr int MM_HS = 1024;   // hash slots per warp
+
+__device__ __forceinline__ int mm_insert(int* h, int c, bool* full) {
+  unsigned slot = ((unsigned)c * 2654435761u) & (MM_HS - 1);
+  for (int t = 0; t < MM_HS; ++t) {
+    const int old = atomicCAS(&h[slot], -1, c);
+    if (old == -1) return 1;
+    if (old == c) return 0;
+    slot = (slot + 1) & (MM_HS - 1);
+  }
+  *full = true;
+  return 0;
+}
+
+__device__ __forceinline__ int warp_sum_int(int v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// fill h (cleared by the caller) with the columns of row I of X Y; returns the count
+__device__ int mm_gather(int I, const int* __restrict__ xrp, const int* __restrict__ xcol,
+                         const int* __restrict__ yrp, const int* __restrict__ ycol, int* h,
+                         bool* full) {
+  const int lane = threadIdx.x & 31;
+  int ins = 0;
+  for (int k = xrp[I]; k < xrp[I + 1]; ++k) {
+    const int K = xcol[k];
+    for (int l = yrp[K] + lane; l < yrp[K + 1]; l += 32) ins += mm_insert(h, ycol[l], full);
+  }
+  __syncwarp();
+  return warp_sum_int(ins);
+}
+
+__global__ void __launch_bounds__(32 * MM_WS) k_mm_count_w(int n, const int* __restrict__ xrp,
+                                                          const int* __restrict__ xcol,
+                                                          const int* __restrict__ yrp,
+                                                          const int* __restrict__ ycol,
+                                                          int* __restrict__ cnt,
+                                                          int* __restrict__ overflow) {
+  __shared__ int hs[MM_WS][MM_HS];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int I = blockIdx.x * MM_WS + w;
+  int* h = hs[w];
+  for (int e = lane; e < MM_HS; e += 32) h[e] = -1;
+  __syncwarp();
+  if (I >= n) return;   // the whole warp leaves together
+  bool full = false;
+  const int c = mm_gather(I, xrp, xcol, yrp, ycol, h, &full);
+  const bool bad = __any_sync(0xffffffffu, full) || c > MM_HS / 2;
+  if (lane == 0) {
+    cnt[I] = c;
+    if (bad) atomicExch(overflow, 1);
+  }
+}
+
+__global__ void __launch_bounds__(32 * MM_WS) k_mm_fill_w(int n, int xr, int xc, int yc,
+                                                         const int* __restrict__ xrp,
+                                                         const int* __restrict__ xcol,
+                                                         const double* __restrict__ xval,
+                                                         const int* __restrict__ yrp,
+                                                         const int* __restrict__ ycol,
+                                                         const double* __restrict__ yval,
+                                                         const int* __restrict__ crp,
+                                                         int* __restrict__ ccol,
+                                                         double* __restrict__ cval) {
+  __shared__ int hs[MM_WS][MM_HS];
+  __shared__ int ls[MM_WS][MM_HS / 2];
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int I = blockIdx.x * MM_WS + w;
+  int* h = hs[w];
+  int* list = ls[w];
+  for (int e = lane; e < MM_HS; e += 32) h[e] = -1;
+  __syncwarp();
+  if (I >= n) return;
+  bool full = false;
+  const int cnt = mm_gather(I, xrp, xcol, yrp, ycol, h, &full);   // = crp[I+1] - crp[I]
+  // compact the keys, then sort them (padded to a power of two with INT_MAX)
+  int m = 1;
+  while (m < cnt) m <<= 1;
+  int base = 0;
+  for (int e0 = 0; e0 < MM_HS; e0 += 32) {
+    const int key = h[e0 + lane];
+    const unsigned b = __ballot_sync(0xffffffffu, key >= 0);
+    if (key >= 0) list[base + __popc(b & ((1u << lane) - 1u))] = key;
+    base += __popc(b);
+  }
+  for (int e = cnt + lane; e < m; e += 32) list[e] = 0x7fffffff;
+  __syncwarp();
+  for (int k = 2; k <= m; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = lane; i < m; i += 32) {
+        const int p = i ^ j;
+        if (p > i) {
+          const bool up = (i & k) == 0;
+          const int a = list[i], b2 = list[p];
+          if ((a > b2) == up) {
+            list[i] = b2;
+            list[p] = a;
+          }
+        }
+      }
+      __syncwarp();
+    }
+  const int c0 = crp[I];
+  const int bs = xr * yc;
+  for (int e = lane; e < cnt; e += 32) ccol[c0 + e] = list[e];
+  for (int e = lane; e < cnt * bs; e += 32) cval[(int64_t)c0 * bs + e] = 0.0;
+  __syncwarp();
+  // block products in the fixed order of X's row and Y's rows
+  for (int k = xrp[I]; k < xrp[I + 1]; ++k) {
+    const int K = xcol[k];
+    const double* Xb = xval + (int64_t)k * xr * xc;
+    for (int l = yrp[K]; l < yrp[K + 1]; ++l) {
+      const int c = ycol[l];
+      int lo = 0, hi = cnt;   // every lane finds the same slot
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (list[mid] < c) lo = mid + 1;
+        else hi = mid;
+      }
+      const double* Yb = yval + (int64_t)l * xc * yc;
+      double* Cb = cval + (int64_t)(c0 + lo) * bs;
+      for (int e = lane; e < bs; e += 32) {
+        const int r = e / yc, cc = e - r * yc;
+        double s = 0.0;
+        for (int q = 0; q < xc; ++q) s += Xb[r * xc + q] * Yb[q * yc + cc];
+        Cb[e] += s;
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // zero diagonal entries (dead coarse DoFs) -> 1
 __global__ void k_fix_diag(int n, int b, const int* __restrict__ rp, const int* __restrict__ col,
                            double* __restrict__ val) {
@@ -1036,19 +1180,36 @@ void spgemm(const Bsr& X, const Bsr& Y, Bsr& C, int* err, cudaStream_t s) {
   C.br = X.br;
   C.bc = Y.bc;
   C.rowptr = dalloc<int>(X.nrows + 1);
-  int* cnt = dalloc<int>(X.nrows + 1);
-  const unsigned g = grid_for(X.nrows, 128);
+  int* cnt = dalloc<int>(X.nrows + 2);
+  int* overflow = cnt + X.nrows + 1;
+  PFF_CUDA(cudaMemsetAsync(overflow, 0, sizeof(int), s));
+  // warp-per-row kernels first; rows wider than their shared tables fall back
+  const unsigned gw = (unsigned)((X.nrows + MM_WS - 1) / MM_WS);
   count_launch();
-  k_mm_count<<<g, 128, 0, s>>>(X.nrows, X.rowptr, X.col, Y.rowptr, Y.col, cnt, err);
-  PFF_LAUNCH("mm_count");
+  k_mm_count_w<<<gw, 32 * MM_WS, 0, s>>>(X.nrows, X.rowptr, X.col, Y.rowptr, Y.col, cnt, overflow);
+  PFF_LAUNCH("mm_count_w");
+  int h_over = 0;
+  PFF_CUDA(cudaMemcpyAsync(&h_over, overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PFF_CUDA(cudaStreamSynchronize(s));
+  const unsigned g = grid_for(X.nrows, 128);
+  if (h_over) {
+    count_launch();
+    k_mm_count<<<g, 128, 0, s>>>(X.nrows, X.rowptr, X.col, Y.rowptr, Y.col, cnt, err);
+    PFF_LAUNCH("mm_count");
+  }
   int total = 0;
   exclusive_scan_int(cnt, C.rowptr, X.nrows, &total, s);
   C.nnzb = total;
   C.col = dalloc<int>(total);
   C.val = dalloc<double>((size_t)total * C.br * C.bc);
   count_launch();
-  k_mm_fill<<<g, 128, 0, s>>>(X.nrows, X.br, X.bc, Y.bc, X.rowptr, X.col, X.val, Y.rowptr, Y.col,
-                              Y.val, C.rowptr, C.col, C.val);
+  if (h_over) {
+    k_mm_fill<<<g, 128, 0, s>>>(X.nrows, X.br, X.bc, Y.bc, X.rowptr, X.col, X.val, Y.rowptr,
+                                Y.col, Y.val, C.rowptr, C.col, C.val);
+  } else {
+    k_mm_fill_w<<<gw, 32 * MM_WS, 0, s>>>(X.nrows, X.br, X.bc, Y.bc, X.rowptr, X.col, X.val,
+                                          Y.rowptr, Y.col, Y.val, C.rowptr, C.col, C.val);
+  }
   PFF_LAUNCH("mm_fill");
   dfree(cnt);
 }
