@@ -598,7 +598,8 @@ __global__ void k_mm_fill(int n, int xr, int xc, int yc, const int* __restrict__
 // the result is deterministic.  A row with more than MM_HS/2 unique columns
 // sets *overflow (the caller then uses the row-per-thread kernels).
 constexpr int MM_WS = 4;      // warps per block
-constexpr int MM_HS = 1024;   // hash slots per warp
+constexpr int MM_HS = 1024;   // hash slots per warp (rows of up to 512 unique columns; the
+                              // 3d hierarchies stay below, and wider tables cost occupancy)
 
 __device__ __forceinline__ int mm_insert(int* h, int c, bool* full) {
   unsigned slot = ((unsigned)c * 2654435761u) & (MM_HS - 1);
@@ -1192,6 +1193,9 @@ void spgemm(const Bsr& X, const Bsr& Y, Bsr& C, int* err, cudaStream_t s) {
   PFF_CUDA(cudaMemcpyAsync(&h_over, overflow, sizeof(int), cudaMemcpyDeviceToHost, s));
   PFF_CUDA(cudaStreamSynchronize(s));
   const unsigned g = grid_for(X.nrows, 128);
+  if (h_over && verbose())
+    std::fprintf(stderr, "[pff] SpGEMM %d rows: a row exceeds %d columns, row-per-thread kernels\n",
+                 X.nrows, MM_HS / 2);
   if (h_over) {
     count_launch();
     k_mm_count<<<g, 128, 0, s>>>(X.nrows, X.rowptr, X.col, Y.rowptr, Y.col, cnt, err);
