@@ -106,6 +106,7 @@ typedef struct pff_options {
   int precond_overlap;  /* 1: the displacement and phase-field V-cycles of the block
                            preconditioner run concurrently on two streams; 0: one after the
                            other; 1 */
+  int cheb_degree_coarse; /* Chebyshev degree on AMG levels >= 1; 0 = cheb_degree; 0 */
   int iter_graph;       /* 1: problems up to 10^6 DoFs on a non-default stream run each
                            FGMRES iteration's preconditioner and Jacobian apply as one CUDA
                            graph (same kernels, same order); 0: ordinary launches; 1 */

@@ -1027,9 +1027,10 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
   T* t = reinterpret_cast<T*>(L.t);
   T* d = reinterpret_cast<T*>(L.d);
   T* r = reinterpret_cast<T*>(L.r);
-  smooth<T>(L, amg.cheb_degree, amg.cheb_ratio, rhs, x, t, d, true, s);
+  const int deg = l == 0 ? amg.cheb_degree : amg.cheb_degree_coarse;
+  smooth<T>(L, deg, amg.cheb_ratio, rhs, x, t, d, true, s);
   if (L.terminal) {
-    smooth<T>(L, amg.cheb_degree, amg.cheb_ratio, rhs, x, t, d, false, s);
+    smooth<T>(L, deg, amg.cheb_ratio, rhs, x, t, d, false, s);
     return;
   }
   const Bsr& A = L.A;
@@ -1046,7 +1047,7 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
   if (l == 0 && amg.use_graph && !amg.inline_levels) coarse_cycle<T>(amg, cb, cx, s);
   else vcycle_level<T>(amg, l + 1, cb, cx, s);
   spmv_t<T>(L.P, cx, x, T(1), T(1), s);
-  smooth<T>(L, amg.cheb_degree, amg.cheb_ratio, rhs, x, t, d, false, s);
+  smooth<T>(L, deg, amg.cheb_ratio, rhs, x, t, d, false, s);
 }
 
 struct SetupScratch {
@@ -1342,6 +1343,7 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
   amg.release();
   amg.mixed = prm.mixed;
   amg.cheb_degree = prm.cheb_degree;
+  amg.cheb_degree_coarse = prm.cheb_degree_coarse;
   amg.cheb_ratio = prm.cheb_ratio;
   amg.use_graph = prm.use_graph;
   SetupScratch sc;

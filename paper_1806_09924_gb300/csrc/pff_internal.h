@@ -148,6 +148,7 @@ struct Amg {
   double *cx = nullptr, *cb = nullptr;
   bool mixed = false;
   int cheb_degree = 2;
+  int cheb_degree_coarse = 2;  // levels >= 1
   double cheb_ratio = 30.0;
   int built = 0;
   uint64_t build_id = 0;      // distinct for every build (process-wide counter)
@@ -164,6 +165,7 @@ struct AmgParams {
   double theta = 0.08;
   int coarse_max = 320;
   int cheb_degree = 2;
+  int cheb_degree_coarse = 2;
   double cheb_ratio = 30.0;
   bool mixed = false;
   int max_levels = 20;

@@ -282,6 +282,7 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   ap.theta = o.amg_theta;
   ap.coarse_max = o.amg_coarse_max;
   ap.cheb_degree = o.cheb_degree;
+  ap.cheb_degree_coarse = o.cheb_degree_coarse > 0 ? o.cheb_degree_coarse : o.cheb_degree;
   ap.cheb_ratio = o.cheb_ratio > 1.0 ? o.cheb_ratio : 30.0;
   ap.coords = P->xyz;
   ap.coord_dim = P->dim;
