@@ -48,7 +48,8 @@ class PffOptions(ctypes.Structure):
         ("cheb_ratio", ctypes.c_double), ("tol_active", ctypes.c_double),
         ("atol_newton", ctypes.c_double), ("tol_change", ctypes.c_double),
         ("spmv_group", ctypes.c_int), ("amg_reuse", ctypes.c_int), ("amg_reuse_tol", ctypes.c_double),
-        ("precond_overlap", ctypes.c_int), ("cheb_degree_coarse", ctypes.c_int), ("iter_graph", ctypes.c_int),
+        ("precond_overlap", ctypes.c_int), ("cheb_degree_coarse", ctypes.c_int),
+        ("forcing_max", ctypes.c_double), ("iter_graph", ctypes.c_int),
     ]
 
 

@@ -251,6 +251,7 @@ pff_options resolve_options(const pff_options* opts) {
   need(o.max_newton >= 0 && o.max_halvings >= 0, "negative iteration limit");
   need(o.tol_change >= 0.0 && o.tol_active >= 0.0, "negative active-set band");
   need(o.amg_reuse_tol >= 0.0, "negative amg_reuse_tol");
+  need(o.forcing_max >= 0.0 && o.forcing_max < 1.0, "forcing_max must be in [0, 1)");
   need(o.precond == PFF_PC_AMG || o.precond == PFF_PC_JACOBI || o.precond == PFF_PC_AMG_TRI,
        "unknown precond");
   need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 1 || o.spmv_group == 2 ||

@@ -371,6 +371,7 @@ struct pff_problem {
   bool amg_p_valid = false;      // false: the phase-field hierarchy must be rebuilt
   uint8_t* active_built = nullptr;  // active set the phase-field hierarchy was built for
   int phi_amg_age = 0;           // Newton iterations since the last build
+  double rho_last = 0.0;         // scaled reduced residual of the previous Newton iteration
   int precision = PFF_PREC_FP64;
 
   // Krylov workspace

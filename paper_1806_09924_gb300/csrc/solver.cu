@@ -780,7 +780,21 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   P->op_S = P->Sw;
   P->op_Sinv = P->Sinvw;
   int its = 0;
-  const int lrc = fgmres(P, o, P->Ftrial, P->dU, &its);
+  // linear tolerance: fixed tol_linear, or (forcing_max > 0) the Eisenstat-Walker
+  // forcing term eta_k = gamma (rho_k / rho_{k-1})^2 within [tol_linear, forcing_max],
+  // eta_0 = forcing_max: early Newton steps need no accurate linear solve; the
+  // Newton stopping test alone decides the accuracy of the converged solution
+  pff_options ol = o;
+  if (o.forcing_max > 0.0) {
+    double eta = o.forcing_max;
+    if (P->k > 0 && P->rho_last > 0.0) {
+      const double q = rho_inf / P->rho_last;
+      eta = std::min(o.forcing_max, 0.9 * q * q);
+    }
+    ol.tol_linear = std::max(o.tol_linear, eta);
+  }
+  P->rho_last = rho_inf;
+  const int lrc = fgmres(P, ol, P->Ftrial, P->dU, &its);
   P->op_S = nullptr;
   P->op_Sinv = nullptr;
   R.krylov_its += its;
