@@ -170,6 +170,7 @@ void release(pff_problem* P) {
   dfree(P->phit_built);
   dfree(P->active_built);
   dfree(P->pc_tmp);
+  dfree(P->qp);
   if (P->side) {
     cudaStreamSynchronize(P->side);
     cudaStreamDestroy(P->side);
@@ -378,6 +379,7 @@ pff_problem* create_problem(int dim, const int32_t* n_cells, const double* const
     P->Kuu = dalloc<double>((size_t)NS * dim * dim * n);
     P->Kpu = dalloc<double>((size_t)NS * dim * n);
     P->Kpp = dalloc<double>((size_t)NS * n);
+    P->qp = dalloc<double>((size_t)pff::qp_doubles(dim, P->n_cells));
     P->F = dalloc<double>(N);
     P->Ft = dalloc<double>(N);
     P->dU = dalloc<double>(N);

@@ -128,97 +128,167 @@ __device__ __forceinline__ int slot_of(int c, int b) {
 
 // ------------------------------------------------------------- residual ---
 // F = -r(U), r = left-hand sides of Eq. (E22ATW) / (E33ATW) tested with chi_i.
+//
+// Two passes.  k_residual_qp evaluates, once per cell and Gauss point q, every
+// quantity the test functions are integrated against, already scaled by the
+// quadrature weight and the inverse edge lengths:
+//   T[a][l] = JxW (g(phi~) sigma(u)[a][l] + phi^2 p delta_al) / h_l   (stress + pressure)
+//   s0      = JxW ((1-kappa) phi sigma:e + 2 phi p div u - G_c/eps (1-phi))
+//   gg[l]   = JxW G_c eps (d phi / dx_l) / h_l
+// so that node a of the cell receives  r_u[a'] += sum_l T[a'][l] dN_a/dxi_l  and
+// r_phi += s0 N_a + sum_l gg[l] dN_a/dxi_l  (reference-cell derivatives).
+// k_residual_gather then sums, for each node, its 2^d cells' records in a fixed
+// order.  Records are stored slot-major (QP[(q R + r) n_cells + cell]) so both
+// passes read and write coalesced.
 template <int D>
-__global__ void __launch_bounds__(BLK) k_residual(MeshDev m, Material mat, int64_t n,
-                                                  const double* __restrict__ u,
-                                                  const double* __restrict__ phi,
-                                                  const double* __restrict__ phit,
-                                                  double* __restrict__ F) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  constexpr int NA = 1 << D;
+__host__ __device__ constexpr int res_rec() { return D * D + D + 1; }
+
+template <int D>
+__device__ __forceinline__ void cell_index(int64_t cl, const MeshDev& m, int* ci) {
+  ci[0] = (int)(cl % m.nc[0]);
+  const int64_t r = cl / m.nc[0];
+  if (D == 2) {
+    ci[1] = (int)r;
+  } else {
+    ci[1] = (int)(r % m.nc[1]);
+    ci[2] = (int)(r / m.nc[1]);
+  }
+}
+
+template <int D>
+__device__ __forceinline__ int64_t cell_of(const int* ci, const MeshDev& m) {
+  int64_t r = ci[0] + (int64_t)m.nc[0] * ci[1];
+  if (D == 3) r += (int64_t)m.nc[0] * m.nc[1] * ci[2];
+  return r;
+}
+
+// Cell adjacent to node idx at offset c (bit l = cell index - node index + 1);
+// false outside the mesh.
+template <int D>
+__device__ __forceinline__ bool adjacent_cell_index(const int* idx, int c, const MeshDev& m,
+                                                    int* ci) {
+  bool in = true;
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    ci[l] = idx[l] - 1 + ((c >> l) & 1);
+    in &= (ci[l] >= 0) & (ci[l] < m.nc[l]);
+  }
+  return in;
+}
+
+template <int D>
+__global__ void __launch_bounds__(BLK) k_residual_qp(MeshDev m, Material mat, int64_t ncell,
+                                                     const double* __restrict__ u,
+                                                     const double* __restrict__ phi,
+                                                     const double* __restrict__ phit,
+                                                     double* __restrict__ QP) {
+  const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cl >= ncell) return;
+  constexpr int NA = 1 << D, R = res_rec<D>();
   const double wq = D == 2 ? 0.25 : 0.125;
-  int idx[3];
-  node_index<D>(i, m, idx);
-  double ru[D];
+  int ci[3];
+  cell_index<D>(cl, m, ci);
+  double ih[D], vol = 1.0;
 #pragma unroll
-  for (int a = 0; a < D; ++a) ru[a] = 0.0;
-  double rp = 0.0;
+  for (int l = 0; l < D; ++l) {
+    const double h = m.X[l][ci[l] + 1] - m.X[l][ci[l]];
+    ih[l] = 1.0 / h;
+    vol *= h;
+  }
+  double ue[NA][D], pe[NA], te[NA];
+#pragma unroll
+  for (int b = 0; b < NA; ++b) {
+    const int64_t nb = cell_node<D>(ci, b, m);
+#pragma unroll
+    for (int a = 0; a < D; ++a) ue[b][a] = u[nb * D + a];
+    pe[b] = phi[nb];
+    te[b] = phit[nb];
+  }
+  const double JxW = wq * vol;
   const double k1 = 1.0 - mat.kappa;
-#pragma unroll 1
-  for (int c = 0; c < NA; ++c) {
-    int ci[3];
-    double h[3];
-    if (!adjacent_cell<D>(idx, c, m, ci, h)) continue;
-    const int ai = (~c) & (NA - 1);
-    double ih[D], vol = 1.0;
 #pragma unroll
-    for (int l = 0; l < D; ++l) {
-      ih[l] = 1.0 / h[l];
-      vol *= h[l];
+  for (int q = 0; q < NA; ++q) {
+    double G[D][D], gp[D], ph = 0.0, pt = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+      gp[a] = 0.0;
+#pragma unroll
+      for (int l = 0; l < D; ++l) G[a][l] = 0.0;
     }
-    double ue[NA][D], pe[NA], te[NA];
 #pragma unroll
     for (int b = 0; b < NA; ++b) {
-      const int64_t nb = cell_node<D>(ci, b, m);
+      const double Nb = shp<D>(b, q);
+      ph += Nb * pe[b];
+      pt += Nb * te[b];
 #pragma unroll
-      for (int a = 0; a < D; ++a) ue[b][a] = u[nb * D + a];
-      pe[b] = phi[nb];
-      te[b] = phit[nb];
+      for (int l = 0; l < D; ++l) {
+        const double dN = dshp<D>(b, q, l);   // reference derivative; 1/h_l applied below
+        gp[l] += dN * pe[b];
+#pragma unroll
+        for (int a = 0; a < D; ++a) G[a][l] += ue[b][a] * dN;
+      }
     }
-    const double JxW = wq * vol;
+#pragma unroll
+    for (int l = 0; l < D; ++l) {
+      gp[l] *= ih[l];
+#pragma unroll
+      for (int a = 0; a < D; ++a) G[a][l] *= ih[l];
+    }
+    double div = 0.0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) div += G[l][l];
+    double sig[D][D], sige = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        const double e = 0.5 * (G[a][l] + G[l][a]);
+        sig[a][l] = 2.0 * mat.mu * e + (a == l ? mat.lam * div : 0.0);
+        sige += sig[a][l] * e;
+      }
+    const double g = k1 * pt * pt + mat.kappa;
+    const double pp = ph * ph * mat.p;
+    double* out = QP + (int64_t)q * R * ncell + cl;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int l = 0; l < D; ++l)
+        out[(a * D + l) * ncell] = JxW * (g * sig[a][l] + (a == l ? pp : 0.0)) * ih[l];
+    out[D * D * ncell] =
+        JxW * (k1 * ph * sige + 2.0 * ph * mat.p * div - mat.Gc / mat.eps * (1.0 - ph));
+#pragma unroll
+    for (int l = 0; l < D; ++l) out[(D * D + 1 + l) * ncell] = JxW * mat.Gc * mat.eps * gp[l] * ih[l];
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(BLK) k_residual_gather(MeshDev m, int64_t n, int64_t ncell,
+                                                         const double* __restrict__ QP,
+                                                         double* __restrict__ F) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  constexpr int NA = 1 << D, R = res_rec<D>();
+  int idx[3];
+  node_index<D>(i, m, idx);
+  double ru[D], rp = 0.0;
+#pragma unroll
+  for (int a = 0; a < D; ++a) ru[a] = 0.0;
+#pragma unroll
+  for (int c = 0; c < NA; ++c) {
+    int ci[3];
+    if (!adjacent_cell_index<D>(idx, c, m, ci)) continue;
+    const int ai = (~c) & (NA - 1);
+    const double* rec = QP + cell_of<D>(ci, m);
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
-      double G[D][D], gp[D], ph = 0.0, pt = 0.0;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        gp[a] = 0.0;
-#pragma unroll
-        for (int l = 0; l < D; ++l) G[a][l] = 0.0;
-      }
-#pragma unroll
-      for (int b = 0; b < NA; ++b) {
-        const double Nb = shp<D>(b, q);
-        ph += Nb * pe[b];
-        pt += Nb * te[b];
-#pragma unroll
-        for (int l = 0; l < D; ++l) {
-          const double dN = dshp<D>(b, q, l) * ih[l];
-          gp[l] += dN * pe[b];
-#pragma unroll
-          for (int a = 0; a < D; ++a) G[a][l] += ue[b][a] * dN;
-        }
-      }
-      double div = 0.0;
-#pragma unroll
-      for (int l = 0; l < D; ++l) div += G[l][l];
-      double sig[D][D], sige = 0.0;
+      const double* r = rec + (int64_t)q * R * ncell;
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-          const double e = 0.5 * (G[a][l] + G[l][a]);
-          sig[a][l] = 2.0 * mat.mu * e + (a == l ? mat.lam * div : 0.0);
-          sige += sig[a][l] * e;
-        }
-      const double g = k1 * pt * pt + mat.kappa;
-      const double Na = shp<D>(ai, q);
-      double dNa[D];
+        for (int l = 0; l < D; ++l) ru[a] += __ldg(r + (a * D + l) * ncell) * dshp<D>(ai, q, l);
+      rp += __ldg(r + D * D * ncell) * shp<D>(ai, q);
 #pragma unroll
-      for (int l = 0; l < D; ++l) dNa[l] = dshp<D>(ai, q, l) * ih[l];
-      const double pp = ph * ph * mat.p;
-#pragma unroll
-      for (int a = 0; a < D; ++a) {
-        double t = 0.0;
-#pragma unroll
-        for (int l = 0; l < D; ++l) t += sig[a][l] * dNa[l];
-        ru[a] += JxW * (g * t + pp * dNa[a]);
-      }
-      double gdot = 0.0;
-#pragma unroll
-      for (int l = 0; l < D; ++l) gdot += gp[l] * dNa[l];
-      rp += JxW * ((k1 * ph * sige + 2.0 * ph * mat.p * div - mat.Gc / mat.eps * (1.0 - ph)) * Na +
-                   mat.Gc * mat.eps * gdot);
+      for (int l = 0; l < D; ++l) rp += __ldg(r + (D * D + 1 + l) * ncell) * dshp<D>(ai, q, l);
     }
   }
 #pragma unroll
@@ -380,104 +450,196 @@ __global__ void __launch_bounds__(BLK) k_assemble_uu(MeshDev m, Material mat, in
 // (M_phi_phi)_ij = ((1-kappa) sigma(u):e(u) + 2p div u + G_c/eps) (chi_j, chi_i)
 //                 + G_c eps (grad chi_j, grad chi_i)
 // Dirichlet displacement columns of M_phi_u are zero (eliminated DoFs).
+//
+// Two passes, as for the residual.  k_assemble_phi_qp stores per cell and Gauss
+// point q
+//   M[e][l] = JxW (2(1-kappa) phi sigma(u)[e][l] + 2 p phi delta_el) / h_l
+//   w0      = JxW ((1-kappa) sigma:e + 2 p div u + G_c/eps)
+// and k_assemble_phi_gather forms the rows of node a from its 2^d cells:
+//   M_phi_u[a][(b,e)] += sum_q N_a sum_l M[e][l] dN_b/dxi_l,
+//   M_phi_phi[a][b]   += sum_q w0 N_a N_b
+//                        + G_c eps JxW sum_q sum_l dN_a/dxi_l dN_b/dxi_l / h_l^2
+// (the last term depends on the cell's edge lengths only and is formed in the
+// gather).  The sums over q for all trial nodes b at once use the tensor-product
+// structure of the Q1 basis (sum factorisation, below).
 template <int D>
-__global__ void __launch_bounds__(BLK) k_assemble_phi(MeshDev m, Material mat, int64_t n,
-                                                      const double* __restrict__ u,
-                                                      const double* __restrict__ phi,
-                                                      double* __restrict__ Kpu,
-                                                      double* __restrict__ Kpp) {
+__host__ __device__ constexpr int phi_rec() { return D * D + 1; }
+
+// out[b] = sum_q A[q] N_b(q) for every local node b: the 2^D x 2^D shape-value
+// matrix is a Kronecker product of D 2 x 2 factors s(b_k, q_k) (s(0,q) = 1 - x_q,
+// s(1,q) = x_q), applied one axis at a time.
+template <int D>
+__device__ __forceinline__ void contract_shp(double (&W)[1 << D]) {
+  constexpr int NA = 1 << D;
+  const double x0 = gauss_pt(0), x1 = gauss_pt(1);
+#pragma unroll
+  for (int k = 0; k < D; ++k)
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      if ((q >> k) & 1) continue;
+      const double v0 = W[q], v1 = W[q | (1 << k)];
+      W[q] = (1.0 - x0) * v0 + (1.0 - x1) * v1;
+      W[q | (1 << k)] = x0 * v0 + x1 * v1;
+    }
+}
+
+// out[b] += sum_q A[q] dN_b/dxi_l(q) for every b.  dN_b/dxi_l = sign(b_l) times
+// the product over the other axes of s(b_k, q_k), which does not depend on q_l:
+// sum A over q_l first, apply the other axes' factors, then the sign.
+template <int D>
+__device__ __forceinline__ void contract_dshp_add(int l, const double (&A)[1 << D],
+                                                  double (&out)[1 << D]) {
+  constexpr int NA = 1 << D;
+  const double x0 = gauss_pt(0), x1 = gauss_pt(1);
+  double W[NA];
+#pragma unroll
+  for (int q = 0; q < NA; ++q) W[q] = ((q >> l) & 1) ? 0.0 : A[q] + A[q | (1 << l)];
+#pragma unroll
+  for (int k = 0; k < D; ++k) {
+    if (k == l) continue;
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      if (((q >> k) & 1) || ((q >> l) & 1)) continue;
+      const double v0 = W[q], v1 = W[q | (1 << k)];
+      W[q] = (1.0 - x0) * v0 + (1.0 - x1) * v1;
+      W[q | (1 << k)] = x0 * v0 + x1 * v1;
+    }
+  }
+#pragma unroll
+  for (int b = 0; b < NA; ++b) {
+    const double v = W[b & ~(1 << l)];
+    out[b] += ((b >> l) & 1) ? v : -v;
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(BLK) k_assemble_phi_qp(MeshDev m, Material mat, int64_t ncell,
+                                                         const double* __restrict__ u,
+                                                         const double* __restrict__ phi,
+                                                         double* __restrict__ QP) {
+  const int64_t cl = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (cl >= ncell) return;
+  constexpr int NA = 1 << D, R = phi_rec<D>();
+  const double wq = D == 2 ? 0.25 : 0.125;
+  int ci[3];
+  cell_index<D>(cl, m, ci);
+  double ih[D], vol = 1.0;
+#pragma unroll
+  for (int l = 0; l < D; ++l) {
+    const double h = m.X[l][ci[l] + 1] - m.X[l][ci[l]];
+    ih[l] = 1.0 / h;
+    vol *= h;
+  }
+  double ue[NA][D], pe[NA];
+#pragma unroll
+  for (int b = 0; b < NA; ++b) {
+    const int64_t nb = cell_node<D>(ci, b, m);
+#pragma unroll
+    for (int a = 0; a < D; ++a) ue[b][a] = u[nb * D + a];
+    pe[b] = phi[nb];
+  }
+  const double JxW = wq * vol;
+  const double k1 = 1.0 - mat.kappa;
+#pragma unroll
+  for (int q = 0; q < NA; ++q) {
+    double G[D][D], ph = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int l = 0; l < D; ++l) G[a][l] = 0.0;
+#pragma unroll
+    for (int b = 0; b < NA; ++b) {
+      ph += shp<D>(b, q) * pe[b];
+#pragma unroll
+      for (int l = 0; l < D; ++l)
+#pragma unroll
+        for (int a = 0; a < D; ++a) G[a][l] += ue[b][a] * dshp<D>(b, q, l);
+    }
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int l = 0; l < D; ++l) G[a][l] *= ih[l];
+    double div = 0.0;
+#pragma unroll
+    for (int l = 0; l < D; ++l) div += G[l][l];
+    double sig[D][D], sige = 0.0;
+#pragma unroll
+    for (int a = 0; a < D; ++a)
+#pragma unroll
+      for (int l = 0; l < D; ++l) {
+        const double e = 0.5 * (G[a][l] + G[l][a]);
+        sig[a][l] = 2.0 * mat.mu * e + (a == l ? mat.lam * div : 0.0);
+        sige += sig[a][l] * e;
+      }
+    const double cs = 2.0 * k1 * ph, cp = 2.0 * mat.p * ph;
+    double* out = QP + (int64_t)q * R * ncell + cl;
+#pragma unroll
+    for (int e = 0; e < D; ++e)
+#pragma unroll
+      for (int l = 0; l < D; ++l)
+        out[(e * D + l) * ncell] = JxW * (cs * sig[e][l] + (e == l ? cp : 0.0)) * ih[l];
+    out[D * D * ncell] = JxW * (k1 * sige + 2.0 * mat.p * div + mat.Gc / mat.eps);
+  }
+}
+
+template <int D>
+__global__ void __launch_bounds__(BLK) k_assemble_phi_gather(MeshDev m, Material mat, int64_t n,
+                                                             int64_t ncell,
+                                                             const double* __restrict__ QP,
+                                                             double* __restrict__ Kpu,
+                                                             double* __restrict__ Kpp) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  constexpr int NA = 1 << D;
+  constexpr int NA = 1 << D, R = phi_rec<D>();
   constexpr int NS = D == 2 ? 9 : 27;
   const double wq = D == 2 ? 0.25 : 0.125;
   int idx[3];
   node_index<D>(i, m, idx);
   for (int s = 0; s < NS * D; ++s) Kpu[(int64_t)s * n + i] = 0.0;
   for (int s = 0; s < NS; ++s) Kpp[(int64_t)s * n + i] = 0.0;
-  const double k1 = 1.0 - mat.kappa;
 #pragma unroll 1
   for (int c = 0; c < NA; ++c) {
     int ci[3];
-    double h[3];
-    if (!adjacent_cell<D>(idx, c, m, ci, h)) continue;
+    if (!adjacent_cell_index<D>(idx, c, m, ci)) continue;
     const int ai = (~c) & (NA - 1);
-    double ih[D], vol = 1.0;
+    double kl[D], vol = 1.0;
 #pragma unroll
     for (int l = 0; l < D; ++l) {
-      ih[l] = 1.0 / h[l];
-      vol *= h[l];
+      const double h = m.X[l][ci[l] + 1] - m.X[l][ci[l]];
+      kl[l] = 1.0 / (h * h);
+      vol *= h;
     }
-    double ue[NA][D], pe[NA];
+    const double gl = mat.Gc * mat.eps * wq * vol;
+    const double* rec = QP + cell_of<D>(ci, m);
+    double Na[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) Na[q] = shp<D>(ai, q);
+    double Kpu_e[D][NA], Kpp_e[NA], A[NA];
 #pragma unroll
     for (int b = 0; b < NA; ++b) {
-      const int64_t nb = cell_node<D>(ci, b, m);
 #pragma unroll
-      for (int a = 0; a < D; ++a) ue[b][a] = u[nb * D + a];
-      pe[b] = phi[nb];
+      for (int e = 0; e < D; ++e) Kpu_e[e][b] = 0.0;
     }
-    double Kpu_e[NA][D], Kpp_e[NA];
 #pragma unroll
-    for (int b = 0; b < NA; ++b) {
-      Kpp_e[b] = 0.0;
+    for (int e = 0; e < D; ++e)
 #pragma unroll
-      for (int a = 0; a < D; ++a) Kpu_e[b][a] = 0.0;
-    }
-    const double JxW = wq * vol;
+      for (int l = 0; l < D; ++l) {
 #pragma unroll
-    for (int q = 0; q < NA; ++q) {
-      double G[D][D], ph = 0.0;
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int l = 0; l < D; ++l) G[a][l] = 0.0;
-#pragma unroll
-      for (int b = 0; b < NA; ++b) {
-        ph += shp<D>(b, q) * pe[b];
-#pragma unroll
-        for (int l = 0; l < D; ++l) {
-          const double dN = dshp<D>(b, q, l) * ih[l];
-#pragma unroll
-          for (int a = 0; a < D; ++a) G[a][l] += ue[b][a] * dN;
-        }
+        for (int q = 0; q < NA; ++q)
+          A[q] = Na[q] * __ldg(rec + ((int64_t)q * R + e * D + l) * ncell);
+        contract_dshp_add<D>(l, A, Kpu_e[e]);
       }
-      double div = 0.0;
+    // mass-like part: sum_q w0 N_a N_b
 #pragma unroll
-      for (int l = 0; l < D; ++l) div += G[l][l];
-      double sig[D][D], sige = 0.0;
+    for (int q = 0; q < NA; ++q) Kpp_e[q] = Na[q] * __ldg(rec + ((int64_t)q * R + D * D) * ncell);
+    contract_shp<D>(Kpp_e);
+    // Laplace part: G_c eps JxW / h_l^2 sum_q dN_a/dxi_l dN_b/dxi_l
 #pragma unroll
-      for (int a = 0; a < D; ++a)
+    for (int l = 0; l < D; ++l) {
+      const double w = gl * kl[l];
 #pragma unroll
-        for (int l = 0; l < D; ++l) {
-          const double e = 0.5 * (G[a][l] + G[l][a]);
-          sig[a][l] = 2.0 * mat.mu * e + (a == l ? mat.lam * div : 0.0);
-          sige += sig[a][l] * e;
-        }
-      const double c0 = k1 * sige + 2.0 * mat.p * div + mat.Gc / mat.eps;
-      const double Na = shp<D>(ai, q);
-      double dNa[D];
-#pragma unroll
-      for (int l = 0; l < D; ++l) dNa[l] = dshp<D>(ai, q, l) * ih[l];
-      const double wa = JxW * Na;
-      const double cs = 2.0 * k1 * ph, cp = 2.0 * mat.p * ph;
-#pragma unroll
-      for (int b = 0; b < NA; ++b) {
-        const double Nb = shp<D>(b, q);
-        double dNb[D], dd = 0.0;
-#pragma unroll
-        for (int l = 0; l < D; ++l) {
-          dNb[l] = dshp<D>(b, q, l) * ih[l];
-          dd += dNa[l] * dNb[l];
-        }
-#pragma unroll
-        for (int e = 0; e < D; ++e) {
-          double t = 0.0;
-#pragma unroll
-          for (int l = 0; l < D; ++l) t += sig[e][l] * dNb[l];
-          Kpu_e[b][e] += wa * (cs * t + cp * dNb[e]);
-        }
-        Kpp_e[b] += JxW * (c0 * Na * Nb + mat.Gc * mat.eps * dd);
-      }
+      for (int q = 0; q < NA; ++q) A[q] = w * dshp<D>(ai, q, l);
+      contract_dshp_add<D>(l, A, Kpp_e);
     }
 #pragma unroll
     for (int b = 0; b < NA; ++b) {
@@ -485,7 +647,7 @@ __global__ void __launch_bounds__(BLK) k_assemble_phi(MeshDev m, Material mat, i
       Kpp[(int64_t)s * n + i] += Kpp_e[b];
       if (node_on_boundary<D>(ci, b, m)) continue;
 #pragma unroll
-      for (int e = 0; e < D; ++e) Kpu[(int64_t)(s * D + e) * n + i] += Kpu_e[b][e];
+      for (int e = 0; e < D; ++e) Kpu[(int64_t)(s * D + e) * n + i] += Kpu_e[e][b];
     }
   }
 }
@@ -857,186 +1019,6 @@ __global__ void k_rigid_modes(MeshDev m, int64_t n, double* __restrict__ B) {
     for (int a = 0; a < D; ++a) B[k * ld + i * D + a] = v[k][a];
 }
 
-// ------------------------------------------- stencil smoother (AMG level 0) --
-// The finest AMG level of each block is the assembled node stencil itself
-// (Kuu with B = d, Kpp with B = 1, slot-major).  acc = K x over the 3^D
-// neighbours of node i, without branches: a neighbour outside the mesh is
-// replaced by node i itself and its product selected away, so every load is
-// in bounds and independent of the others, and all of them can be in flight
-// together (node indices fit in 32 bits).
-template <class T, int D, int B>
-__device__ __forceinline__ void stencil_apply(const MeshDev& m, int64_t n, int i,
-                                              const T* __restrict__ K, const T* __restrict__ x,
-                                              T (&acc)[B]) {
-  constexpr int NS = D == 2 ? 9 : 27;
-  const int n0 = m.nn[0], n1 = m.nn[1];
-  const int ix = i % n0;
-  const int r = i / n0;
-  const int iy = D == 2 ? r : r % n1;
-  const int iz = D == 2 ? 0 : r / n1;
-  const bool lo[3] = {ix > 0, iy > 0, iz > 0};
-  const bool hi[3] = {ix < n0 - 1, iy < n1 - 1, D == 3 && iz < m.nn[2] - 1};
-#pragma unroll
-  for (int a = 0; a < B; ++a) acc[a] = T(0);
-#pragma unroll
-  for (int s = 0; s < NS; ++s) {
-    const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = D == 3 ? s / 9 - 1 : 0;
-    const bool ok = (ox < 0 ? lo[0] : ox > 0 ? hi[0] : true) &&
-                    (oy < 0 ? lo[1] : oy > 0 ? hi[1] : true) &&
-                    (oz < 0 ? lo[2] : oz > 0 ? hi[2] : true);
-    const int j = ok ? i + ox + oy * n0 + oz * n0 * n1 : i;
-    T xj[B];
-#pragma unroll
-    for (int c = 0; c < B; ++c) {
-      const T v = x[(int64_t)j * B + c];
-      xj[c] = ok ? v : T(0);
-    }
-#pragma unroll
-    for (int a = 0; a < B; ++a)
-#pragma unroll
-      for (int c = 0; c < B; ++c) {
-        const T k = K[((int64_t)(s * B + a) * B + c) * n + i];
-        acc[a] += (ok ? k : T(0)) * xj[c];
-      }
-  }
-}
-
-// One Chebyshev step fused with the operator apply:
-// res = dinv .* (rhs - K x_in),  d = cd d + cr res,  x_out = x_in + d.
-// With zero_x the iterate starts at 0 (no apply).
-template <class T, int D, int B>
-__global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
-                                                      const T* __restrict__ K,
-                                                      const T* __restrict__ dinv,
-                                                      const T* __restrict__ rhs,
-                                                      const T* __restrict__ xin,
-                                                      T* __restrict__ xout, T* __restrict__ d,
-                                                      T cd, T cr, int zero_x) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  T acc[B];
-  if (zero_x) {
-#pragma unroll
-    for (int a = 0; a < B; ++a) acc[a] = T(0);
-  } else {
-    stencil_apply<T, D, B>(m, n, i, K, xin, acc);
-  }
-#pragma unroll
-  for (int a = 0; a < B; ++a) {
-    const int64_t r = (int64_t)i * B + a;
-    const T res = dinv[r] * (rhs[r] - acc[a]);
-    const T dn = (zero_x ? T(0) : cd * d[r]) + cr * res;
-    d[r] = dn;
-    xout[r] = (zero_x ? T(0) : xin[r]) + dn;
-  }
-}
-
-// 2d displacement block in FP32 with the node-major layout Kq[(s n + i) * 4 + 2a + c]:
-// each node's 2x2 block of slot s is one 16-byte load, each neighbour's x one
-// 8-byte load.  RESID: r = rhs - K x; otherwise one Chebyshev step as above.
-template <bool RESID>
-__device__ __forceinline__ void stencil_q2(const MeshDev& m, int n, const float* __restrict__ Kq,
-                                           const float* __restrict__ dinv,
-                                           const float* __restrict__ rhs,
-                                           const float* __restrict__ xin, float* __restrict__ out,
-                                           float* __restrict__ d, float cd, float cr, int zero_x) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  float a0 = 0.f, a1 = 0.f;
-  if (RESID || !zero_x) {
-    const int n0 = m.nn[0];
-    const int ix = i % n0, iy = i / n0;
-    const bool lx = ix > 0, hx = ix < n0 - 1, ly = iy > 0, hy = iy < m.nn[1] - 1;
-#pragma unroll
-    for (int s = 0; s < 9; ++s) {
-      const int ox = s % 3 - 1, oy = s / 3 - 1;
-      const bool ok = (ox < 0 ? lx : ox > 0 ? hx : true) && (oy < 0 ? ly : oy > 0 ? hy : true);
-      const int j = ok ? i + ox + oy * n0 : i;
-      const float2 x = reinterpret_cast<const float2*>(xin)[j];
-      const float4 k = reinterpret_cast<const float4*>(Kq)[(int64_t)s * n + i];
-      const float x0 = ok ? x.x : 0.f, x1 = ok ? x.y : 0.f;
-      a0 += k.x * x0 + k.y * x1;
-      a1 += k.z * x0 + k.w * x1;
-    }
-  }
-  const float2 b = reinterpret_cast<const float2*>(rhs)[i];
-  if constexpr (RESID) {
-    reinterpret_cast<float2*>(out)[i] = make_float2(b.x - a0, b.y - a1);
-  } else {
-    const float2 di = reinterpret_cast<const float2*>(dinv)[i];
-    float2 dn = make_float2(cr * di.x * (b.x - a0), cr * di.y * (b.y - a1));
-    float2 xo = dn;
-    if (!zero_x) {
-      const float2 dd = reinterpret_cast<const float2*>(d)[i];
-      const float2 xi = reinterpret_cast<const float2*>(xin)[i];
-      dn.x += cd * dd.x;
-      dn.y += cd * dd.y;
-      xo = make_float2(xi.x + dn.x, xi.y + dn.y);
-    }
-    reinterpret_cast<float2*>(d)[i] = dn;
-    reinterpret_cast<float2*>(out)[i] = xo;
-  }
-}
-
-__global__ void __launch_bounds__(256) k_stencil_cheb_q2(MeshDev m, int n, const float* __restrict__ Kq,
-                                                         const float* __restrict__ dinv,
-                                                         const float* __restrict__ rhs,
-                                                         const float* __restrict__ xin,
-                                                         float* __restrict__ xout,
-                                                         float* __restrict__ d, float cd, float cr,
-                                                         int zero_x) {
-  stencil_q2<false>(m, n, Kq, dinv, rhs, xin, xout, d, cd, cr, zero_x);
-}
-
-__global__ void __launch_bounds__(256) k_stencil_resid_q2(MeshDev m, int n,
-                                                          const float* __restrict__ Kq,
-                                                          const float* __restrict__ rhs,
-                                                          const float* __restrict__ x,
-                                                          float* __restrict__ r) {
-  stencil_q2<true>(m, n, Kq, nullptr, rhs, x, r, nullptr, 0.f, 0.f, 0);
-}
-
-// node-major FP32 copy of the 2d displacement stencil (9 slots x 2 x 2)
-__global__ void k_stencil_to_q2(int64_t n, const double* __restrict__ K, float* __restrict__ Kq) {
-  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 9 * n) return;
-  const int64_t s = t / n, i = t - s * n;
-  float4 q;
-  q.x = (float)K[(s * 4 + 0) * n + i];
-  q.y = (float)K[(s * 4 + 1) * n + i];
-  q.z = (float)K[(s * 4 + 2) * n + i];
-  q.w = (float)K[(s * 4 + 3) * n + i];
-  reinterpret_cast<float4*>(Kq)[t] = q;
-}
-
-// r = rhs - K x
-template <class T, int D, int B>
-__global__ void __launch_bounds__(256) k_stencil_resid(MeshDev m, int64_t n,
-                                                       const T* __restrict__ K,
-                                                       const T* __restrict__ rhs,
-                                                       const T* __restrict__ x,
-                                                       T* __restrict__ r) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  T acc[B];
-  stencil_apply<T, D, B>(m, n, i, K, x, acc);
-#pragma unroll
-  for (int a = 0; a < B; ++a) r[(int64_t)i * B + a] = rhs[(int64_t)i * B + a] - acc[a];
-}
-
-// inverse diagonal of a node stencil (block size B, centre slot c0)
-__global__ void k_stencil_dinv(int64_t n, int B, int c0, const double* __restrict__ K,
-                               double* __restrict__ dinv, float* __restrict__ dinvf) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= n) return;
-  for (int a = 0; a < B; ++a) {
-    const double v = K[((int64_t)(c0 * B + a) * B + a) * n + i];
-    const double r = v != 0.0 ? 1.0 / v : 0.0;
-    dinv[i * B + a] = r;
-    if (dinvf) dinvf[i * B + a] = (float)r;
-  }
-}
-
 __global__ void k_d2f(int64_t n, const double* __restrict__ a, float* __restrict__ b) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) b[i] = (float)a[i];
@@ -1213,11 +1195,21 @@ void launch_lumped_mass(const MeshDev& m, int64_t n, double* mass, cudaStream_t 
   PFF_LAUNCH("lumped_mass");
 }
 
-void launch_residual(const MeshDev& m, const Material& mat, int64_t n, const double* u,
-                     const double* phi, const double* phit, double* F, cudaStream_t s) {
-  // reads u, phi, phi~; writes F
-  ProfScope ps("residual", B8 * n * (2.0 * m.dim + 3.0), s);
-  DISPATCH(m.dim, (k_residual<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, u, phi, phit, F)));
+int64_t qp_doubles(int dim, int64_t n_cells) {
+  const int na = 1 << dim;
+  const int rec = dim == 2 ? res_rec<2>() : res_rec<3>();   // the larger of the two records
+  static_assert(res_rec<2>() >= phi_rec<2>() && res_rec<3>() >= phi_rec<3>(), "record sizes");
+  return (int64_t)na * rec * n_cells;
+}
+
+void launch_residual(const MeshDev& m, const Material& mat, int64_t n, int64_t n_cells,
+                     const double* u, const double* phi, const double* phit, double* qp,
+                     double* F, cudaStream_t s) {
+  // reads u, phi, phi~; writes F (the quadrature records stay in L2 / are not counted)
+  ProfScope ps("residual", B8 * n * (2.0 * m.dim + 3.0), s, 2);
+  DISPATCH(m.dim, (k_residual_qp<D><<<grid_for(n_cells, BLK), BLK, 0, s>>>(m, mat, n_cells, u, phi,
+                                                                           phit, qp)));
+  DISPATCH(m.dim, (k_residual_gather<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, n, n_cells, qp, F)));
   PFF_LAUNCH("residual");
 }
 
@@ -1228,11 +1220,14 @@ void launch_assemble_uu(const MeshDev& m, const Material& mat, int64_t n, const 
   PFF_LAUNCH("assemble_uu");
 }
 
-void launch_assemble_phi(const MeshDev& m, const Material& mat, int64_t n, const double* u,
-                         const double* phi, double* Kpu, double* Kpp, cudaStream_t s) {
-  ProfScope ps("assemble_phi", B8 * n * ((m.dim + 1.0) + NSd(m.dim) * (m.dim + 1.0)), s);
-  DISPATCH(m.dim,
-           (k_assemble_phi<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, u, phi, Kpu, Kpp)));
+void launch_assemble_phi(const MeshDev& m, const Material& mat, int64_t n, int64_t n_cells,
+                         const double* u, const double* phi, double* qp, double* Kpu, double* Kpp,
+                         cudaStream_t s) {
+  ProfScope ps("assemble_phi", B8 * n * ((m.dim + 1.0) + NSd(m.dim) * (m.dim + 1.0)), s, 2);
+  DISPATCH(m.dim, (k_assemble_phi_qp<D><<<grid_for(n_cells, BLK), BLK, 0, s>>>(m, mat, n_cells, u,
+                                                                               phi, qp)));
+  DISPATCH(m.dim, (k_assemble_phi_gather<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, n_cells, qp,
+                                                                             Kpu, Kpp)));
   PFF_LAUNCH("assemble_phi");
 }
 
@@ -1330,76 +1325,6 @@ void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s) 
   count_launch();
   DISPATCH(m.dim, (k_rigid_modes<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, B)));
   PFF_LAUNCH("rigid_modes");
-}
-
-#define STENCIL_DISPATCH(dim, b, KERNEL, ...)                                   \
-  do {                                                                           \
-    const unsigned g_ = grid_for(n, 256);                                        \
-    if ((dim) == 2 && (b) == 2) KERNEL<T, 2, 2><<<g_, 256, 0, s>>>(__VA_ARGS__); \
-    else if ((dim) == 2 && (b) == 1) KERNEL<T, 2, 1><<<g_, 256, 0, s>>>(__VA_ARGS__); \
-    else if ((dim) == 3 && (b) == 3) KERNEL<T, 3, 3><<<g_, 256, 0, s>>>(__VA_ARGS__); \
-    else if ((dim) == 3 && (b) == 1) KERNEL<T, 3, 1><<<g_, 256, 0, s>>>(__VA_ARGS__); \
-    else fail(PFF_ERR_INVALID_ARG, "stencil block size must be dim or 1");     \
-  } while (0)
-
-template <class T>
-void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T* dinv,
-                         const T* rhs, const T* xin, T* xout, T* d, double cd, double cr,
-                         int zero_x, cudaStream_t s, bool node_major) {
-  // stencil values (unless starting from zero), then dinv, rhs, x_in, x_out, d read + write
-  const double bytes = sizeof(T) * (double)n *
-                       ((zero_x ? 0.0 : NSd(m.dim) * b * b) + b * (zero_x ? 4.0 : 6.0));
-  ProfScope ps(sizeof(T) == 8 ? "cheb0_f64" : "cheb0_f32", bytes, s);
-  if constexpr (sizeof(T) == 4) {
-    if (node_major && m.dim == 2 && b == 2) {
-      k_stencil_cheb_q2<<<grid_for(n, 256), 256, 0, s>>>(m, (int)n, K, dinv, rhs, xin, xout, d,
-                                                         (float)cd, (float)cr, zero_x);
-      PFF_LAUNCH("stencil_cheb");
-      return;
-    }
-  }
-  STENCIL_DISPATCH(m.dim, b, k_stencil_cheb, m, n, K, dinv, rhs, xin, xout, d, (T)cd, (T)cr, zero_x);
-  PFF_LAUNCH("stencil_cheb");
-}
-
-template <class T>
-void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const T* rhs, const T* x,
-                          T* r, cudaStream_t s, bool node_major) {
-  const double bytes = sizeof(T) * (double)n * (NSd(m.dim) * b * b + 3.0 * b);
-  ProfScope ps(sizeof(T) == 8 ? "resid0_f64" : "resid0_f32", bytes, s);
-  if constexpr (sizeof(T) == 4) {
-    if (node_major && m.dim == 2 && b == 2) {
-      k_stencil_resid_q2<<<grid_for(n, 256), 256, 0, s>>>(m, (int)n, K, rhs, x, r);
-      PFF_LAUNCH("stencil_resid");
-      return;
-    }
-  }
-  STENCIL_DISPATCH(m.dim, b, k_stencil_resid, m, n, K, rhs, x, r);
-  PFF_LAUNCH("stencil_resid");
-}
-
-template void launch_stencil_cheb<float>(const MeshDev&, int64_t, int, const float*, const float*,
-                                         const float*, const float*, float*, float*, double, double,
-                                         int, cudaStream_t, bool);
-template void launch_stencil_cheb<double>(const MeshDev&, int64_t, int, const double*,
-                                          const double*, const double*, const double*, double*,
-                                          double*, double, double, int, cudaStream_t, bool);
-template void launch_stencil_resid<float>(const MeshDev&, int64_t, int, const float*, const float*,
-                                          const float*, float*, cudaStream_t, bool);
-template void launch_stencil_resid<double>(const MeshDev&, int64_t, int, const double*,
-                                           const double*, const double*, double*, cudaStream_t, bool);
-
-void stencil_to_node_major(const double* K, float* Kq, int64_t n, cudaStream_t s) {
-  ProfScope ps("to_f32", 48.0 * 9 * n, s);
-  k_stencil_to_q2<<<grid_for(9 * n, 256), 256, 0, s>>>(n, K, Kq);
-  PFF_LAUNCH("stencil_to_q2");
-}
-
-void launch_stencil_dinv(const MeshDev& m, int64_t n, int b, const double* K, double* dinv,
-                         float* dinvf, cudaStream_t s) {
-  ProfScope ps("stencil_dinv", (double)n * b * (8.0 + 8.0 + (dinvf ? 4.0 : 0.0)), s);
-  k_stencil_dinv<<<grid_for(n, 256), 256, 0, s>>>(n, b, m.dim == 2 ? 4 : 13, K, dinv, dinvf);
-  PFF_LAUNCH("stencil_dinv");
 }
 
 void convert_d2f(const double* a, float* b, int64_t n, cudaStream_t s) {

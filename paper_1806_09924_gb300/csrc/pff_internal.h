@@ -244,12 +244,17 @@ inline int n_slots(int dim) { return dim == 2 ? 9 : 27; }
 void launch_phi_tilde(const MeshDev& m, int64_t n, int steps_done, const double* phi_old,
                       const double* phi_prev, double* phit, cudaStream_t s);
 void launch_lumped_mass(const MeshDev& m, int64_t n, double* mass, cudaStream_t s);
-void launch_residual(const MeshDev& m, const Material& mat, int64_t n, const double* u,
-                     const double* phi, const double* phit, double* F, cudaStream_t s);
+// Per-cell quadrature records shared by the residual and the phase-field
+// assembly (doubles for a mesh of n_cells cells).
+int64_t qp_doubles(int dim, int64_t n_cells);
+void launch_residual(const MeshDev& m, const Material& mat, int64_t n, int64_t n_cells,
+                     const double* u, const double* phi, const double* phit, double* qp,
+                     double* F, cudaStream_t s);
 void launch_assemble_uu(const MeshDev& m, const Material& mat, int64_t n, const double* phit,
                         double* Kuu, cudaStream_t s);
-void launch_assemble_phi(const MeshDev& m, const Material& mat, int64_t n, const double* u,
-                         const double* phi, double* Kpu, double* Kpp, cudaStream_t s);
+void launch_assemble_phi(const MeshDev& m, const Material& mat, int64_t n, int64_t n_cells,
+                         const double* u, const double* phi, double* qp, double* Kpu, double* Kpp,
+                         cudaStream_t s);
 // scaling S (u: diag M_uu, Dirichlet 1; phi: diag G_c(M/eps + eps K)) and its inverse
 void launch_scaling(const MeshDev& m, const Material& mat, int64_t n, const double* Kuu,
                     double* S, double* Sinv, cudaStream_t s);
@@ -288,9 +293,11 @@ void build_stencil_bsr_structure(const MeshDev& m, int64_t n, int b, Bsr& A, cud
 void launch_rigid_modes(const MeshDev& m, int64_t n, double* B, cudaStream_t s);
 // node coordinates [n][dim]
 void launch_node_coords(const MeshDev& m, int64_t n, double* xyz, cudaStream_t s);
-// AMG finest level on the node stencil (T = float or double; b = dim or 1)
-// node_major: K is the FP32 node-major copy of a 2d displacement stencil
-// (stencil_to_node_major); otherwise slot-major with slot stride n
+// AMG finest level on the node stencil (T = float or double; b = dim or 1).
+// FP64: the full slot-major stencil.  FP32: the symmetric half (centre slot
+// and the slots after it, stencil_to_f32 / stencil_to_node_major); node_major:
+// K is the node-major copy of a 2d displacement stencil, otherwise slot-major
+// with slot stride n
 template <class T>
 void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T* dinv,
                          const T* rhs, const T* xin, T* xout, T* d, double cd, double cr,
@@ -298,8 +305,13 @@ void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T
 template <class T>
 void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const T* rhs, const T* x,
                           T* r, cudaStream_t s, bool node_major = false);
-// FP32 node-major copy Kq[(s n + i) * 4 + 2a + c] of a 2d displacement stencil
+// FP32 node-major copy Kq[(h n + i) * 4 + 2a + c], slot s = h + 4, of the
+// symmetric half of a 2d displacement stencil (5 n float4)
 void stencil_to_node_major(const double* K, float* Kq, int64_t n, cudaStream_t s);
+// FP32 slot-major copy of the symmetric half of a stencil of block size b
+// (stencil_f32_count floats)
+int64_t stencil_f32_count(int dim, int b, int64_t n);
+void stencil_to_f32(int dim, int b, const double* K, float* Kf, int64_t n, cudaStream_t s);
 void convert_d2f(const double* a, float* b, int64_t n, cudaStream_t s);
 // dinv (and its FP32 copy, may be null) = inverse diagonal of a node stencil
 void launch_stencil_dinv(const MeshDev& m, int64_t n, int b, const double* K, double* dinv,
@@ -378,7 +390,8 @@ struct pff_problem {
   int krylov_m = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *tmp = nullptr;
   float* gs_part = nullptr;   // partial sums of the mixed-precision Gram-Schmidt
-  double* pc_tmp = nullptr;   // work vector of the block lower-triangular preconditioner
+  double* pc_tmp = nullptr;
+  double* qp = nullptr;       // per-cell quadrature records (residual, phase-field assembly)   // work vector of the block lower-triangular preconditioner
   // one FGMRES iteration's device work (preconditioner + Jacobian apply) as a
   // CUDA graph on fixed buffers, for problems small enough to be launch-bound
   cudaGraphExec_t iter_graph = nullptr;

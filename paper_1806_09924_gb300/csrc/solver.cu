@@ -153,7 +153,7 @@ void ensure_krylov(pff_problem* P, int m) {
 }
 
 void compute_residual(pff_problem* P, const double* u, const double* phi, double* F) {
-  launch_residual(P->mesh(), P->mat, P->n_nodes, u, phi, P->phit, F, P->stream);
+  launch_residual(P->mesh(), P->mat, P->n_nodes, P->n_cells, u, phi, P->phit, P->qp, F, P->stream);
 }
 
 void compute_active_set(pff_problem* P, double c_rel, double tol_active, double tol_change,
@@ -171,7 +171,8 @@ void assemble_all(pff_problem* P) {
     launch_scaling(m, P->mat, P->n_nodes, P->Kuu, P->S, P->Sinv, P->stream);
     P->uu_assembled = true;
   }
-  launch_assemble_phi(m, P->mat, P->n_nodes, P->u, P->phi, P->Kpu, P->Kpp, P->stream);
+  launch_assemble_phi(m, P->mat, P->n_nodes, P->n_cells, P->u, P->phi, P->qp, P->Kpu, P->Kpp,
+                      P->stream);
   launch_reduce_phi(m, P->n_nodes, P->active, P->phi, P->phi_old, P->F, P->Ft, P->dUA, P->Kpu,
                     P->Kpp, P->stream);
   P->phi_assembled = true;
@@ -290,19 +291,18 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   ap.spmv_group = o.spmv_group;
   const auto m = P->mesh();
   const int64_t n = P->n_nodes;
-  const int ns = n_slots(P->dim);
   // the finest level of each hierarchy smooths on the assembled stencil itself
-  auto use_stencil = [&](Amg& amg, const double* K, float*& Kf, int64_t count) {
+  auto use_stencil = [&](Amg& amg, const double* K, float*& Kf, int b) {
     if (amg.lev.empty()) return;
     AmgLevel& L0 = amg.lev[0];
     L0.stencil = true;
     L0.mesh = m;
     L0.st = K;
     if (ap.mixed) {
-      if (!Kf) Kf = dalloc<float>(count);
-      L0.stf_node_major = P->dim == 2 && count == (int64_t)ns * 4 * n;
+      if (!Kf) Kf = dalloc<float>(stencil_f32_count(P->dim, b, n));
+      L0.stf_node_major = P->dim == 2 && b == 2;
       if (L0.stf_node_major) stencil_to_node_major(K, Kf, n, P->stream);
-      else convert_d2f(K, Kf, count, P->stream);
+      else stencil_to_f32(P->dim, b, K, Kf, n, P->stream);
       L0.stf = Kf;
     }
   };
@@ -325,7 +325,7 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     if (reuse_u) {
       AmgLevel& L0 = P->amg_u.lev[0];
       launch_stencil_dinv(m, n, P->dim, P->Kuu, L0.dinv, ap.mixed ? L0.dinvf : nullptr, P->stream);
-      use_stencil(P->amg_u, P->Kuu, P->Kuu_f, (int64_t)ns * P->dim * P->dim * n);
+      use_stencil(P->amg_u, P->Kuu, P->Kuu_f, P->dim);
       P->amg_u_age += 1;
     }
     P->amg_u_check = false;
@@ -334,7 +334,7 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     ProfScope ps("amg_setup_u", 0.0, P->stream, 0);   // wall time of the build (syncs inside)
     launch_stencil_to_bsr(m, n, P->dim, P->Kuu, P->Auu, P->stream);
     amg_build(P->amg_u, P->Auu, P->Bu, P->dim == 2 ? 3 : 6, ap, P->stream);
-    use_stencil(P->amg_u, P->Kuu, P->Kuu_f, (int64_t)ns * P->dim * P->dim * n);
+    use_stencil(P->amg_u, P->Kuu, P->Kuu_f, P->dim);
     if (!P->phit_built) P->phit_built = dalloc<double>(n);
     PFF_CUDA(cudaMemcpyAsync(P->phit_built, P->phit, sizeof(double) * n, cudaMemcpyDeviceToDevice,
                              P->stream));
@@ -367,7 +367,7 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     launch_stencil_dinv(m, n, 1, P->Kpp, L0.dinv, ap.mixed ? L0.dinvf : nullptr, P->stream);
     P->phi_amg_age += 1;
   }
-  use_stencil(P->amg_p, P->Kpp, P->Kpp_f, (int64_t)ns * n);
+  use_stencil(P->amg_p, P->Kpp, P->Kpp_f, 1);
 }
 
 // z = diag(V_u, V_phi) (S .* r) -- the right preconditioner of the scaled system

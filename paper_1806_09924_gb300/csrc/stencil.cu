@@ -1,0 +1,302 @@
+// Level-0 smoother of both AMG hierarchies: Chebyshev steps and residuals on
+// the assembled node stencils (Kuu with block size d, Kpp with block size 1,
+// slot-major as produced by the element kernels), in FP32 or FP64, plus the
+// node-major FP32 copy of the 2d displacement stencil and the inverse
+// diagonals.  These are the bandwidth-bound kernels of every V-cycle (Section
+// 3.2: block-diagonal AMG preconditioner), kept in a file of their own.
+#include "pff_internal.h"
+
+namespace pff {
+
+namespace {
+
+// ------------------------------------------- stencil smoother (AMG level 0) --
+// The finest AMG level of each block is the assembled node stencil itself
+// (Kuu with B = d, Kpp with B = 1, slot-major).  acc = K x over the 3^D
+// neighbours of node i, without branches: a neighbour outside the mesh is
+// replaced by node i itself and its product selected away, so every load is
+// in bounds and independent of the others, and all of them can be in flight
+// together (node indices fit in 32 bits).
+//
+// The stencils are symmetric (M_uu and the reduced M_phi_phi: Dirichlet and
+// active rows and columns are eliminated alike), so the FP32 copies keep only
+// the centre slot and the slots after it (h = s - C, C = (3^D - 1) / 2).  The
+// block of a slot s < C is the transpose of the block node j = i + offset(s)
+// stores for the opposite slot 3^D - 1 - s, read from j's column: consecutive
+// threads still read consecutive addresses, and the copy moves 5/9 (2d) or
+// 14/27 (3d) of the full stencil's bytes.  FP64 stencils are full.
+template <class T, int D, int B>
+__device__ __forceinline__ void stencil_apply(const MeshDev& m, int64_t n, int i,
+                                              const T* __restrict__ K, const T* __restrict__ x,
+                                              T (&acc)[B]) {
+  constexpr int NS = D == 2 ? 9 : 27;
+  constexpr int C = NS / 2;
+  constexpr bool HALF = sizeof(T) == 4;
+  const int n0 = m.nn[0], n1 = m.nn[1];
+  const int ix = i % n0;
+  const int r = i / n0;
+  const int iy = D == 2 ? r : r % n1;
+  const int iz = D == 2 ? 0 : r / n1;
+  const bool lo[3] = {ix > 0, iy > 0, iz > 0};
+  const bool hi[3] = {ix < n0 - 1, iy < n1 - 1, D == 3 && iz < m.nn[2] - 1};
+#pragma unroll
+  for (int a = 0; a < B; ++a) acc[a] = T(0);
+#pragma unroll
+  for (int s = 0; s < NS; ++s) {
+    const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = D == 3 ? s / 9 - 1 : 0;
+    const bool ok = (ox < 0 ? lo[0] : ox > 0 ? hi[0] : true) &&
+                    (oy < 0 ? lo[1] : oy > 0 ? hi[1] : true) &&
+                    (oz < 0 ? lo[2] : oz > 0 ? hi[2] : true);
+    const int j = ok ? i + ox + oy * n0 + oz * n0 * n1 : i;
+    T xj[B];
+#pragma unroll
+    for (int c = 0; c < B; ++c) {
+      const T v = x[(int64_t)j * B + c];
+      xj[c] = ok ? v : T(0);
+    }
+#pragma unroll
+    for (int a = 0; a < B; ++a)
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        T k;
+        if (!HALF) k = K[((int64_t)(s * B + a) * B + c) * n + i];
+        else if (s >= C) k = K[((int64_t)((s - C) * B + a) * B + c) * n + i];
+        else k = K[((int64_t)((NS - 1 - s - C) * B + c) * B + a) * n + j];
+        acc[a] += (ok ? k : T(0)) * xj[c];
+      }
+  }
+}
+
+// One Chebyshev step fused with the operator apply:
+// res = dinv .* (rhs - K x_in),  d = cd d + cr res,  x_out = x_in + d.
+// With zero_x the iterate starts at 0 (no apply).
+template <class T, int D, int B>
+__global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
+                                                      const T* __restrict__ K,
+                                                      const T* __restrict__ dinv,
+                                                      const T* __restrict__ rhs,
+                                                      const T* __restrict__ xin,
+                                                      T* __restrict__ xout, T* __restrict__ d,
+                                                      T cd, T cr, int zero_x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T acc[B];
+  if (zero_x) {
+#pragma unroll
+    for (int a = 0; a < B; ++a) acc[a] = T(0);
+  } else {
+    stencil_apply<T, D, B>(m, n, i, K, xin, acc);
+  }
+#pragma unroll
+  for (int a = 0; a < B; ++a) {
+    const int64_t r = (int64_t)i * B + a;
+    const T res = dinv[r] * (rhs[r] - acc[a]);
+    const T dn = (zero_x ? T(0) : cd * d[r]) + cr * res;
+    d[r] = dn;
+    xout[r] = (zero_x ? T(0) : xin[r]) + dn;
+  }
+}
+
+// 2d displacement block in FP32 with the node-major layout Kq[(h n + i) * 4 + 2a + c]
+// (slots s = h + 4 >= 4 only, as above): each node's 2x2 block of a slot is one
+// 16-byte load, each neighbour's x one 8-byte load.  RESID: r = rhs - K x;
+// otherwise one Chebyshev step as above.
+template <bool RESID>
+__device__ __forceinline__ void stencil_q2(const MeshDev& m, int n, const float* __restrict__ Kq,
+                                           const float* __restrict__ dinv,
+                                           const float* __restrict__ rhs,
+                                           const float* __restrict__ xin, float* __restrict__ out,
+                                           float* __restrict__ d, float cd, float cr, int zero_x) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float a0 = 0.f, a1 = 0.f;
+  if (RESID || !zero_x) {
+    const int n0 = m.nn[0];
+    const int ix = i % n0, iy = i / n0;
+    const bool lx = ix > 0, hx = ix < n0 - 1, ly = iy > 0, hy = iy < m.nn[1] - 1;
+#pragma unroll
+    for (int s = 0; s < 9; ++s) {
+      const int ox = s % 3 - 1, oy = s / 3 - 1;
+      const bool ok = (ox < 0 ? lx : ox > 0 ? hx : true) && (oy < 0 ? ly : oy > 0 ? hy : true);
+      const int j = ok ? i + ox + oy * n0 : i;
+      const float2 x = reinterpret_cast<const float2*>(xin)[j];
+      float4 k;
+      if (s >= 4) {
+        k = reinterpret_cast<const float4*>(Kq)[(int64_t)(s - 4) * n + i];
+      } else {
+        const float4 kt = reinterpret_cast<const float4*>(Kq)[(int64_t)(4 - s) * n + j];
+        k = make_float4(kt.x, kt.z, kt.y, kt.w);   // transpose of node j's block
+      }
+      const float x0 = ok ? x.x : 0.f, x1 = ok ? x.y : 0.f;
+      a0 += k.x * x0 + k.y * x1;
+      a1 += k.z * x0 + k.w * x1;
+    }
+  }
+  const float2 b = reinterpret_cast<const float2*>(rhs)[i];
+  if constexpr (RESID) {
+    reinterpret_cast<float2*>(out)[i] = make_float2(b.x - a0, b.y - a1);
+  } else {
+    const float2 di = reinterpret_cast<const float2*>(dinv)[i];
+    float2 dn = make_float2(cr * di.x * (b.x - a0), cr * di.y * (b.y - a1));
+    float2 xo = dn;
+    if (!zero_x) {
+      const float2 dd = reinterpret_cast<const float2*>(d)[i];
+      const float2 xi = reinterpret_cast<const float2*>(xin)[i];
+      dn.x += cd * dd.x;
+      dn.y += cd * dd.y;
+      xo = make_float2(xi.x + dn.x, xi.y + dn.y);
+    }
+    reinterpret_cast<float2*>(d)[i] = dn;
+    reinterpret_cast<float2*>(out)[i] = xo;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_stencil_cheb_q2(MeshDev m, int n, const float* __restrict__ Kq,
+                                                         const float* __restrict__ dinv,
+                                                         const float* __restrict__ rhs,
+                                                         const float* __restrict__ xin,
+                                                         float* __restrict__ xout,
+                                                         float* __restrict__ d, float cd, float cr,
+                                                         int zero_x) {
+  stencil_q2<false>(m, n, Kq, dinv, rhs, xin, xout, d, cd, cr, zero_x);
+}
+
+__global__ void __launch_bounds__(256) k_stencil_resid_q2(MeshDev m, int n,
+                                                          const float* __restrict__ Kq,
+                                                          const float* __restrict__ rhs,
+                                                          const float* __restrict__ x,
+                                                          float* __restrict__ r) {
+  stencil_q2<true>(m, n, Kq, nullptr, rhs, x, r, nullptr, 0.f, 0.f, 0);
+}
+
+// node-major FP32 copy of the 2d displacement stencil, slots 4..8 (2 x 2 blocks)
+__global__ void k_stencil_to_q2(int64_t n, const double* __restrict__ K, float* __restrict__ Kq) {
+  const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 5 * n) return;
+  const int64_t h = t / n, i = t - h * n, s = h + 4;
+  float4 q;
+  q.x = (float)K[(s * 4 + 0) * n + i];
+  q.y = (float)K[(s * 4 + 1) * n + i];
+  q.z = (float)K[(s * 4 + 2) * n + i];
+  q.w = (float)K[(s * 4 + 3) * n + i];
+  reinterpret_cast<float4*>(Kq)[t] = q;
+}
+
+// r = rhs - K x
+template <class T, int D, int B>
+__global__ void __launch_bounds__(256) k_stencil_resid(MeshDev m, int64_t n,
+                                                       const T* __restrict__ K,
+                                                       const T* __restrict__ rhs,
+                                                       const T* __restrict__ x,
+                                                       T* __restrict__ r) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  T acc[B];
+  stencil_apply<T, D, B>(m, n, i, K, x, acc);
+#pragma unroll
+  for (int a = 0; a < B; ++a) r[(int64_t)i * B + a] = rhs[(int64_t)i * B + a] - acc[a];
+}
+
+// inverse diagonal of a node stencil (block size B, centre slot c0)
+__global__ void k_stencil_dinv(int64_t n, int B, int c0, const double* __restrict__ K,
+                               double* __restrict__ dinv, float* __restrict__ dinvf) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  for (int a = 0; a < B; ++a) {
+    const double v = K[((int64_t)(c0 * B + a) * B + a) * n + i];
+    const double r = v != 0.0 ? 1.0 / v : 0.0;
+    dinv[i * B + a] = r;
+    if (dinvf) dinvf[i * B + a] = (float)r;
+  }
+}
+
+}  // namespace
+
+namespace {
+inline double NSd(int d) { return d == 2 ? 9.0 : 27.0; }
+// slots a stencil copy of element size es holds (FP32 copies: centre and after)
+inline double slots_stored(int d, size_t es) { return es == 4 ? (NSd(d) + 1.0) / 2.0 : NSd(d); }
+}  // namespace
+
+#define STENCIL_DISPATCH(dim, b, KERNEL, ...)                                   \
+  do {                                                                           \
+    const unsigned g_ = grid_for(n, 256);                                        \
+    if ((dim) == 2 && (b) == 2) KERNEL<T, 2, 2><<<g_, 256, 0, s>>>(__VA_ARGS__); \
+    else if ((dim) == 2 && (b) == 1) KERNEL<T, 2, 1><<<g_, 256, 0, s>>>(__VA_ARGS__); \
+    else if ((dim) == 3 && (b) == 3) KERNEL<T, 3, 3><<<g_, 256, 0, s>>>(__VA_ARGS__); \
+    else if ((dim) == 3 && (b) == 1) KERNEL<T, 3, 1><<<g_, 256, 0, s>>>(__VA_ARGS__); \
+    else fail(PFF_ERR_INVALID_ARG, "stencil block size must be dim or 1");     \
+  } while (0)
+
+template <class T>
+void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T* dinv,
+                         const T* rhs, const T* xin, T* xout, T* d, double cd, double cr,
+                         int zero_x, cudaStream_t s, bool node_major) {
+  // stencil values (unless starting from zero), then dinv, rhs, x_in, x_out, d read + write
+  const double bytes = sizeof(T) * (double)n *
+                       ((zero_x ? 0.0 : slots_stored(m.dim, sizeof(T)) * b * b) + b * (zero_x ? 4.0 : 6.0));
+  ProfScope ps(sizeof(T) == 8 ? "cheb0_f64" : "cheb0_f32", bytes, s);
+  if constexpr (sizeof(T) == 4) {
+    if (node_major && m.dim == 2 && b == 2) {
+      k_stencil_cheb_q2<<<grid_for(n, 256), 256, 0, s>>>(m, (int)n, K, dinv, rhs, xin, xout, d,
+                                                         (float)cd, (float)cr, zero_x);
+      PFF_LAUNCH("stencil_cheb");
+      return;
+    }
+  }
+  STENCIL_DISPATCH(m.dim, b, k_stencil_cheb, m, n, K, dinv, rhs, xin, xout, d, (T)cd, (T)cr, zero_x);
+  PFF_LAUNCH("stencil_cheb");
+}
+
+template <class T>
+void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const T* rhs, const T* x,
+                          T* r, cudaStream_t s, bool node_major) {
+  const double bytes = sizeof(T) * (double)n * (slots_stored(m.dim, sizeof(T)) * b * b + 3.0 * b);
+  ProfScope ps(sizeof(T) == 8 ? "resid0_f64" : "resid0_f32", bytes, s);
+  if constexpr (sizeof(T) == 4) {
+    if (node_major && m.dim == 2 && b == 2) {
+      k_stencil_resid_q2<<<grid_for(n, 256), 256, 0, s>>>(m, (int)n, K, rhs, x, r);
+      PFF_LAUNCH("stencil_resid");
+      return;
+    }
+  }
+  STENCIL_DISPATCH(m.dim, b, k_stencil_resid, m, n, K, rhs, x, r);
+  PFF_LAUNCH("stencil_resid");
+}
+
+template void launch_stencil_cheb<float>(const MeshDev&, int64_t, int, const float*, const float*,
+                                         const float*, const float*, float*, float*, double, double,
+                                         int, cudaStream_t, bool);
+template void launch_stencil_cheb<double>(const MeshDev&, int64_t, int, const double*,
+                                          const double*, const double*, const double*, double*,
+                                          double*, double, double, int, cudaStream_t, bool);
+template void launch_stencil_resid<float>(const MeshDev&, int64_t, int, const float*, const float*,
+                                          const float*, float*, cudaStream_t, bool);
+template void launch_stencil_resid<double>(const MeshDev&, int64_t, int, const double*,
+                                           const double*, const double*, double*, cudaStream_t, bool);
+
+void stencil_to_node_major(const double* K, float* Kq, int64_t n, cudaStream_t s) {
+  ProfScope ps("to_f32", 48.0 * 5 * n, s);
+  k_stencil_to_q2<<<grid_for(5 * n, 256), 256, 0, s>>>(n, K, Kq);
+  PFF_LAUNCH("stencil_to_q2");
+}
+
+int64_t stencil_f32_count(int dim, int b, int64_t n) {
+  const int64_t nh = dim == 2 ? 5 : 14;
+  return nh * b * b * n;
+}
+
+void stencil_to_f32(int dim, int b, const double* K, float* Kf, int64_t n, cudaStream_t s) {
+  // slot-major: the stored slots C..3^d-1 are one contiguous range of K
+  const int64_t c = dim == 2 ? 4 : 13;
+  convert_d2f(K + c * b * b * n, Kf, stencil_f32_count(dim, b, n), s);
+}
+
+void launch_stencil_dinv(const MeshDev& m, int64_t n, int b, const double* K, double* dinv,
+                         float* dinvf, cudaStream_t s) {
+  ProfScope ps("stencil_dinv", (double)n * b * (8.0 + 8.0 + (dinvf ? 4.0 : 0.0)), s);
+  k_stencil_dinv<<<grid_for(n, 256), 256, 0, s>>>(n, b, m.dim == 2 ? 4 : 13, K, dinv, dinvf);
+  PFF_LAUNCH("stencil_dinv");
+}
+
+}  // namespace pff

@@ -322,9 +322,12 @@ def test_block_sparse_kernel_variants_agree(dim, shape, seed, precision):
 
 @pytest.mark.parametrize("dim,shape,seed", [(2, (36, 22), 71), (3, (8, 6, 4), 72)])
 def test_mixed_vcycle_matches_fp64_vcycle(dim, shape, seed):
-    """The FP32 V-cycle (four-node stencil kernels, FP32 hierarchy copies) and the
-    FP64 V-cycle (separate one-node kernels) on the same hierarchy agree to FP32
-    accuracy; node counts that are not multiples of 4 exercise the ragged tail."""
+    """The FP32 V-cycle and the FP64 V-cycle on the same hierarchy agree to FP32
+    accuracy.  The FP32 level-0 kernels read only the symmetric half of each
+    stencil (the other half transposed from the neighbours, 2d u in the
+    node-major layout); the FP64 ones read the full stencil, so a wrong slot or
+    a missing transpose shows here.  Node counts that are not multiples of 4
+    exercise the ragged tail."""
     P, mesh, prm, state = make_case(dim, shape, seed, p=1e-3)
     assert mesh.n_nodes % 4 != 0
     act = torch.empty(mesh.n_nodes, dtype=torch.uint8, device="cuda")
