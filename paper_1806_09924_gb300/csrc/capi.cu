@@ -171,6 +171,7 @@ void release(pff_problem* P) {
   dfree(P->active_built);
   dfree(P->pc_tmp);
   dfree(P->qp);
+  dfree(P->Vf);
   if (P->side) {
     cudaStreamSynchronize(P->side);
     cudaStreamDestroy(P->side);

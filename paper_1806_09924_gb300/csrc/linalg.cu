@@ -131,20 +131,12 @@ __global__ void k_multi_axpy(const double* __restrict__ V, int64_t ld, int nv,
 // GB300 executes FP64 arithmetic at a small fraction of its FP32 rate, which
 // puts an FP64 multiply-add per streamed double below the HBM roofline.  The
 // mixed-precision Krylov path therefore takes its projection coefficients and
-// norms from an FP32 view of the FP64 data (the high word re-biased with
-// integer operations), and keeps FP64 arithmetic only for the update
-// w <- w - V h, whose coefficients h are the ones stored in the Hessenberg
-// matrix, so the Arnoldi relation holds to FP64 rounding.
-
-// FP32 view of a double from its high word: sign, exponent re-biased, 20 mantissa
-// bits (relative error < 2^-20).  |x| < 2^-126 gives 0, |x| >= 2^128 gives inf.
-__device__ __forceinline__ float f32_view(double x) {
-  const unsigned hw = (unsigned)__double2hiint(x);
-  const unsigned a = hw & 0x7fffffffu;
-  unsigned f = a >= (1151u << 20) ? 0x7f800000u : ((a - (896u << 20)) << 3);
-  f = a >= (897u << 20) ? f : 0u;
-  return __uint_as_float(f | (hw & 0x80000000u));
-}
+// norms in FP32: from FP32 views of the FP64 data (f32_view: the high word
+// re-biased with integer operations).  The view of each basis vector is stored
+// when the vector is normalised, so the coefficient pass streams 4 bytes per
+// element of V instead of 8.  FP64 arithmetic is kept only for the update w <- w - V h,
+// whose coefficients h are the ones stored in the Hessenberg matrix, so the
+// Arnoldi relation holds to FP64 rounding.
 
 template <int K>
 __device__ __forceinline__ void block_sum_f(float (&v)[K], float (*sh)[K]) {
@@ -167,9 +159,9 @@ __device__ __forceinline__ void block_sum_f(float (&v)[K], float (*sh)[K]) {
 constexpr int GS_CH = 8;
 
 // block b owns rows [b R, b R + R): it stages the FP32 view of w there in shared
-// memory, then sweeps the basis vectors GS_CH at a time.
-// part[k g + b] = block partial of <V_k, w> (k < nv); part[nv g + b] = of ||w||^2
-__global__ void __launch_bounds__(RB) k_gs_dot(const double* __restrict__ V, int64_t ld, int nv,
+// memory, then sweeps the FP32 basis vectors GS_CH at a time.
+// part[k g + b] = block partial of <Vf_k, w> (k < nv); part[nv g + b] = of ||w||^2
+__global__ void __launch_bounds__(RB) k_gs_dot(const float* __restrict__ Vf, int64_t ld, int nv,
                                                 const double* __restrict__ w, int64_t n, int R,
                                                 float* __restrict__ part) {
   extern __shared__ float swf[];
@@ -187,13 +179,13 @@ __global__ void __launch_bounds__(RB) k_gs_dot(const double* __restrict__ V, int
   if (threadIdx.x == 0) part[(int64_t)nv * g + b] = nrm[0];
   for (int k0 = 0; k0 < nv; k0 += GS_CH) {
     float acc[GS_CH] = {};
-    const double* Vk = V + (int64_t)k0 * ld + r0;
+    const float* Vk = Vf + (int64_t)k0 * ld + r0;
     const int kc = min(GS_CH, nv - k0);
     for (int i = threadIdx.x; i < len; i += RB) {
       const float wf = swf[i];
 #pragma unroll
       for (int c = 0; c < GS_CH; ++c)
-        if (c < kc) acc[c] += f32_view(Vk[(int64_t)c * ld + i]) * wf;
+        if (c < kc) acc[c] += Vk[(int64_t)c * ld + i] * wf;
     }
     block_sum_f<GS_CH>(acc, red);
     if (threadIdx.x < kc) part[(int64_t)(k0 + threadIdx.x) * g + b] = acc[0];
@@ -371,14 +363,14 @@ int gs_grid(int64_t n, int* rows_per_block) {
   return (int)((n + *rows_per_block - 1) / *rows_per_block);
 }
 
-void gs_dot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, float* part,
+void gs_dot_dev(const float* Vf, int64_t ld, int nv, const double* w, int64_t n, float* part,
                 double* out, cudaStream_t s) {
   int R = 0;
   const int g = gs_grid(n, &R);
   if (R > GS_MAX_ROWS || g > GS_MAX_BLOCKS || nv > 64)
     fail(PFF_ERR_INVALID_ARG, "mixed Gram-Schmidt: system or basis too large");
-  ProfScope ps("gs_dot", 8.0 * n * (nv + 1.0), s, 2);
-  k_gs_dot<<<g, RB, sizeof(float) * R, s>>>(V, ld, nv, w, n, R, part);
+  ProfScope ps("gs_dot", n * (4.0 * nv + 8.0), s, 2);
+  k_gs_dot<<<g, RB, sizeof(float) * R, s>>>(Vf, ld, nv, w, n, R, part);
   k_gs_final<<<nv + 1, RB, 0, s>>>(part, g, out);
   PFF_LAUNCH("gs_dot");
 }

@@ -84,6 +84,19 @@ T* dalloc(size_t n) {
   return static_cast<T*>(dmalloc(n * sizeof(T) + 16));
 }
 
+#ifdef __CUDACC__
+// FP32 view of a double from its high word: sign, exponent re-biased, 20 mantissa
+// bits (truncated; relative error < 2^-20), integer operations only.
+// |x| < 2^-126 gives 0, |x| >= 2^128 gives inf.
+__device__ __forceinline__ float f32_view(double x) {
+  const unsigned hw = (unsigned)__double2hiint(x);
+  const unsigned a = hw & 0x7fffffffu;
+  unsigned f = a >= (1151u << 20) ? 0x7f800000u : ((a - (896u << 20)) << 3);
+  f = a >= (897u << 20) ? f : 0u;
+  return __uint_as_float(f | (hw & 0x80000000u));
+}
+#endif
+
 // grid size for n threads of block b, capped
 inline unsigned grid_for(int64_t n, int block, int64_t cap = 1 << 30) {
   int64_t g = (n + block - 1) / block;
@@ -197,9 +210,10 @@ void dot_dev_f32(const float* x, const float* y, int64_t n, double* out, double*
 void multidot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, double* out,
                   double* partials, cudaStream_t s);
 // w -= sum_k h[k] V_k   (h on device)
-// Gram-Schmidt with FP32-view coefficients (mixed precision): out[k] = <V_k, w>
-// (k < nv), out[nv] = ||w||^2; part holds (nv + 1) * GS_MAX_BLOCKS floats
-void gs_dot_dev(const double* V, int64_t ld, int nv, const double* w, int64_t n, float* part,
+// Gram-Schmidt with FP32 coefficients (mixed precision): out[k] = <Vf_k, w>
+// (k < nv; Vf the f32_view of the basis), out[nv] = ||w||^2, from the f32_view
+// of w; part holds (nv + 1) * GS_MAX_BLOCKS floats
+void gs_dot_dev(const float* Vf, int64_t ld, int nv, const double* w, int64_t n, float* part,
                 double* out, cudaStream_t s);
 // w <- w - V h in FP64; *nrm2 = ||w_new||^2 (FP32 view); part holds GS_MAX_BLOCKS floats
 void gs_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n,
@@ -390,6 +404,7 @@ struct pff_problem {
   int krylov_m = 0;
   double *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *tmp = nullptr;
   float* gs_part = nullptr;   // partial sums of the mixed-precision Gram-Schmidt
+  float* Vf = nullptr;        // f32_view of the Krylov basis (mixed Gram-Schmidt)
   double* pc_tmp = nullptr;
   double* qp = nullptr;       // per-cell quadrature records (residual, phase-field assembly)   // work vector of the block lower-triangular preconditioner
   // one FGMRES iteration's device work (preconditioner + Jacobian apply) as a

@@ -28,16 +28,16 @@ namespace {
 using Clock = std::chrono::steady_clock;
 
 // Device bytes of a problem with nn nodes in dim dimensions and an FGMRES
-// restart of m: the Krylov basis (V: m+1, Z: m vectors), plus per node the
-// state, the stencils and their FP32 copies, both AMG hierarchies and the
-// set-up temporaries (measured peaks of the stream-ordered pool: about 12 KB
-// per node for a 2d 256^2 request including the fixed cost below, 20.3 KB per
-// node for the 3d 128^3 one), plus a fixed allowance for module load and pool
-// granularity.  The per-cell quadrature records of the residual and the
+// restart of m: the Krylov basis (V: m+1, Z: m vectors, and V's FP32 copy),
+// plus per node the state, the stencils and their FP32 copies, both AMG
+// hierarchies and the set-up temporaries (measured peaks of the stream-ordered
+// pool: about 12 KB per node for a 2d 256^2 request including the fixed cost
+// below, 20.3 KB per node for the 3d 128^3 one), plus a fixed allowance for
+// module load and pool granularity.  The per-cell quadrature records of the residual and the
 // phase-field assembly come on top (fewer cells than nodes, so nn bounds them).
 int64_t estimate_bytes(int dim, int64_t nn, int m) {
   const int64_t ndof = (int64_t)(dim + 1) * nn;
-  const int64_t krylov = (int64_t)(2 * m + 3) * ndof * 8;
+  const int64_t krylov = (int64_t)(2 * m + 3) * ndof * 8 + (int64_t)(m + 1) * ndof * 4;
   const int64_t per_node = dim == 2 ? 6000 : 19500;
   return krylov + per_node * nn + 8 * pff::qp_doubles(dim, nn) + (512LL << 20);
 }

@@ -53,10 +53,11 @@ __global__ void k_mul(int64_t n, const double* __restrict__ a, const double* __r
   if (i < n) c[i] = a[i] * b[i];
 }
 
-// w /= sqrt(*nrm2) (into dst); the scale is computed once per block (FP64
-// square roots and divides are slow on this GPU)
+// w /= sqrt(*nrm2) (into dst, and its f32_view into dstf unless null: the FP32
+// values the mixed Gram-Schmidt takes its coefficients from); the scale is
+// computed once per block (FP64 square roots and divides are slow on this GPU)
 __global__ void k_normalize(int64_t n, const double* __restrict__ w, const double* __restrict__ nrm2,
-                            double* __restrict__ dst) {
+                            double* __restrict__ dst, float* __restrict__ dstf) {
   __shared__ double sc;
   if (threadIdx.x == 0) {
     const double nn = *nrm2;
@@ -65,8 +66,11 @@ __global__ void k_normalize(int64_t n, const double* __restrict__ w, const doubl
   __syncthreads();
   const double s = sc;
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (int64_t)gridDim.x * blockDim.x)
-    dst[i] = w[i] * s;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const double v = w[i] * s;
+    dst[i] = v;
+    if (dstf) dstf[i] = f32_view(v);
+  }
 }
 
 __global__ void k_sub(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
@@ -140,6 +144,8 @@ void ensure_krylov(pff_problem* P, int m) {
   dfree(P->h);
   dfree(P->tmp);
   dfree(P->gs_part);
+  dfree(P->Vf);
+  P->Vf = nullptr;   // reallocated at the new size by the mixed path
   if (P->h_host) cudaFreeHost(P->h_host);
   const int64_t N = P->n_dofs;
   P->V = dalloc<double>((size_t)(m + 1) * N);
@@ -527,6 +533,9 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
   const bool gs_mixed = P->precision == PFF_PREC_MIXED && m + 1 <= 64 &&
                         N <= (int64_t)GS_MAX_ROWS * GS_MAX_BLOCKS;
   const bool use_iter_graph = o.precond == PFF_PC_AMG && N <= ITER_GRAPH_MAX_DOFS && o.iter_graph != 0;
+  // FP32 view of the basis for the projection coefficients of the mixed path
+  if (gs_mixed && !P->Vf) P->Vf = dalloc<float>((size_t)(P->krylov_m + 1) * N);
+  float* Vf = gs_mixed ? P->Vf : nullptr;
   PFF_CUDA(cudaMemsetAsync(x, 0, sizeof(double) * N, s));
   dot_dev(b, b, N, P->d_scalars, P->partials, s);
   const double beta0 = std::sqrt(fetch(P, P->d_scalars));
@@ -540,8 +549,8 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
   double beta = beta0;
   while (true) {
     {
-      ProfScope ps("normalize", 16.0 * N, s);
-      k_normalize<<<g, 256, 0, s>>>(N, w, P->d_scalars, V);   // d_scalars holds ||r||^2
+      ProfScope ps("normalize", (Vf ? 20.0 : 16.0) * N, s);
+      k_normalize<<<g, 256, 0, s>>>(N, w, P->d_scalars, V, Vf);   // d_scalars holds ||r||^2
     }
     PFF_LAUNCH("normalize");
     std::fill(gv.begin(), gv.end(), 0.0);
@@ -565,14 +574,14 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
       double hn = 0.0;
       if (gs_mixed) {
         // dh[0..j] = h, dh[j+1] = ||w||^2; dh[2(m+2)] = ||w - V h||^2
-        gs_dot_dev(V, N, j + 1, w, N, P->gs_part, dh, s);
+        gs_dot_dev(Vf, N, j + 1, w, N, P->gs_part, dh, s);
         gs_axpy_dev(V, N, j + 1, dh, w, N, P->gs_part, dh + 2 * (m + 2), s);
         PFF_CUDA(cudaMemcpyAsync(hh, dh, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, s));
         sync(P);
         for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i];
         if (hh[2 * (m + 2)] < hh[j + 1] / 64.0) {
           double* h2 = dh + (m + 2);
-          gs_dot_dev(V, N, j + 1, w, N, P->gs_part, h2, s);
+          gs_dot_dev(Vf, N, j + 1, w, N, P->gs_part, h2, s);
           gs_axpy_dev(V, N, j + 1, h2, w, N, P->gs_part, dh + 2 * (m + 2), s);
           PFF_CUDA(cudaMemcpyAsync(hh, dh, sizeof(double) * 3 * (m + 2), cudaMemcpyDeviceToHost, s));
           sync(P);
@@ -595,8 +604,9 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
       H[(size_t)(j + 1) * m + j] = hn;
       // V_{j+1} = w / hn  (norm squared already on device)
       {
-        ProfScope ps("normalize", 16.0 * N, s);
-        k_normalize<<<g, 256, 0, s>>>(N, w, dh + 2 * (m + 2), V + (int64_t)(j + 1) * N);
+        ProfScope ps("normalize", (Vf ? 20.0 : 16.0) * N, s);
+        k_normalize<<<g, 256, 0, s>>>(N, w, dh + 2 * (m + 2), V + (int64_t)(j + 1) * N,
+                                      Vf ? Vf + (int64_t)(j + 1) * N : nullptr);
       }
       PFF_LAUNCH("normalize");
       for (int i = 0; i < j; ++i) {
