@@ -925,7 +925,8 @@ template <>
 const float* stencil_vals<float>(const AmgLevel& L) { return L.stf; }
 
 template <class T>
-void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s);
+void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s,
+                  const double* rhs64 = nullptr, double* out64 = nullptr);
 
 // Levels 1.. of the cycle (many small, launch-bound kernels) replayed as one
 // CUDA graph.  It is captured on first use after each build, on a private
@@ -977,9 +978,13 @@ void coarse_cycle(Amg& amg, T* cb, T* cx, cudaStream_t s) {
   }
 }
 
+// rhs64 (stencil levels only): the first step reads the FP64 right-hand side and
+// stores it into rhs; out64: the last step writes the result there in FP64
+// (x is then not written)
 template <class T>
 void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* t, T* d, bool zero_start,
-            cudaStream_t s) {
+            cudaStream_t s, const double* rhs64 = nullptr, T* rhs_store = nullptr,
+            double* out64 = nullptr) {
   // Chebyshev iteration for D^-1 A on [lmax/30, 1.1 lmax]
   const double beta = 1.1 * L.lmax, alpha = L.lmax / ratio;
   const double theta = 0.5 * (beta + alpha), delta = 0.5 * (beta - alpha);
@@ -987,12 +992,14 @@ void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* 
   double rho = 1.0 / sigma;
   const Bsr& A = L.A;
   const int nb = A.nrows, b = A.br;
+  if ((rhs64 || out64) && !L.stencil) fail(PFF_ERR_INVALID_ARG, "FP64 cycle ends need a stencil level");
   T* cur = x;
   T* nxt = t;
   // first step: d = r / theta
   if (L.stencil) {
     launch_stencil_cheb<T>(L.mesh, nb, b, stencil_vals<T>(L), dinvs<T>(L), rhs, cur, nxt, d, 0.0,
-                           1.0 / theta, zero_start ? 1 : 0, s, sizeof(T) == 4 && L.stf_node_major);
+                           1.0 / theta, zero_start ? 1 : 0, s, sizeof(T) == 4 && L.stf_node_major,
+                           rhs64, rhs_store, degree == 1 ? out64 : nullptr);
   } else {
     bsr_cheb<T>(A, dinvs<T>(L), rhs, cur, nxt, d, T(0), T(1.0 / theta), zero_start, s);
   }
@@ -1001,19 +1008,25 @@ void smooth(const AmgLevel& L, int degree, double ratio, const T* rhs, T* x, T* 
     const double rn = 1.0 / (2.0 * sigma - rho);
     if (L.stencil) {
       launch_stencil_cheb<T>(L.mesh, nb, b, stencil_vals<T>(L), dinvs<T>(L), rhs, cur, nxt, d,
-                             rn * rho, 2.0 * rn / delta, 0, s, sizeof(T) == 4 && L.stf_node_major);
+                             rn * rho, 2.0 * rn / delta, 0, s, sizeof(T) == 4 && L.stf_node_major,
+                             nullptr, nullptr, k == degree - 1 ? out64 : nullptr);
     } else {
       bsr_cheb<T>(A, dinvs<T>(L), rhs, cur, nxt, d, T(rn * rho), T(2.0 * rn / delta), false, s);
     }
     std::swap(cur, nxt);
     rho = rn;
   }
-  if (cur != x) PFF_CUDA(cudaMemcpyAsync(x, cur, sizeof(T) * (size_t)nb * b, cudaMemcpyDeviceToDevice, s));
+  if (cur != x && !out64)
+    PFF_CUDA(cudaMemcpyAsync(x, cur, sizeof(T) * (size_t)nb * b, cudaMemcpyDeviceToDevice, s));
   PFF_LAUNCH("chebyshev");
 }
 
+// rhs64 / out64 (level 0 of a mixed cycle on a stencil level): the FP64 input
+// and output of the cycle, converted inside the first and last smoothing steps;
+// rhs then names the level's own FP32 right-hand side buffer, filled there.
 template <class T>
-void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
+void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s, const double* rhs64,
+                  double* out64) {
   if (l == (int)amg.lev.size()) {
     const T* M = nullptr;
     if constexpr (sizeof(T) == 8) M = reinterpret_cast<const T*>(amg.cinv);
@@ -1028,9 +1041,10 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
   T* d = reinterpret_cast<T*>(L.d);
   T* r = reinterpret_cast<T*>(L.r);
   const int deg = l == 0 ? amg.cheb_degree : amg.cheb_degree_coarse;
-  smooth<T>(L, deg, amg.cheb_ratio, rhs, x, t, d, true, s);
+  T* rhs_store = rhs64 ? const_cast<T*>(rhs) : nullptr;
+  smooth<T>(L, deg, amg.cheb_ratio, rhs, x, t, d, true, s, rhs64, rhs_store);
   if (L.terminal) {
-    smooth<T>(L, deg, amg.cheb_ratio, rhs, x, t, d, false, s);
+    smooth<T>(L, deg, amg.cheb_ratio, rhs, x, t, d, false, s, nullptr, nullptr, out64);
     return;
   }
   const Bsr& A = L.A;
@@ -1047,7 +1061,7 @@ void vcycle_level(Amg& amg, int l, const T* rhs, T* x, cudaStream_t s) {
   if (l == 0 && amg.use_graph && !amg.inline_levels) coarse_cycle<T>(amg, cb, cx, s);
   else vcycle_level<T>(amg, l + 1, cb, cx, s);
   spmv_t<T>(L.P, cx, x, T(1), T(1), s);
-  smooth<T>(L, deg, amg.cheb_ratio, rhs, x, t, d, false, s);
+  smooth<T>(L, deg, amg.cheb_ratio, rhs, x, t, d, false, s, nullptr, nullptr, out64);
 }
 
 struct SetupScratch {
@@ -1650,7 +1664,11 @@ void amg_vcycle(Amg& amg, const double* r, double* z, cudaStream_t s) {
   }
   AmgLevel& L0 = amg.lev[0];
   const int64_t n = L0.n;
-  if (amg.mixed) {
+  if (amg.mixed && L0.stencil) {
+    // the first and last level-0 smoothing steps convert r and z themselves
+    vcycle_level<float>(amg, 0, reinterpret_cast<float*>(L0.b), reinterpret_cast<float*>(L0.x), s,
+                        r, z);
+  } else if (amg.mixed) {
     float* b = reinterpret_cast<float*>(L0.b);
     float* x = reinterpret_cast<float*>(L0.x);
     {

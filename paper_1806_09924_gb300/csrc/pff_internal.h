@@ -312,10 +312,14 @@ void launch_node_coords(const MeshDev& m, int64_t n, double* xyz, cudaStream_t s
 // and the slots after it, stencil_to_f32 / stencil_to_node_major); node_major:
 // K is the node-major copy of a 2d displacement stencil, otherwise slot-major
 // with slot stride n
+// rhs64 (with rhs_store): take the right-hand side from an FP64 vector and store
+// its T copy; out64: write x_out in FP64 there instead of x_out and d.
 template <class T>
 void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T* dinv,
                          const T* rhs, const T* xin, T* xout, T* d, double cd, double cr,
-                         int zero_x, cudaStream_t s, bool node_major = false);
+                         int zero_x, cudaStream_t s, bool node_major = false,
+                         const double* rhs64 = nullptr, T* rhs_store = nullptr,
+                         double* out64 = nullptr);
 template <class T>
 void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const T* rhs, const T* x,
                           T* r, cudaStream_t s, bool node_major = false);

@@ -530,6 +530,9 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
   double* dh = P->h;            // [0, m+1): pass 1, [m+2, ...): pass 2, [2(m+2)]: ||w||^2
   double* hh = P->h_host;
   const unsigned g = grid_for(N, 256);
+  // k_normalize is grid-stride and each block first forms the scale (an FP64
+  // square root and divide, slow here): one resident wave of blocks
+  const unsigned gn = std::min<unsigned>(g, (unsigned)sm_count() * 8u);
   const bool gs_mixed = P->precision == PFF_PREC_MIXED && m + 1 <= 64 &&
                         N <= (int64_t)GS_MAX_ROWS * GS_MAX_BLOCKS;
   const bool use_iter_graph = o.precond == PFF_PC_AMG && N <= ITER_GRAPH_MAX_DOFS && o.iter_graph != 0;
@@ -550,7 +553,7 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
   while (true) {
     {
       ProfScope ps("normalize", (Vf ? 20.0 : 16.0) * N, s);
-      k_normalize<<<g, 256, 0, s>>>(N, w, P->d_scalars, V, Vf);   // d_scalars holds ||r||^2
+      k_normalize<<<gn, 256, 0, s>>>(N, w, P->d_scalars, V, Vf);   // d_scalars holds ||r||^2
     }
     PFF_LAUNCH("normalize");
     std::fill(gv.begin(), gv.end(), 0.0);
@@ -605,7 +608,7 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
       // V_{j+1} = w / hn  (norm squared already on device)
       {
         ProfScope ps("normalize", (Vf ? 20.0 : 16.0) * N, s);
-        k_normalize<<<g, 256, 0, s>>>(N, w, dh + 2 * (m + 2), V + (int64_t)(j + 1) * N,
+        k_normalize<<<gn, 256, 0, s>>>(N, w, dh + 2 * (m + 2), V + (int64_t)(j + 1) * N,
                                       Vf ? Vf + (int64_t)(j + 1) * N : nullptr);
       }
       PFF_LAUNCH("normalize");

@@ -69,7 +69,10 @@ __device__ __forceinline__ void stencil_apply(const MeshDev& m, int64_t n, int i
 
 // One Chebyshev step fused with the operator apply:
 // res = dinv .* (rhs - K x_in),  d = cd d + cr res,  x_out = x_in + d.
-// With zero_x the iterate starts at 0 (no apply).
+// With zero_x the iterate starts at 0 (no apply).  The first step of a mixed
+// V-cycle takes the FP64 right-hand side (rhs64, also stored as T into
+// rhs_store for the later steps) and the last one writes the FP64 result
+// (out64, instead of x_out and d), which saves two conversion passes.
 template <class T, int D, int B>
 __global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
                                                       const T* __restrict__ K,
@@ -77,7 +80,10 @@ __global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
                                                       const T* __restrict__ rhs,
                                                       const T* __restrict__ xin,
                                                       T* __restrict__ xout, T* __restrict__ d,
-                                                      T cd, T cr, int zero_x) {
+                                                      T cd, T cr, int zero_x,
+                                                      const double* __restrict__ rhs64,
+                                                      T* __restrict__ rhs_store,
+                                                      double* __restrict__ out64) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   T acc[B];
@@ -90,10 +96,22 @@ __global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
 #pragma unroll
   for (int a = 0; a < B; ++a) {
     const int64_t r = (int64_t)i * B + a;
-    const T res = dinv[r] * (rhs[r] - acc[a]);
+    T bv;
+    if (rhs64) {
+      bv = (T)rhs64[r];
+      rhs_store[r] = bv;
+    } else {
+      bv = rhs[r];
+    }
+    const T res = dinv[r] * (bv - acc[a]);
     const T dn = (zero_x ? T(0) : cd * d[r]) + cr * res;
-    d[r] = dn;
-    xout[r] = (zero_x ? T(0) : xin[r]) + dn;
+    const T xo = (zero_x ? T(0) : xin[r]) + dn;
+    if (out64) {
+      out64[r] = (double)xo;
+    } else {
+      d[r] = dn;
+      xout[r] = xo;
+    }
   }
 }
 
@@ -106,7 +124,10 @@ __device__ __forceinline__ void stencil_q2(const MeshDev& m, int n, const float*
                                            const float* __restrict__ dinv,
                                            const float* __restrict__ rhs,
                                            const float* __restrict__ xin, float* __restrict__ out,
-                                           float* __restrict__ d, float cd, float cr, int zero_x) {
+                                           float* __restrict__ d, float cd, float cr, int zero_x,
+                                           const double* __restrict__ rhs64,
+                                           float* __restrict__ rhs_store,
+                                           double* __restrict__ out64) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   float a0 = 0.f, a1 = 0.f;
@@ -132,7 +153,14 @@ __device__ __forceinline__ void stencil_q2(const MeshDev& m, int n, const float*
       a1 += k.z * x0 + k.w * x1;
     }
   }
-  const float2 b = reinterpret_cast<const float2*>(rhs)[i];
+  float2 b;
+  if (!RESID && rhs64) {
+    // scalar FP64 accesses: an FP64 vector may start at an odd element offset
+    b = make_float2((float)rhs64[2 * (int64_t)i], (float)rhs64[2 * (int64_t)i + 1]);
+    reinterpret_cast<float2*>(rhs_store)[i] = b;
+  } else {
+    b = reinterpret_cast<const float2*>(rhs)[i];
+  }
   if constexpr (RESID) {
     reinterpret_cast<float2*>(out)[i] = make_float2(b.x - a0, b.y - a1);
   } else {
@@ -146,8 +174,13 @@ __device__ __forceinline__ void stencil_q2(const MeshDev& m, int n, const float*
       dn.y += cd * dd.y;
       xo = make_float2(xi.x + dn.x, xi.y + dn.y);
     }
-    reinterpret_cast<float2*>(d)[i] = dn;
-    reinterpret_cast<float2*>(out)[i] = xo;
+    if (out64) {
+      out64[2 * (int64_t)i] = (double)xo.x;
+      out64[2 * (int64_t)i + 1] = (double)xo.y;
+    } else {
+      reinterpret_cast<float2*>(d)[i] = dn;
+      reinterpret_cast<float2*>(out)[i] = xo;
+    }
   }
 }
 
@@ -157,8 +190,11 @@ __global__ void __launch_bounds__(256) k_stencil_cheb_q2(MeshDev m, int n, const
                                                          const float* __restrict__ xin,
                                                          float* __restrict__ xout,
                                                          float* __restrict__ d, float cd, float cr,
-                                                         int zero_x) {
-  stencil_q2<false>(m, n, Kq, dinv, rhs, xin, xout, d, cd, cr, zero_x);
+                                                         int zero_x,
+                                                         const double* __restrict__ rhs64,
+                                                         float* __restrict__ rhs_store,
+                                                         double* __restrict__ out64) {
+  stencil_q2<false>(m, n, Kq, dinv, rhs, xin, xout, d, cd, cr, zero_x, rhs64, rhs_store, out64);
 }
 
 __global__ void __launch_bounds__(256) k_stencil_resid_q2(MeshDev m, int n,
@@ -166,7 +202,7 @@ __global__ void __launch_bounds__(256) k_stencil_resid_q2(MeshDev m, int n,
                                                           const float* __restrict__ rhs,
                                                           const float* __restrict__ x,
                                                           float* __restrict__ r) {
-  stencil_q2<true>(m, n, Kq, nullptr, rhs, x, r, nullptr, 0.f, 0.f, 0);
+  stencil_q2<true>(m, n, Kq, nullptr, rhs, x, r, nullptr, 0.f, 0.f, 0, nullptr, nullptr, nullptr);
 }
 
 // node-major FP32 copy of the 2d displacement stencil, slots 4..8 (2 x 2 blocks)
@@ -231,20 +267,26 @@ inline double slots_stored(int d, size_t es) { return es == 4 ? (NSd(d) + 1.0) /
 template <class T>
 void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T* dinv,
                          const T* rhs, const T* xin, T* xout, T* d, double cd, double cr,
-                         int zero_x, cudaStream_t s, bool node_major) {
-  // stencil values (unless starting from zero), then dinv, rhs, x_in, x_out, d read + write
+                         int zero_x, cudaStream_t s, bool node_major, const double* rhs64,
+                         T* rhs_store, double* out64) {
+  if (rhs64 && !rhs_store) fail(PFF_ERR_INVALID_ARG, "stencil Chebyshev: FP64 rhs without a store");
+  // stencil values (unless starting from zero), then dinv, rhs, x_in, x_out, d read + write;
+  // an FP64 rhs adds its FP32 store and 4 bytes per read, an FP64 result replaces x_out and d
   const double bytes = sizeof(T) * (double)n *
-                       ((zero_x ? 0.0 : slots_stored(m.dim, sizeof(T)) * b * b) + b * (zero_x ? 4.0 : 6.0));
+                       ((zero_x ? 0.0 : slots_stored(m.dim, sizeof(T)) * b * b) + b * (zero_x ? 4.0 : 6.0)) +
+                       (rhs64 ? 8.0 * n * b : 0.0) + (out64 ? (8.0 - 2.0 * sizeof(T)) * n * b : 0.0);
   ProfScope ps(sizeof(T) == 8 ? "cheb0_f64" : "cheb0_f32", bytes, s);
   if constexpr (sizeof(T) == 4) {
     if (node_major && m.dim == 2 && b == 2) {
       k_stencil_cheb_q2<<<grid_for(n, 256), 256, 0, s>>>(m, (int)n, K, dinv, rhs, xin, xout, d,
-                                                         (float)cd, (float)cr, zero_x);
+                                                         (float)cd, (float)cr, zero_x, rhs64,
+                                                         rhs_store, out64);
       PFF_LAUNCH("stencil_cheb");
       return;
     }
   }
-  STENCIL_DISPATCH(m.dim, b, k_stencil_cheb, m, n, K, dinv, rhs, xin, xout, d, (T)cd, (T)cr, zero_x);
+  STENCIL_DISPATCH(m.dim, b, k_stencil_cheb, m, n, K, dinv, rhs, xin, xout, d, (T)cd, (T)cr, zero_x,
+                   rhs64, rhs_store, out64);
   PFF_LAUNCH("stencil_cheb");
 }
 
@@ -266,10 +308,11 @@ void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const 
 
 template void launch_stencil_cheb<float>(const MeshDev&, int64_t, int, const float*, const float*,
                                          const float*, const float*, float*, float*, double, double,
-                                         int, cudaStream_t, bool);
+                                         int, cudaStream_t, bool, const double*, float*, double*);
 template void launch_stencil_cheb<double>(const MeshDev&, int64_t, int, const double*,
                                           const double*, const double*, const double*, double*,
-                                          double*, double, double, int, cudaStream_t, bool);
+                                          double*, double, double, int, cudaStream_t, bool,
+                                          const double*, double*, double*);
 template void launch_stencil_resid<float>(const MeshDev&, int64_t, int, const float*, const float*,
                                           const float*, float*, cudaStream_t, bool);
 template void launch_stencil_resid<double>(const MeshDev&, int64_t, int, const double*,
