@@ -340,6 +340,19 @@ int sm_count() {
   return n;
 }
 
+int64_t l2_cache_bytes() {
+  static const int64_t l2 = [] {
+    int dev = 0, v = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&v, cudaDevAttrL2CacheSize, dev) != cudaSuccess) {
+      cudaGetLastError();
+      v = 0;
+    }
+    return (int64_t)v;
+  }();
+  return l2;
+}
+
 // resident blocks per SM of a kernel (registers and shared memory permitting)
 template <class K>
 int resident_blocks(K kernel, size_t smem) {

@@ -219,6 +219,9 @@ void gs_dot_dev(const float* Vf, int64_t ld, int nv, const double* w, int64_t n,
 void gs_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n,
                  float* part, double* nrm2, cudaStream_t s);
 int sm_count();
+// L2 size of the current device in bytes (0 if unknown); first called outside
+// any stream capture
+int64_t l2_cache_bytes();
 void multi_axpy_dev(const double* V, int64_t ld, int nv, const double* h, double* w, int64_t n,
                     double sign, cudaStream_t s);
 void exclusive_scan_int(const int* in, int* out, int n, int* total_host, cudaStream_t s);

@@ -284,6 +284,7 @@ static double max_abs_diff(pff_problem* P, const double* a, const double* b, int
 void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   P->precision = o.precision;
   P->overlap = o.precond_overlap != 0;
+  l2_cache_bytes();   // device query made here, never inside a captured iteration
   if (o.precond == PFF_PC_JACOBI) return;
   AmgParams ap;
   ap.theta = o.amg_theta;
