@@ -114,6 +114,10 @@ typedef struct pff_options {
   int iter_graph;       /* 1: problems up to 10^6 DoFs on a non-default stream run each
                            FGMRES iteration's preconditioner and Jacobian apply as one CUDA
                            graph (same kernels, same order); 0: ordinary launches; 1 */
+  double amg_rebuild_phi; /* the phase-field hierarchy is rebuilt when the active set differs
+                           from the one it was built for in more than this fraction of the
+                           nodes (otherwise only its finest level is refreshed); 1e-3 */
+  int amg_age_phi;      /* ... or once it has served this many Newton iterations; 8 */
 } pff_options;
 
 /* Per loading step (or per Newton iteration for pff_newton_step) report. */

@@ -254,6 +254,7 @@ pff_options resolve_options(const pff_options* opts) {
   need(o.tol_change >= 0.0 && o.tol_active >= 0.0, "negative active-set band");
   need(o.amg_reuse_tol >= 0.0, "negative amg_reuse_tol");
   need(o.forcing_max >= 0.0 && o.forcing_max < 1.0, "forcing_max must be in [0, 1)");
+  need(o.amg_rebuild_phi >= 0.0 && o.amg_age_phi >= 1, "amg_rebuild_phi < 0 or amg_age_phi < 1");
   need(o.precond == PFF_PC_AMG || o.precond == PFF_PC_JACOBI || o.precond == PFF_PC_AMG_TRI,
        "unknown precond");
   need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 1 || o.spmv_group == 2 ||
@@ -292,6 +293,8 @@ void pff_default_options(pff_options* o) {
   o->amg_reuse_tol = 0.05;
   o->precond_overlap = 1;
   o->iter_graph = 1;
+  o->amg_rebuild_phi = 1e-3;
+  o->amg_age_phi = 8;
 }
 
 const char* pff_last_error(void) { return pff::g_msg.c_str(); }

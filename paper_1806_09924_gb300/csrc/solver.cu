@@ -351,15 +351,16 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     P->cur.amg_builds_u += 1;
   }
   // Phase-field block: rebuild when the active set differs from the one the
-  // hierarchy was built for in more than 0.1 % of the nodes (also across
-  // loading steps), or after 8 Newton iterations; otherwise keep the hierarchy
-  // and refresh only the finest level's stencil values and diagonal.  FGMRES
+  // hierarchy was built for in more than amg_rebuild_phi of the nodes (also
+  // across loading steps), or after amg_age_phi Newton iterations; otherwise
+  // keep the hierarchy and refresh only the finest level's stencil values and
+  // diagonal.  FGMRES
   // converges to its tolerance either way: a stale coarse space costs
   // iterations, not accuracy.
   bool rebuild = !allow_reuse || !P->amg_p_valid || !P->amg_p.built ||
-                 P->amg_p.mixed != ap.mixed || P->phi_amg_age >= 8 || P->amg_p.lev.empty() ||
-                 !P->active_built;
-  if (!rebuild) rebuild = count_diff(P, P->active, P->active_built, n) > n / 1000;
+                 P->amg_p.mixed != ap.mixed || P->phi_amg_age >= o.amg_age_phi ||
+                 P->amg_p.lev.empty() || !P->active_built;
+  if (!rebuild) rebuild = (double)count_diff(P, P->active, P->active_built, n) > o.amg_rebuild_phi * n;
   if (rebuild) {
     ProfScope ps("amg_setup_phi", 0.0, P->stream, 0);
     launch_stencil_to_bsr(m, n, 1, P->Kpp, P->App, P->stream);

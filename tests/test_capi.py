@@ -80,6 +80,7 @@ def test_defaults_and_argument_errors_without_gpu(lib):
     assert o.spmv_group == 0 and o.amg_reuse == 1 and o.amg_reuse_tol == 0.05
     assert o.precond_overlap == 1 and o.iter_graph == 1 and o.cheb_degree_coarse == 0
     assert o.forcing_max == 0.0
+    assert o.amg_rebuild_phi == 1e-3 and o.amg_age_phi == 8
     h = ctypes.c_void_p()
     nc = (ctypes.c_int32 * 3)(4, 4, 4)
     # invalid dimension is rejected before any device work
