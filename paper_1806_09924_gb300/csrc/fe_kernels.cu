@@ -1,9 +1,12 @@
 // Element-batched Q1 kernels for Formulation 1 (Section 2) and the Jacobian
 // blocks of Section 3.1 on tensor-product meshes.
 //
-// Every kernel is node-centric: one thread owns one mesh node and gathers the
-// contributions of its 2^d adjacent cells, so results are written once, without
-// atomics, and are bitwise reproducible.  Cells are axis-aligned boxes, so the
+// Every output is owned by one thread: a node's rows are gathered by that node's
+// thread from its 2^d adjacent cells, so results are written once, without
+// atomics, and are bitwise reproducible.  The residual and the phase-field
+// assembly first evaluate each cell's Gauss points once (one thread per cell,
+// records in global memory) and then gather; the other kernels recompute the
+// cell quantities they need per node.  Cells are axis-aligned boxes, so the
 // reference-to-physical map is diagonal (d/dx_l = (1/h_l) d/dxi_l); the
 // quadrature is the tensor 2^d-point Gauss rule.  Quadrature-point values use
 // the interpolated nodal phi, phi~ (then squared).
