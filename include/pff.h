@@ -141,6 +141,12 @@ typedef struct pff_step_report {
 
 void pff_default_options(pff_options* opts);
 
+/* Checks opts (NULL: the defaults) against the ranges documented above without
+ * touching the device.  Returns PFF_OK, or PFF_ERR_INVALID_ARG with the first
+ * violated rule in pff_last_error().  Every solver entry point applies the same
+ * check; pff_server_create applies it to the server's options. */
+int pff_check_options(const pff_options* opts);
+
 /* Mesh and problem set-up -------------------------------------------------- */
 
 /* Tensor-product Q1 mesh of the box spanned by axis_coords (Section 3: Q1^c on

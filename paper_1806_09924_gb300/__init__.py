@@ -112,6 +112,7 @@ _P = ctypes.c_void_p
 _D = ctypes.POINTER(ctypes.c_double)
 _SIGS = {
     "pff_default_options": (None, [ctypes.POINTER(PffOptions)]),
+    "pff_check_options": (ctypes.c_int, [ctypes.POINTER(PffOptions)]),
     "pff_create_mesh": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(_D), ctypes.POINTER(_P)]),
     "pff_set_material": (ctypes.c_int, [_P] + [ctypes.c_double] * 5),
@@ -198,6 +199,11 @@ def options(**kw) -> PffOptions:
             raise KeyError(k)
         setattr(o, k, v)
     return o
+
+
+def check_options(o: PffOptions) -> None:
+    """pff_check_options: raises PffError naming the first out-of-range field."""
+    _check(load_library().pff_check_options(ctypes.byref(o)))
 
 
 def _host(a, dtype=np.float64):

@@ -297,6 +297,12 @@ void pff_default_options(pff_options* o) {
   o->amg_age_phi = 8;
 }
 
+int pff_check_options(const pff_options* opts) {
+  API_BEGIN
+  resolve_options(opts);
+  API_END
+}
+
 const char* pff_last_error(void) { return pff::g_msg.c_str(); }
 
 int pff_memory_usage(int64_t* current, int64_t* peak, int reset_peak) {

@@ -266,6 +266,7 @@ int pff_server_create(int64_t budget_bytes, int n_workers, const pff_options* op
     pff::set_error(PFF_ERR_INVALID_ARG, "pff_server_create: bad budget, worker count or out");
     return PFF_ERR_INVALID_ARG;
   }
+  if (pff_check_options(opts) != PFF_OK) return PFF_ERR_INVALID_ARG;   // message already set
   auto* S = new pff_server();
   S->budget = budget_bytes;
   pff_default_options(&S->opts);

@@ -91,6 +91,25 @@ def test_defaults_and_argument_errors_without_gpu(lib):
     assert lib.pff_newton_step(None, None, None) == pff.PFF_ERR_INVALID_ARG
 
 
+def test_option_ranges_without_gpu(lib):
+    """pff_check_options accepts the defaults and rejects each out-of-range field
+    with its reason; a server is not created with invalid options."""
+    import paper_1806_09924_gb300 as pff
+    pff.check_options(pff.options())
+    assert lib.pff_check_options(None) == pff.PFF_OK
+    bad = [dict(precision=7), dict(krylov_restart=0), dict(cheb_degree=0), dict(max_newton=-1),
+           dict(tol_change=-1.0), dict(amg_reuse_tol=-0.1), dict(forcing_max=1.0), dict(precond=9),
+           dict(spmv_group=3), dict(amg_rebuild_phi=-1e-3), dict(amg_age_phi=0)]
+    for kw in bad:
+        with pytest.raises(pff.PffError) as e:
+            pff.check_options(pff.options(**kw))
+        assert e.value.code == pff.PFF_ERR_INVALID_ARG, kw
+    h = ctypes.c_void_p()
+    o = pff.options(amg_age_phi=0)
+    assert lib.pff_server_create(1 << 30, 1, ctypes.byref(o), ctypes.byref(h)) == pff.PFF_ERR_INVALID_ARG
+    assert b"amg_age_phi" in lib.pff_last_error()
+
+
 def test_server_host_logic_without_gpu(lib):
     """Argument checks, the admission estimate and the request queue need no GPU
     (workers that cannot get a stream leave the queue untouched)."""
