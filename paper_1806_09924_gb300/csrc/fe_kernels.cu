@@ -727,20 +727,31 @@ __global__ void __launch_bounds__(256) k_apply_assembled(MeshDev m, int64_t n,
 #pragma unroll
   for (int a = 0; a < D; ++a) yu[a] = 0.0;
   const double* xp = x + (int64_t)D * n;
+  const int64_t sy = m.nn[0], sz = (int64_t)m.nn[0] * m.nn[1];
+  // branch-free over the 3^d slots: a neighbour outside the mesh is replaced by
+  // node i and its x selected to zero, so all loads are independent
 #pragma unroll
   for (int s = 0; s < NS; ++s) {
-    const int64_t j = neighbour<D>(idx, s, m);
-    if (j < 0) continue;
+    const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = D == 3 ? s / 9 - 1 : 0;
+    bool ok = (idx[0] + ox >= 0) & (idx[0] + ox < m.nn[0]) & (idx[1] + oy >= 0) &
+              (idx[1] + oy < m.nn[1]);
+    if (D == 3) ok = ok & (idx[2] + oz >= 0) & (idx[2] + oz < m.nn[2]);
+    const int64_t j = ok ? i + ox + oy * sy + oz * sz : i;
     double xu[D];
 #pragma unroll
-    for (int e = 0; e < D; ++e) xu[e] = x[j * D + e];
+    for (int e = 0; e < D; ++e) {
+      const double v = x[j * D + e];
+      xu[e] = ok ? v : 0.0;
+    }
+    const double vp = xp[j];
+    const double xj = ok ? vp : 0.0;
 #pragma unroll
     for (int a = 0; a < D; ++a)
 #pragma unroll
       for (int e = 0; e < D; ++e) yu[a] += Kuu[((int64_t)(s * D + a) * D + e) * n + i] * xu[e];
 #pragma unroll
     for (int e = 0; e < D; ++e) yp += Kpu[(int64_t)(s * D + e) * n + i] * xu[e];
-    yp += Kpp[(int64_t)s * n + i] * xp[j];
+    yp += Kpp[(int64_t)s * n + i] * xj;
   }
   if (Sinv) {
 #pragma unroll
