@@ -345,8 +345,8 @@ pff_problem* create_problem(int dim, const int32_t* n_cells, const double* const
       P->nc[a] = n_cells[a];
       P->nn[a] = n_cells[a] + 1;
       P->hX[a].assign(axis_coords[a], axis_coords[a] + n_cells[a] + 1);
-      for (int i = 0; i < n_cells[a]; ++i)
-        need(std::isfinite(P->hX[a][i]) && P->hX[a][i + 1] > P->hX[a][i],
+      for (int i = 0; i <= n_cells[a]; ++i)
+        need(std::isfinite(P->hX[a][i]) && (i == 0 || P->hX[a][i] > P->hX[a][i - 1]),
              "axis coordinates must be finite and strictly increasing");
       nn *= P->nn[a];
       nc *= P->nc[a];

@@ -91,6 +91,36 @@ def test_defaults_and_argument_errors_without_gpu(lib):
     assert lib.pff_newton_step(None, None, None) == pff.PFF_ERR_INVALID_ARG
 
 
+def test_degenerate_meshes_are_rejected_without_gpu(lib):
+    """Zero cells, missing axes and coordinates that are not finite and strictly
+    increasing are argument errors, found before any device work."""
+    import numpy as np
+    import paper_1806_09924_gb300 as pff
+    h = ctypes.c_void_p()
+
+    def create(dim, axes):
+        nc = (ctypes.c_int32 * 3)(*[len(a) - 1 if a is not None else 1 for a in axes], *([1] * (3 - dim)))
+        keep = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None for a in axes]
+        ptrs = (ctypes.POINTER(ctypes.c_double) * dim)(
+            *[k.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if k is not None else None for k in keep])
+        rc = lib.pff_create_mesh(dim, nc, ptrs, ctypes.byref(h))
+        return rc, lib.pff_last_error()
+
+    good = np.linspace(-1.0, 1.0, 5)
+    cases = {
+        "zero cells": (2, [np.array([0.0]), good], b"n_cells"),
+        "missing axis": (2, [good, None], b"NULL"),
+        "repeated coordinate": (2, [good, np.array([0.0, 0.5, 0.5, 1.0])], b"strictly increasing"),
+        "decreasing": (3, [good, good, good[::-1].copy()], b"strictly increasing"),
+        "nan": (2, [good, np.array([0.0, np.nan, 1.0])], b"finite"),
+        "inf at the end": (2, [np.array([0.0, 1.0, np.inf]), good], b"finite"),
+    }
+    for name, (dim, axes, why) in cases.items():
+        rc, msg = create(dim, axes)
+        assert rc == pff.PFF_ERR_INVALID_ARG, name
+        assert why in msg, (name, msg)
+
+
 def test_option_ranges_without_gpu(lib):
     """pff_check_options accepts the defaults and rejects each out-of-range field
     with its reason; a server is not created with invalid options."""
