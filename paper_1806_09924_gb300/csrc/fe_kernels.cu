@@ -1194,7 +1194,7 @@ constexpr double B8 = 8.0;
 inline double NSd(int d) { return d == 2 ? 9.0 : 27.0; }
 }  // namespace
 
-void launch_phi_tilde(const MeshDev& m, int64_t n, int steps_done, const double* phi_old,
+void launch_phi_tilde(const MeshDev& /*m*/, int64_t n, int steps_done, const double* phi_old,
                       const double* phi_prev, double* phit, cudaStream_t s) {
   ProfScope ps("phi_tilde", 3.0 * B8 * n, s);
   // extrapolation needs two computed time levels: the initial crack field is not one

@@ -73,8 +73,8 @@ __global__ void k_normalize(int64_t n, const double* __restrict__ w, const doubl
   }
 }
 
-__global__ void k_sub(int64_t n, const double* __restrict__ a, const double* __restrict__ b,
-                      double* __restrict__ c) {
+// c = a - b elementwise; c may alias b (each thread reads before it writes)
+__global__ void k_sub(int64_t n, const double* a, const double* b, double* c) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) c[i] = a[i] - b[i];
 }
@@ -443,7 +443,7 @@ static void precond_apply_tri(pff_problem* P, const double* r, double* z) {
 // graph cannot be used (capture failed); the caller then launches directly.
 constexpr int64_t ITER_GRAPH_MAX_DOFS = 1000000;
 
-static bool iteration_graph(pff_problem* P, const pff_options& o) {
+static bool iteration_graph(pff_problem* P) {
   const uint64_t key[8] = {P->amg_u.build_id, P->amg_p.build_id,
                            (uint64_t)(uintptr_t)(P->op_S ? P->op_S : P->S),
                            (uint64_t)(uintptr_t)(P->op_Sinv ? P->op_Sinv : P->Sinv),
@@ -565,7 +565,7 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
     for (; j < m; ++j) {
       double* vj = V + (int64_t)j * N;
       double* zj = Z + (int64_t)j * N;
-      if (use_iter_graph && iteration_graph(P, o)) {
+      if (use_iter_graph && iteration_graph(P)) {
         PFF_CUDA(cudaMemcpyAsync(P->g_in, vj, sizeof(double) * N, cudaMemcpyDeviceToDevice, s));
         {
           ProfScope ps("iteration_graph", 0.0, s, P->iter_graph_kernels);
