@@ -1,4 +1,4 @@
-// Vector-BSR kernels of the AMG hierarchy (Section 3.2: each preconditioner
+// Vector-BSR kernels of the AMG hierarchy (Section 3.1: each preconditioner
 // block is one smoothed-aggregation V-cycle; its coarse operators, prolongators
 // and restrictions are block-sparse).
 //

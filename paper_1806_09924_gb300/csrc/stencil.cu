@@ -3,7 +3,7 @@
 // slot-major as produced by the element kernels), in FP32 or FP64, plus the
 // node-major FP32 copy of the 2d displacement stencil and the inverse
 // diagonals.  These are the bandwidth-bound kernels of every V-cycle (Section
-// 3.2: block-diagonal AMG preconditioner), kept in a file of their own.
+// 3.1: block-diagonal AMG preconditioner), kept in a file of their own.
 #include "pff_internal.h"
 
 namespace pff {
