@@ -258,10 +258,12 @@ int pff_set_state_dev(pff_problem* prob, const double* u_dev, const double* phi_
 
 /* Allocation-free TCV / COD ------------------------------------------------ */
 
-/* The paper has no counterpart of this entry point; it exists for callers that
- * must not allocate device memory when they evaluate the crack functionals --
- * code running while a stream is being captured into a CUDA graph, or an
- * application whose device memory is all handed out by its own pool.
+/* The paper has no counterpart of this entry point.  It exists for callers
+ * that cannot let a library allocate device memory: an application whose
+ * device memory is all handed out by its own pool allocator, or that reserved
+ * the whole GPU up front, would see an unplanned cudaMalloc fail or upset its
+ * own accounting.  pff_eval_tcv_cod allocates a small buffer for the COD line
+ * descriptors on every call; this variant does not.
  *
  * Same results as pff_eval_tcv_cod (same kernels, same arguments and
  * layouts), but all scratch memory (COD line descriptors, per-line integrals,
@@ -270,13 +272,16 @@ int pff_set_state_dev(pff_problem* prob, const double* u_dev, const double* phi_
  * until the process exits; nothing is allocated with cudaMalloc, cudaFree or
  * any allocating library routine.  At most PFF_NOALLOC_MAX_POINTS COD points
  * per call: larger n_pts returns PFF_ERR_CAPACITY without doing any work.
+ * The call synchronizes the problem's stream before it returns: tcv and cod
+ * are ordinary (pageable) host memory that holds the results on return.
  *
  * The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress); make that first call before any stream capture.
- * Every call on a device shares the one array: calls whose work overlaps on
- * the GPU (several problems or threads on different streams at once) race and
- * must be serialized by the caller.  No part of the array needs to start at
- * zero: each slot a call reads was written earlier in the same call. */
+ * (cudaGetSymbolAddress, checked) with that device current.  Every call on a
+ * device shares the one array and it keeps the last call's contents: calls
+ * whose work overlaps on the GPU (several problems or threads on different
+ * streams at once) race and must be serialized by the caller.  No part of the
+ * array needs to start at zero: each slot a call reads was written earlier in
+ * the same call. */
 #define PFF_NOALLOC_MAX_POINTS 1024
 int pff_eval_tcv_cod_noalloc(pff_problem* prob, int n_pts, const double* pts, double* tcv,
                              double* cod);

@@ -116,22 +116,6 @@ void dfree(void* p) {
 
 using pff::fail;
 
-#define API_BEGIN try {
-#define API_END                                      \
-  }                                                  \
-  catch (const pff::Failure& f) {                    \
-    pff::set_error(f.code, f.msg);                   \
-    return f.code;                                   \
-  }                                                  \
-  catch (const std::bad_alloc&) {                    \
-    pff::set_error(PFF_ERR_OOM, "host allocation failed"); \
-    return PFF_ERR_OOM;                              \
-  }                                                  \
-  catch (const std::exception& e) {                  \
-    pff::set_error(PFF_ERR_INVALID_ARG, e.what());   \
-    return PFF_ERR_INVALID_ARG;                      \
-  }                                                  \
-  return PFF_OK;
 
 namespace {
 
@@ -225,8 +209,12 @@ std::vector<double> crack_field(const pff_problem* P, double l0) {
   return phi;
 }
 
+}  // namespace
+
+namespace pff {
+
 // cells of one axis whose closed interval contains x, with averaging weights
-std::vector<std::pair<int, double>> columns(const std::vector<double>& X, double x) {
+static std::vector<std::pair<int, double>> axis_columns(const std::vector<double>& X, double x) {
   std::vector<std::pair<int, double>> hits;
   const int n = (int)X.size() - 1;
   if (!(x >= X[0] && x <= X[n])) fail(PFF_ERR_INVALID_ARG, "COD point outside the domain");
@@ -237,7 +225,34 @@ std::vector<std::pair<int, double>> columns(const std::vector<double>& X, double
   return hits;
 }
 
-}  // namespace
+std::vector<CodColumn> cod_columns(const pff_problem* P, int n_pts, const double* pts) {
+  const int d = P->dim;
+  std::vector<CodColumn> cols;
+  cols.reserve((size_t)n_pts * (d == 3 ? 4 : 2));
+  for (int k = 0; k < n_pts; ++k) {
+    const double x = pts[k * (d - 1)];
+    const auto cx = axis_columns(P->hX[0], x);
+    std::vector<std::pair<int, double>> cy = {{0, 1.0}};
+    if (d == 3) cy = axis_columns(P->hX[1], pts[k * 2 + 1]);
+    for (auto& a : cx)
+      for (auto& b : cy) {
+        CodColumn c{};
+        c.col[0] = a.first;
+        c.xi[0] = (x - P->hX[0][a.first]) / (P->hX[0][a.first + 1] - P->hX[0][a.first]);
+        if (d == 3) {
+          const double y = pts[k * 2 + 1];
+          c.col[1] = b.first;
+          c.xi[1] = (y - P->hX[1][b.first]) / (P->hX[1][b.first + 1] - P->hX[1][b.first]);
+        }
+        c.w = a.second * b.second;
+        c.point = k;
+        cols.push_back(c);
+      }
+  }
+  return cols;
+}
+
+}  // namespace pff
 
 extern "C" void pff_default_options(pff_options* o);
 
@@ -585,26 +600,7 @@ int pff_eval_tcv_cod(pff_problem* P, int n_pts, const double* pts, double* tcv, 
     *tcv = P->h_scalars[0];
   }
   if (cod && n_pts > 0) {
-    const int d = P->dim;
-    std::vector<pff::CodColumn> cols;
-    for (int k = 0; k < n_pts; ++k) {
-      const auto cx = columns(P->hX[0], pts[k * (d - 1)]);
-      std::vector<std::pair<int, double>> cy = {{0, 1.0}};
-      if (d == 3) cy = columns(P->hX[1], pts[k * 2 + 1]);
-      for (auto& a : cx)
-        for (auto& b : cy) {
-          pff::CodColumn c{};
-          c.col[0] = a.first;
-          c.xi[0] = (pts[k * (d - 1)] - P->hX[0][a.first]) / (P->hX[0][a.first + 1] - P->hX[0][a.first]);
-          if (d == 3) {
-            c.col[1] = b.first;
-            c.xi[1] = (pts[k * 2 + 1] - P->hX[1][b.first]) / (P->hX[1][b.first + 1] - P->hX[1][b.first]);
-          }
-          c.w = a.second * b.second;
-          c.point = k;
-          cols.push_back(c);
-        }
-    }
+    const std::vector<pff::CodColumn> cols = pff::cod_columns(P, n_pts, pts);
     const int nc = (int)cols.size();
     auto* dcols = pff::dalloc<pff::CodColumn>(nc);
     double* dout = pff::dalloc<double>(nc);

@@ -1,16 +1,17 @@
 // TCV / COD evaluation that performs no device allocation.
 //
 // pff_eval_tcv_cod allocates a small device buffer for the COD line
-// descriptors on every call.  Callers that cannot allocate device memory at
-// that point -- for instance code that runs while a CUDA stream is being
-// captured into a graph, or an application whose device memory is entirely
-// owned by its own pool allocator -- use pff_eval_tcv_cod_noalloc instead.  It
-// runs the same TCV and COD kernels, but every piece of scratch they need (line
-// descriptors, per-line sums, per-block TCV partial sums) lives in one
-// file-scope device array of fixed size, loaded with the library and kept by
-// every GPU that uses it until the process exits.
-#include <algorithm>
-#include <cmath>
+// descriptors on every call.  Some callers cannot let a library allocate
+// device memory: an application whose device memory is all handed out by its
+// own pool allocator, or one that has reserved the whole memory of the GPU up
+// front, gets an out-of-memory error (or breaks its own accounting) from a
+// cudaMalloc it did not plan for.  Those callers use pff_eval_tcv_cod_noalloc
+// instead.  It runs the same TCV and COD kernels, but every piece of scratch
+// they need (line descriptors, per-line sums, per-block TCV partial sums)
+// lives in one file-scope device array of fixed size, loaded with the library
+// and kept by every GPU that uses it until the process exits.  The call
+// synchronizes the problem's stream before it returns (the results are copied
+// to the caller's host memory).
 #include <mutex>
 #include <string>
 #include <vector>
@@ -48,85 +49,44 @@ double* scratch_address() {
   return g_addr[dev];
 }
 
-// cells along one axis whose closed interval contains x, each with its averaging weight
-void axis_cells(const std::vector<double>& X, double x, int* idx, double* w, int* count) {
-  const int n = (int)X.size() - 1;
-  if (!(x >= X[0] && x <= X[n])) fail(PFF_ERR_INVALID_ARG, "COD point outside the domain");
-  const int p = (int)(std::upper_bound(X.begin(), X.end(), x) - X.begin());
-  int c = 0;
-  for (int i = std::max(0, p - 2); i < std::min(n, p + 1) && c < 2; ++i)
-    if (X[i] <= x && x <= X[i + 1]) idx[c++] = i;
-  for (int k = 0; k < c; ++k) w[k] = 1.0 / c;
-  *count = c;
-}
-
 }  // namespace
 }  // namespace pff
 
 extern "C" int pff_eval_tcv_cod_noalloc(pff_problem* P, int n_pts, const double* pts, double* tcv,
                                         double* cod) {
-  try {
-    if (!P) pff::fail(PFF_ERR_INVALID_ARG, "problem is NULL");
-    if (n_pts < 0 || (n_pts > 0 && !pts)) pff::fail(PFF_ERR_INVALID_ARG, "bad COD points");
-    if (n_pts > PFF_NOALLOC_MAX_POINTS)
-      pff::fail(PFF_ERR_CAPACITY, "pff_eval_tcv_cod_noalloc: " + std::to_string(n_pts) +
-                                      " points exceed the fixed scratch limit of " +
-                                      std::to_string(PFF_NOALLOC_MAX_POINTS));
-    double* base = pff::scratch_address();
-    auto* cols_dev = reinterpret_cast<pff::CodColumn*>(base);
-    double* vals_dev = base + pff::kColDoubles;
-    double* part_dev = vals_dev + pff::kMaxCols;
-    double* tcv_dev = part_dev + pff::RED_PARTIALS;
-    const auto m = P->mesh();
-    cudaStream_t s = P->stream;
-    if (tcv) {
-      // every partial slot the final sum reads is written by this launch
-      pff::tcv_dev(m, P->n_cells, P->u, P->phi, tcv_dev, part_dev, s);
-      PFF_CUDA(cudaMemcpyAsync(tcv, tcv_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
-    }
-    if (cod && n_pts > 0) {
-      const int d = P->dim;
-      std::vector<pff::CodColumn> cols;
-      cols.reserve((size_t)n_pts * (d == 3 ? 4 : 2));
-      for (int k = 0; k < n_pts; ++k) {
-        int ix[2], iy[2] = {0, 0}, nx = 0, ny = 1;
-        double wx[2], wy[2] = {1.0, 1.0};
-        pff::axis_cells(P->hX[0], pts[k * (d - 1)], ix, wx, &nx);
-        if (d == 3) pff::axis_cells(P->hX[1], pts[k * 2 + 1], iy, wy, &ny);
-        for (int a = 0; a < nx; ++a)
-          for (int b = 0; b < ny; ++b) {
-            pff::CodColumn c{};
-            const double x = pts[k * (d - 1)];
-            c.col[0] = ix[a];
-            c.xi[0] = (x - P->hX[0][ix[a]]) / (P->hX[0][ix[a] + 1] - P->hX[0][ix[a]]);
-            if (d == 3) {
-              const double y = pts[k * 2 + 1];
-              c.col[1] = iy[b];
-              c.xi[1] = (y - P->hX[1][iy[b]]) / (P->hX[1][iy[b] + 1] - P->hX[1][iy[b]]);
-            }
-            c.w = wx[a] * wy[b];
-            c.point = k;
-            cols.push_back(c);
-          }
-      }
-      const int nc = (int)cols.size();
-      std::vector<double> vals(nc);
-      // each line's integral is written by its own block before it is read back
-      PFF_CUDA(cudaMemcpyAsync(cols_dev, cols.data(), sizeof(pff::CodColumn) * nc,
-                               cudaMemcpyHostToDevice, s));
-      pff::cod_dev(m, cols_dev, nc, P->u, P->phi, vals_dev, n_pts, s);
-      PFF_CUDA(cudaMemcpyAsync(vals.data(), vals_dev, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
-      PFF_CUDA(cudaStreamSynchronize(s));
-      for (int k = 0; k < n_pts; ++k) cod[k] = 0.0;
-      for (int c = 0; c < nc; ++c) cod[cols[c].point] += vals[c];
-    }
-    PFF_CUDA(cudaStreamSynchronize(s));
-  } catch (const pff::Failure& f) {
-    pff::set_error(f.code, f.msg);
-    return f.code;
-  } catch (const std::exception& e) {
-    pff::set_error(PFF_ERR_INVALID_ARG, e.what());
-    return PFF_ERR_INVALID_ARG;
+  API_BEGIN
+  if (!P) pff::fail(PFF_ERR_INVALID_ARG, "problem is NULL");
+  if (n_pts < 0 || (n_pts > 0 && !pts)) pff::fail(PFF_ERR_INVALID_ARG, "bad COD points");
+  if (n_pts > PFF_NOALLOC_MAX_POINTS)
+    pff::fail(PFF_ERR_CAPACITY, "pff_eval_tcv_cod_noalloc: " + std::to_string(n_pts) +
+                                    " points exceed the fixed scratch limit of " +
+                                    std::to_string(PFF_NOALLOC_MAX_POINTS));
+  double* base = pff::scratch_address();
+  auto* cols_dev = reinterpret_cast<pff::CodColumn*>(base);
+  double* vals_dev = base + pff::kColDoubles;
+  double* part_dev = vals_dev + pff::kMaxCols;
+  double* tcv_dev = part_dev + pff::RED_PARTIALS;
+  const auto m = P->mesh();
+  cudaStream_t s = P->stream;
+  if (tcv) {
+    // every partial slot the final sum reads is written by this launch
+    pff::tcv_dev(m, P->n_cells, P->u, P->phi, tcv_dev, part_dev, s);
+    PFF_CUDA(cudaMemcpyAsync(tcv, tcv_dev, sizeof(double), cudaMemcpyDeviceToHost, s));
   }
-  return PFF_OK;
+  if (cod && n_pts > 0) {
+    // the same line descriptors as pff_eval_tcv_cod (at most 4 per point)
+    const std::vector<pff::CodColumn> cols = pff::cod_columns(P, n_pts, pts);
+    const int nc = (int)cols.size();
+    std::vector<double> vals(nc);
+    // each line's integral is written by its own block before it is read back
+    PFF_CUDA(cudaMemcpyAsync(cols_dev, cols.data(), sizeof(pff::CodColumn) * nc,
+                             cudaMemcpyHostToDevice, s));
+    pff::cod_dev(m, cols_dev, nc, P->u, P->phi, vals_dev, n_pts, s);
+    PFF_CUDA(cudaMemcpyAsync(vals.data(), vals_dev, sizeof(double) * nc, cudaMemcpyDeviceToHost, s));
+    PFF_CUDA(cudaStreamSynchronize(s));
+    for (int k = 0; k < n_pts; ++k) cod[k] = 0.0;
+    for (int c = 0; c < nc; ++c) cod[cols[c].point] += vals[c];
+  }
+  PFF_CUDA(cudaStreamSynchronize(s));
+  API_END
 }

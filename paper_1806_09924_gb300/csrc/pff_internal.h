@@ -17,6 +17,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -41,6 +43,26 @@ void set_error(int code, const std::string& msg);
 void check_cuda(cudaError_t e, const char* what);
 #define PFF_CUDA(x) ::pff::check_cuda((x), #x)
 #define PFF_LAUNCH(what) ::pff::check_cuda(cudaGetLastError(), what)
+
+// Body of an extern "C" entry point: a Failure returns its code, a failed host
+// allocation PFF_ERR_OOM, any other exception PFF_ERR_INVALID_ARG; the message
+// is kept for pff_last_error.
+#define API_BEGIN try {
+#define API_END                                            \
+  }                                                        \
+  catch (const ::pff::Failure& f) {                        \
+    ::pff::set_error(f.code, f.msg);                       \
+    return f.code;                                         \
+  }                                                        \
+  catch (const std::bad_alloc&) {                          \
+    ::pff::set_error(PFF_ERR_OOM, "host allocation failed"); \
+    return PFF_ERR_OOM;                                    \
+  }                                                        \
+  catch (const std::exception& e) {                        \
+    ::pff::set_error(PFF_ERR_INVALID_ARG, e.what());       \
+    return PFF_ERR_INVALID_ARG;                            \
+  }                                                        \
+  return PFF_OK;
 
 // ------------------------------------------------------- launch accounting --
 // Every kernel launch is counted; when profiling is enabled, the launches of a
@@ -463,4 +485,8 @@ int fgmres(pff_problem* P, const pff_options& o, const double* b, double* x, int
 void apply_jacobian(pff_problem* P, int variant, const double* x, double* y, const double* Sinv);
 void ensure_krylov(pff_problem* P, int m);
 void scale_into(const double* s, const double* x, double* y, int64_t n, cudaStream_t st);
+// COD line descriptors of n_pts points (x in 2d; (x, y) pairs in 3d): the cells each
+// line crosses, a line on a mesh line split between the two adjacent cells with
+// weight 1/2 each (capi.cu; shared by both TCV / COD entry points)
+std::vector<CodColumn> cod_columns(const pff_problem* P, int n_pts, const double* pts);
 }  // namespace pff

@@ -1,13 +1,13 @@
 """The allocation-free TCV / COD entry point agrees with the allocating one.
 
-Some callers cannot allocate device memory at the moment they evaluate the
-crack functionals: code running while a CUDA stream is being captured into a
-graph (allocation calls are not allowed inside a capture), or an application
-whose device memory is handed out entirely by its own pool allocator.
-pff_eval_tcv_cod_noalloc serves them from a fixed scratch array inside the
-library.  It must return what pff_eval_tcv_cod returns, also on a second call
-with fewer points (the scratch keeps the previous call's contents), and it must
-refuse more points than its scratch holds.
+Some callers cannot let a library allocate device memory while they evaluate
+the crack functionals: an application whose device memory is all handed out
+by its own pool allocator, or that reserved the whole GPU up front, would see
+an unplanned cudaMalloc fail.  pff_eval_tcv_cod_noalloc serves them from a
+fixed scratch array inside the library.  It must return what pff_eval_tcv_cod
+returns, also on a second call with fewer points (the scratch keeps the
+previous call's contents), and it must refuse more points than its scratch
+holds.
 """
 import numpy as np
 import pytest
