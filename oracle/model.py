@@ -6,7 +6,7 @@ cell, evaluate the integrands of Eq. (E22ATW) / (E33ATW) and of the Jacobian
 blocks of Section 3.1, integrate, and scatter-add into global vectors /
 sparse matrices.
 
-Conventions (readings of the paper listed in the design doc):
+Conventions (readings of the paper where it is silent or inconsistent):
 
 * ``gradient`` returns r(U), the left-hand sides of Eq. (E22ATW) and
   (E33ATW) tested with each basis function (r = grad E).  The Newton

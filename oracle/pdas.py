@@ -64,6 +64,7 @@ class Options:
     full_jacobian: bool = False
     tol_active: float = 1e-10    # threshold tau of step 2, in units of G_c / eps
     tol_change: float = 1e-9     # membership changes within this band (G_c/eps units) are ties
+    trace: bool = False          # keep (raw set, locked set, A_k) of every iteration in the report
 
 
 @dataclass
@@ -79,6 +80,7 @@ class StepReport:
     rho: float = 0.0
     history: List[float] = field(default_factory=list)
     omegas: List[float] = field(default_factory=list)
+    trace: list = field(default_factory=list)   # (raw, locked, A) per iteration when Options.trace
 
 
 @dataclass
@@ -185,6 +187,8 @@ def loading_step(st: State, p: float, opts: Options = Options()) -> StepReport:
             toggles += raw != raw_prev
             locked |= toggles >= opts.cycle_lock
         A = raw | locked
+        if opts.trace:
+            rep.trace.append((raw.copy(), locked.copy(), A.copy()))
         free = ~np.concatenate([fixed_u, A])
         rho = _reduced_scaled(F, S, free)
         rho_inf = float(np.max(np.abs(rho))) if rho.size else 0.0

@@ -166,3 +166,126 @@ def test_two_loading_steps_irreversible_and_extrapolated():
     assert np.all(phi2 <= phi1 + 1e-15) and np.all(st.phi <= phi2 + 1e-15)   # phi <= phi_old
     # the opening grows with the pressure and stays bounded (no kappa-only region is loaded)
     assert np.max(np.abs(st.u)) < 10 * 1.5e-3
+
+
+# ---------------------------------------------------------------- cycle rule --
+def _cyclic_case(n_cells, p):
+    w = W.cyclic_loading(n_cells)
+    mesh = fe.Mesh(w.coords)
+    prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=p)
+    return w, mesh, prm
+
+
+def test_cycle_lock_replays_the_unlocked_iteration():
+    """Section 3: indices whose active-set membership alternates are locked active.
+
+    Reading: an index is locked once its raw membership (indicator > tau) has
+    changed ``cycle_lock`` times within the loading step.  Until the first
+    lock the locked run must repeat the unlocked run exactly; the lock must
+    fire at the first iteration where the toggle counts -- counted here by
+    hand from the unlocked run's raw sets -- reach the limit, on exactly those
+    indices; a locked index never unlocks and stays in A_k; and the converged
+    point satisfies the complementarity conditions on every index the rule
+    did not lock.  The case (low G_c, pressure near critical) alternates."""
+    L = 2
+    w, mesh, prm = _cyclic_case(24, 5e-3)
+    st_free = pdas.State.initial(mesh, prm, w.phi0())
+    rep_free = pdas.loading_step(st_free, prm.p, pdas.Options(cycle_lock=10 ** 9, trace=True))
+    st = pdas.State.initial(mesh, prm, w.phi0())
+    rep = pdas.loading_step(st, prm.p, pdas.Options(cycle_lock=L, trace=True))
+    raws = [t[0] for t in rep_free.trace]
+    counts = np.zeros(mesh.n_nodes, dtype=np.int64)
+    t_star = None
+    for k in range(1, len(raws)):
+        counts += raws[k] != raws[k - 1]
+        if np.any(counts >= L):
+            t_star = k
+            break
+    assert t_star is not None, "the case must alternate"
+    for k in range(t_star + 1):
+        assert np.array_equal(rep.trace[k][0], raws[k])
+    for k in range(t_star):
+        assert not rep.trace[k][1].any()
+    assert np.array_equal(rep.trace[t_star][1], counts >= L)
+    for k in range(t_star, len(rep.trace)):
+        raw, lk, A = rep.trace[k]
+        assert np.array_equal(A, raw | lk)
+        if k > t_star:
+            assert np.all(lk[rep.trace[k - 1][1]])          # locks persist
+    locked = rep.trace[-1][1]
+    assert rep.converged and rep.locked == int(locked.sum()) > 0
+    # complementarity at the converged point
+    d, n = mesh.d, mesh.n_nodes
+    phit = st.phi_prev                                       # first step: phi~ = phi_old
+    r_u, r_phi = model.gradient(mesh, prm, st.u, st.phi, phit)
+    S = model.scaling(mesh, prm, phit)
+    m = model.lumped_mass(mesh)
+    A = st.active
+    free_u = ~np.repeat(mesh.boundary_nodes(), d)
+    assert np.max(np.abs(r_u.ravel()[free_u] / S[: d * n][free_u])) <= 1e-10 * rep.rho0
+    assert np.all(A[locked]) and np.all(st.phi[A] == st.phi_prev[A])
+    lam = -r_phi / m
+    tau = pdas.active_threshold(prm, pdas.Options())
+    assert np.all(lam[A & ~locked] > tau)                    # multiplier positive where not locked
+    assert np.max(np.abs(r_phi[~A] / S[d * n:][~A])) <= 1e-10 * rep.rho0
+
+
+def test_phi_tilde_is_exact_on_linear_histories():
+    """Formulation 1: phi~ is the linear extrapolation in time of the two
+    previous levels.  A history that is linear in time, phi(t) = a + b t with
+    phi_prev = phi(0), phi_old = phi(1), must give phi(2) wherever that value
+    lies in [0, 1]; only outside [0, 1] may the clamp act, and then it returns
+    the nearer bound.  A constant history extrapolates to itself, and before
+    two computed time levels exist (steps 1, 2) phi~ = phi_old."""
+    rng = np.random.default_rng(7)
+    n = 4000
+    a = rng.uniform(0.3, 0.7, n)
+    b = rng.uniform(-0.3, 0.3, n)
+    b[:50] = 0.0
+    st = pdas.State(mesh=None, prm=None, u=None, phi=a + b, phi_old=a + b, phi_prev=a,
+                    steps_done=2)
+    pred = a + 2.0 * b
+    got = st.phi_tilde()
+    inside = (pred >= 0.0) & (pred <= 1.0)
+    assert inside.sum() > n // 2 and (~inside).sum() > 100
+    np.testing.assert_allclose(got[inside], pred[inside], rtol=0, atol=4e-16)
+    assert np.all(got[pred < 0.0] == 0.0) and np.all(got[pred > 1.0] == 1.0)
+    np.testing.assert_allclose(got[:50], a[:50], rtol=0, atol=4e-16)
+    for done in (0, 1):
+        st.steps_done = done
+        assert np.array_equal(st.phi_tilde(), st.phi_old)
+
+
+@pytest.mark.parametrize("which", ["sneddon64", "cyclic24"])
+def test_irreversibility_slack_is_bounded_by_tau_over_c(which):
+    """phi <= phi_old (Formulation 1) holds up to tau / c on the inactive set.
+
+    The active-set rule with threshold tau > 0 leaves a node free while
+    lambda_i + c (phi_i - phi_old,i) <= tau, and at a converged point the free
+    rows are stationary (lambda_i ~ 0), so a free node can exceed phi_old by
+    up to (tau - lambda_i) / c ~ tau / c = 1e-9 (c = 0.1 G_c/eps, tau = 1e-10
+    G_c/eps); active nodes meet the constraint exactly.  Checked over every
+    step of a load / unload / reload cycle and on the Sneddon step, where the
+    slack is attained in part (far-field nodes with phi_old = 1)."""
+    if which == "sneddon64":
+        w = W.scaled_workload(W.config(0), 64)
+    else:
+        w = W.cyclic_loading(24)
+    mesh = fe.Mesh(w.coords)
+    prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressures[0])
+    st = pdas.State.initial(mesh, prm, w.phi0())
+    o = pdas.Options()
+    tau, c = pdas.active_threshold(prm, o), pdas.active_constant(prm, o)
+    worst = -np.inf
+    for p in w.pressures:
+        rep = pdas.loading_step(st, p, o)
+        assert rep.converged
+        free = ~st.active
+        lam = st.indicator - c * (st.phi - st.phi_prev)
+        assert np.max(np.abs(lam[free])) <= 1e-3 * tau
+        exc = st.phi - st.phi_prev
+        assert np.all(exc[st.active] == 0.0)
+        assert np.max(exc[free]) <= (tau + np.max(np.abs(lam[free]))) / c
+        worst = max(worst, float(np.max(exc[free])))
+    if which == "sneddon64":
+        assert worst > 0.1 * tau / c       # the slack is real, not vacuous

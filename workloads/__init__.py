@@ -22,7 +22,7 @@ import numpy as np
 __all__ = [
     "uniform_axis", "graded_axis", "crack_phi", "Workload", "config",
     "CONFIG_NAMES", "batched_instances", "served_requests", "random_state",
-    "scaled_workload",
+    "scaled_workload", "cyclic_loading", "CYCLIC_PRESSURES",
 ]
 
 
@@ -189,6 +189,29 @@ def scaled_workload(w: Workload, n_cells: int, graded: Optional[bool] = None) ->
         ax = uniform_axis(n_cells, -half, half)
         eps = w.eps * n0 / n_cells
     return replace(w, name=f"{w.name}@{n_cells}", coords=[ax.copy() for _ in range(w.dim)], eps=eps)
+
+
+# load, unload, reload: the first three steps approach the critical pressure, the
+# next two unload, the last two reload past the earlier maximum
+CYCLIC_PRESSURES = (4e-3, 8e-3, 1.1e-2, 6e-3, 2e-3, 8e-3, 1.2e-2)
+
+
+def cyclic_loading(n_cells: int = 64) -> Workload:
+    """A crack that grows under a load / unload / reload pressure cycle.
+
+    Geometry of the 2d Sneddon test (uniform on [-2,2]^2, l0 = 0.25, eps = 2h,
+    E = 1, nu = 0.2, kappa = 1e-10) with G_c lowered to 1e-4, so that the
+    sharp-crack critical pressure sqrt(E G_c / ((1 - nu^2) pi l0)) ~ 1.15e-2
+    lies inside the schedule CYCLIC_PRESSURES.  While the pressure rises the
+    phase field drops ahead of both tips and the crack lengthens; while it
+    falls the phase field would heal, and the irreversibility constraint
+    phi <= phi_old holds it on the whole damaged zone (Formulation 1).
+    Pressure control past the critical pressure makes the growth unstable, so
+    the schedule stays near it.
+    """
+    ax = uniform_axis(n_cells, -2.0, 2.0)
+    return Workload(f"cyclic2d_{n_cells}", 2, [ax, ax.copy()], Gc=1e-4, eps=2.0 * 4.0 / n_cells,
+                    pressures=list(CYCLIC_PRESSURES))
 
 
 def batched_instances(count: int = 256, seed: int = 1806) -> List[Workload]:
