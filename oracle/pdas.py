@@ -126,8 +126,15 @@ def _update(u, phi, phi_old, du, dphi, active, omega):
     return u_new, phi_new
 
 
-def _solve_reduced(J, rhs, free, nu_dofs, full_jacobian):
-    """Exact solve of the reduced system on the free DoFs (step 5)."""
+def _solve_reduced(J, rhs, free, nu_dofs, full_jacobian, cache=None):
+    """Exact solve of the reduced system on the free DoFs (step 5).
+
+    M_uu = (g(phi~) sigma(chi_j), e(chi_i)) depends on phi~ alone, which is
+    fixed within a loading step, and its free rows (all but the Dirichlet
+    ones) never change; ``cache`` (one dict per loading step) keeps its sparse
+    LU factors, so every Newton iteration solves with the same factors a fresh
+    factorization would produce.
+    """
     x = np.zeros_like(rhs)
     if full_jacobian:
         idx = np.flatnonzero(free)
@@ -140,7 +147,11 @@ def _solve_reduced(J, rhs, free, nu_dofs, full_jacobian):
     Jpu = J[nu_dofs:, :nu_dofs]
     Jpp = J[nu_dofs:, nu_dofs:]
     if fu.size:
-        x[fu] = spla.spsolve(Juu[fu][:, fu].tocsc(), rhs[fu])
+        if cache is None:
+            cache = {}
+        if "uu" not in cache:
+            cache["uu"] = spla.splu(Juu[fu][:, fu].tocsc())
+        x[fu] = cache["uu"].solve(rhs[fu])
     rp = rhs[nu_dofs:] - Jpu @ x[:nu_dofs]
     if fp.size:
         x[nu_dofs + fp] = spla.spsolve(Jpp[fp][:, fp].tocsc(), rp[fp])
@@ -178,6 +189,7 @@ def loading_step(st: State, p: float, opts: Options = Options()) -> StepReport:
     toggles = np.zeros(n, dtype=np.int64)
     locked = np.zeros(n, dtype=bool)
     last_small = False
+    lu_cache = {}          # factors of the free M_uu rows, valid for this loading step
     for k in range(opts.max_newton + 1):
         r_u, r_phi = gradient(mesh, prm, u, phi, phit)
         F = -np.concatenate([r_u.ravel(), r_phi])
@@ -216,7 +228,7 @@ def loading_step(st: State, p: float, opts: Options = Options()) -> StepReport:
         dUA = np.zeros(nu_dofs + n)
         dUA[nu_dofs:][A] = phi_old[A] - phi[A]
         rhs = F - J @ dUA
-        dU = dUA + _solve_reduced(J, rhs, free, nu_dofs, opts.full_jacobian)
+        dU = dUA + _solve_reduced(J, rhs, free, nu_dofs, opts.full_jacobian, lu_cache)
         du, dphi = dU[:nu_dofs].reshape(n, d), dU[nu_dofs:]
         u1, phi1 = _update(u, phi, phi_old, du, dphi, A, 1.0)
         small = (np.max(np.abs(du), initial=0.0) <= opts.tol_step * np.max(np.abs(u1), initial=0.0)
