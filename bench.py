@@ -1,25 +1,38 @@
 #!/usr/bin/env python
 """Throughput of the GB300 pressurized phase-field fracture solver.
 
-One benchmark step = the whole hot path on the 2d graded Sneddon workload
-(1024 x 1024 Q1 cells, graded from h_min = 2e-4 on [-10, 10]^2, 3,151,875
-DoFs): five loading steps with the pressure ramped to 1e-3, each solved to
-convergence by the Newton / active-set method with FGMRES + AMG on the device,
+One benchmark step = the whole hot path on one problem, solved to
+convergence by the Newton / active-set method with FGMRES + block AMG on the
+device (mixed precision: FP32 V-cycles inside the FP64 outer iteration),
 followed by TCV and the COD at 64 points.
 
+Default line (the largest single-GPU configuration): the 3d penny-shaped
+Sneddon crack, [-2,2]^3 graded 128^3 Q1 hexes from h_min = 4e-3 (8,586,756
+DoFs), one loading step at p = 1e-3.  The same run measures the 2d graded
+Sneddon ramp (1024^2 cells graded from h_min = 2e-4 on [-10,10]^2, 3,151,875
+DoFs, five loading steps to p = 1e-3) the same way and reports it under
+"workloads".  --workload penny3d / graded2d prints one of them alone.
+
 value  = DoF/s = (loading steps solved x DoFs) / device time, inputs resident
-         in HBM (the state is reset from device buffers each step).
+         in HBM (the state is reset from device buffers each step); the timed
+         region carries no instrumentation.
 e2e    = the same through the C ABI with host buffers: the initial state is
          copied host -> device and the solution device -> host every step.
+fp64_path = the plain FP64 GPU path (FP64 V-cycles too) on the same steps.
+roofline  = the dominant kernel, timed with CUDA event pairs in a separate
+         instrumented step after the timed region; the coarse AMG levels (one
+         CUDA graph replay per V-cycle) are reported beside it.
 cpu_baseline / --impl reference = the CPU oracle (oracle/) on a bounded sample
          of the same workload recipe, on the host cores.
 
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-       [--cells C]   (same recipe at C x C cells: small cases for profiler captures)
+       [--workload default|penny3d|graded2d] [--cells C]   (C: the same recipe at
+              C cells per axis, small cases for profiler captures)
        [--workload batched [--instances 256] [--workers 16]]
               256 independent 2d instances (32^2..512^2) through the batch executor
-       [--workload served [--requests 12] [--load 1.0] [--budget-gb 150] [--workers 16]]
-              a Poisson stream of mixed 2d / 3d 10-step requests through the server
+       [--workload served [--requests 12] [--loads 0.5,1,2,4] [--budget-gb 150]]
+              a Poisson stream of mixed 2d / 3d 10-step requests through the server,
+              at each arrival rate (multiples of the FP64 one-at-a-time service rate)
 Multi-GPU runs (torchrun) are independent replicas: each rank solves its own
 copy of the workload; value sums the ranks' work over the slowest rank's time.
 """
@@ -29,6 +42,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -40,9 +54,12 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Newton-Krylov solves/s & DoF/s at <=1e-8 rel err; p50/p99 latency; HBM GB/s"
 UNIT = "DoF/s"
-WORKLOAD_INDEX = 1          # the 2d graded 1024^2 Sneddon configuration
-SAMPLE_CELLS = 128          # oracle sample: same recipe at 128^2 cells
-SAMPLE_STEPS = 2            # loading steps of the sample timed by the CPU baseline
+# workload recipes: index of the standard configuration, CPU-oracle sample size
+# (cells per axis) and loading steps of the sample
+WORKLOADS = {
+    "penny3d": {"index": 2, "sample_cells": 16, "sample_steps": 1},
+    "graded2d": {"index": 1, "sample_cells": 128, "sample_steps": 2},
+}
 
 
 def _peaks():
@@ -53,6 +70,29 @@ def _peaks():
         return float(d["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def host_cpu():
+    """Model name and logical core count of the host."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith("model name"):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except Exception:
+            pass
+    return {"model": model or platform.machine(), "arch": platform.machine(), "nproc": os.cpu_count()}
 
 
 # ------------------------------------------------------------ CPU oracle ----
@@ -77,39 +117,51 @@ print(json.dumps({{"times": times, "n_dofs": w.n_dofs, "name": w.name}}))
 """
 
 
-def run_oracle(nsteps: int, cells: int = SAMPLE_CELLS):
+def run_oracle(kind: str, nsteps: int):
+    spec = WORKLOADS[kind]
     env = dict(os.environ)
     for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
         env[k] = "1"
-    code = ORACLE_SNIPPET.format(root=ROOT, idx=WORKLOAD_INDEX, cells=cells, nsteps=nsteps)
+    code = ORACLE_SNIPPET.format(root=ROOT, idx=spec["index"], cells=spec["sample_cells"],
+                                 nsteps=nsteps)
     out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env,
                          check=True)
     return json.loads(out.stdout.strip().splitlines()[-1])
 
 
-def cpu_baseline():
-    r = run_oracle(SAMPLE_STEPS)
+def cpu_baseline(kind: str):
+    spec = WORKLOADS[kind]
+    r = run_oracle(kind, spec["sample_steps"])
     total = sum(r["times"])
-    return {"value": SAMPLE_STEPS * r["n_dofs"] / total, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{SAMPLE_STEPS} loading steps (p = 2e-4, 4e-4) of the same recipe at "
-                      f"{SAMPLE_CELLS}^2 cells ({r['n_dofs']} DoFs), {total:.1f} s single-threaded"}
+    c = spec["sample_cells"]
+    cells = f"{c}^3" if kind == "penny3d" else f"{c}^2"
+    return {"value": spec["sample_steps"] * r["n_dofs"] / total, "unit": UNIT, "cores": 1,
+            "kind": "oracle", "host": host_cpu(),
+            "sample": f"{spec['sample_steps']} loading step(s) of the same recipe at {cells} cells "
+                      f"({r['n_dofs']} DoFs), {total:.1f} s single-threaded (FP64 numpy/scipy, "
+                      f"exact sparse LU solves)"}
 
 
 def reference_arm(args, rank, world):
     if rank != 0:
         return 0
-    r = run_oracle(args.warmup + args.steps)
+    kind = "penny3d" if args.workload == "default" else args.workload
+    spec = WORKLOADS[kind]
+    r = run_oracle(kind, args.warmup + args.steps)
     times = r["times"][args.warmup:]
     total = sum(times)
     value = len(times) * r["n_dofs"] / total
+    c = spec["sample_cells"]
+    cells = f"{c}^3" if kind == "penny3d" else f"{c}^2"
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": r["name"], "loading_steps_per_step": 1,
                                             "n_dofs": r["n_dofs"]},
             "cpu_baseline": {"value": value, "unit": UNIT, "kind": "oracle", "cores": 1,
-                             "sample": f"one loading step per bench step at {SAMPLE_CELLS}^2 cells "
-                                       f"({r['n_dofs']} DoFs) of the graded 1024^2 recipe"},
+                             "host": host_cpu(),
+                             "sample": f"one loading step per bench step at {cells} cells "
+                                       f"({r['n_dofs']} DoFs) of the {kind} recipe"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -188,105 +240,103 @@ def _traffic_for(kernel: str):
         return None
 
 
-def gpu_arm(args, rank, world, local_rank):
+def _cod_points(w, fn, np):
+    xs = fn.cod_points(w.l0, 64)
+    if w.dim == 2:
+        return xs
+    return np.stack([xs, np.zeros_like(xs)], axis=1).ravel()   # lines along z through y = 0
+
+
+COARSE = ("coarse_levels_graph_u", "coarse_levels_graph_phi")
+
+
+def measure_problem(kind, args, rank, world, local_rank, dist, with_fp64=True):
+    """Time one workload (mixed precision) as the module docstring describes and
+    return the fields of its bench line."""
     import numpy as np
     import torch
     import paper_1806_09924_gb300 as pff
     import workloads as W
-    from oracle import functionals as fn
+    from oracle import functionals as fn   # COD sample points only
 
-    torch.cuda.set_device(local_rank)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-
-    w = W.config(WORKLOAD_INDEX)
+    w = W.config(WORKLOADS[kind]["index"])
     if args.cells:
         w = W.scaled_workload(w, args.cells)
-    prec = pff.PFF_PREC_MIXED if args.precision == "mixed" else pff.PFF_PREC_FP64
-    opts = pff.options(precision=prec)
-    stream = torch.cuda.Stream()
+    dev = torch.device("cuda", local_rank)
+    opts = pff.options(precision=pff.PFF_PREC_MIXED)
+    # the profiled step runs the two preconditioner blocks one after the other,
+    # so every kernel is timed alone (isolated efficiencies)
+    opts_isolated = pff.options(precision=pff.PFF_PREC_MIXED, precond_overlap=0)
+    stream = torch.cuda.Stream(device=dev)
     P = pff.problem_from_workload(w)
     P.set_stream(stream)
     n, d = P.n_nodes, w.dim
     phi0_h = w.phi0()
     u0_h = np.zeros((n, d))
-    dev = torch.device("cuda", local_rank)
     u0 = torch.zeros(n * d, dtype=torch.float64, device=dev)
     phi0 = torch.tensor(phi0_h, device=dev)
-    pts = fn.cod_points(w.l0, 64)
+    pts = _cod_points(w, fn, np)
     pressures = list(w.pressures)
 
-    # the profiled warm-up step runs the two preconditioner blocks one after the
-    # other, so every kernel is timed alone (isolated efficiencies); the timed
-    # steps run them concurrently, as users do
-    opts_isolated = pff.options(precision=prec, precond_overlap=0)
-
-    def step_device(o=None):
-        P.set_state_dev(u0, phi0, phi0, phi0, 0)
-        reps = P.solve_loading_steps(pressures, o if o is not None else opts)
-        tcv, cod = P.eval_tcv_cod(pts)
+    def step_device(Q, o):
+        Q.set_state_dev(u0, phi0, phi0, phi0, 0)
+        reps = Q.solve_loading_steps(pressures, o)
+        tcv, cod = Q.eval_tcv_cod(pts)
         return reps, tcv, cod
 
     def step_e2e():
         P.set_state(u0_h, phi0_h, phi0_h, phi0_h, 0)
         reps = P.solve_loading_steps(pressures, opts)
         tcv, cod = P.eval_tcv_cod(pts)
-        u, phi, act = P.get_solution()
+        P.get_solution()
         return reps, tcv, cod
 
-    with torch.cuda.stream(stream):
-        # warm-up; the last warm-up step is fully profiled to find the dominant kernel
-        warm_prof = {}
-        for k in range(args.warmup):
-            last = k == args.warmup - 1
-            if last:
-                pff.profile_select(None)
-                pff.profile_enable(True)
-            reps, tcv, cod = step_device(opts_isolated if last else None)
-        if args.warmup > 0:
-            warm_prof = pff.profile_report()
-            pff.profile_enable(False)
-        # the dominant kernel: largest total time among entries that move data
-        # (graph replays and set-up scopes carry no byte count)
-        kern = {k: v for k, v in warm_prof.items() if v["bytes"] > 0}
-        top_name = max(kern.items(), key=lambda kv: kv[1]["ms"])[0] if kern else None
-        # timed region: resident inputs
+    def timed(Q, o, steps):
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
-        gpu_id = str(local_rank)
-        try:
-            gpu_id = "GPU-" + str(torch.cuda.get_device_properties(local_rank).uuid)
-        except Exception:
-            pass
-        sampler = ClockSampler(gpu_id)
-        sampler.start()
-        # timed region: only the dominant kernel is timed (event pairs on its stream)
-        pff.profile_select(top_name)
-        pff.profile_enable(True)
-        launches0 = pff.launch_count()
         ev0 = torch.cuda.Event(enable_timing=True)
         ev1 = torch.cuda.Event(enable_timing=True)
         ev0.record(stream)
-        all_reps = []
-        for _ in range(args.steps):
-            reps, tcv, cod = step_device()
-            all_reps.append(reps)
+        reps = []
+        for _ in range(steps):
+            reps.append(step_device(Q, o))
         ev1.record(stream)
         torch.cuda.synchronize()
-        launches = pff.launch_count() - launches0
-        prof = pff.profile_report()
-        pff.profile_enable(False)
-        pff.profile_select(None)
-        clocks = sampler.stop()
         ms = ev0.elapsed_time(ev1)
         if dist:
             t = torch.tensor([ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             ms = float(t.item())
-            dist.barrier()
+        return ms, reps
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step_device(P, opts)
+        # timed region: resident inputs, no instrumentation
+        sampler = ClockSampler(_gpu_id(torch, local_rank))
+        sampler.start()
+        launches0 = pff.launch_count()
+        ms, runs = timed(P, opts, args.steps)
+        launches = pff.launch_count() - launches0
+        clocks = sampler.stop()
+        reps, tcv, cod = runs[-1]
+        # instrumented step 1: blocks serialised, every kernel timed (isolated)
+        pff.profile_select(None)
+        pff.profile_enable(True)
+        step_device(P, opts_isolated)
+        iso = pff.profile_report()
+        pff.profile_enable(False)
+        kern = {k: v for k, v in iso.items() if v["bytes"] > 0 and k not in COARSE}
+        top_name = max(kern.items(), key=lambda kv: kv[1]["ms"])[0] if kern else None
+        # instrumented step 2: as timed (blocks concurrent), the roofline kernel and
+        # the coarse-level graph replays timed with event pairs on their streams
+        pff.profile_select(",".join([top_name, *COARSE]) if top_name else ",".join(COARSE))
+        pff.profile_enable(True)
+        step_device(P, opts)
+        live = pff.profile_report()
+        pff.profile_enable(False)
+        pff.profile_select(None)
         # e2e through host buffers
         torch.cuda.synchronize()
         t0 = time.perf_counter()
@@ -302,82 +352,135 @@ def gpu_arm(args, rank, world, local_rank):
             t = torch.tensor([e2e_ms], device=dev)
             dist.all_reduce(t, op=dist.ReduceOp.MAX)
             e2e_ms = float(t.item())
-        # accuracy of this precision against the FP64 GPU path (untimed)
-        err = None
-        if prec == pff.PFF_PREC_MIXED and rank == 0:
-            u_m, phi_m, _ = P.get_solution()
+        u_m, phi_m, _ = P.get_solution()
+        P.close()
+        # the plain FP64 GPU path on the same steps (FP64 V-cycles and Gram-Schmidt)
+        fp64 = None
+        if with_fp64:
             Q = pff.problem_from_workload(w)
-            Q.solve_loading_steps(pressures, pff.options(precision=pff.PFF_PREC_FP64))
+            Q.set_stream(stream)
+            o64 = pff.options(precision=pff.PFF_PREC_FP64)
+            step_device(Q, o64)
+            ms64, runs64 = timed(Q, o64, args.steps)
             u_f, phi_f, _ = Q.get_solution()
             Q.close()
-            err = {"u": float(np.linalg.norm(u_m - u_f) / np.linalg.norm(u_f)),
-                   "phi": float(np.linalg.norm(phi_m - phi_f) / np.linalg.norm(phi_f))}
-    P.close()
-    if rank != 0:
-        if dist:
-            dist.destroy_process_group()
-        return 0
+            solves = args.steps * len(pressures) * world
+            fp64 = {"value": solves * w.n_dofs / (ms64 / 1e3), "unit": UNIT,
+                    "solves_per_s": solves / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
+                    "newton_its": [r["newton_its"] for r in runs64[-1][0]],
+                    "krylov_its": [r["krylov_its"] for r in runs64[-1][0]],
+                    "mixed_speedup": ms64 / ms,
+                    "rel_err_mixed_vs_fp64": {
+                        "u": float(np.linalg.norm(u_m - u_f) / np.linalg.norm(u_f)),
+                        "phi": float(np.linalg.norm(phi_m - phi_f) / np.linalg.norm(phi_f)),
+                        "u_max_norm": float(np.max(np.abs(u_m - u_f)) / np.max(np.abs(u_f))),
+                        "phi_max_norm": float(np.max(np.abs(phi_m - phi_f)) / np.max(np.abs(phi_f)))}}
 
     solves = args.steps * len(pressures)
     dofs = solves * w.n_dofs * world
     value = dofs / (ms / 1e3)
     h2d = n * (d + 3) * 8
-    d2h = n * (d * 8 + 8 + 1) + 8 * (len(pts) + 1)
-    # dominant instrumented kernel and its roofline
+    d2h = n * (d * 8 + 8 + 1) + 8 * (len(pts) // (d - 1) + 1)
     peak, peak_kind = _peaks()
-    top = (top_name, prof[top_name]) if top_name in prof else None
+
+    def rate(st):
+        if not st or st["ms"] <= 0 or st["bytes"] <= 0:
+            return None
+        per = st["bytes"] / max(st["count"], 1)
+        avg = st["ms"] / max(st["count"], 1)
+        ach = per / (avg / 1e3) / 1e9
+        return {"achieved": ach, "frac": ach / peak, "launches": st["count"],
+                "avg_launch_us": 1e3 * avg, "algorithmic_bytes_per_launch": per}
+
     roof = None
-    if top:
-        name, st = top
-        per_launch_bytes = st["bytes"] / max(st["count"], 1)
-        avg_ms = st["ms"] / max(st["count"], 1)
-        achieved = per_launch_bytes / (avg_ms / 1e3) / 1e9
-        roof = {"bound": "hbm", "kernel": name, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": _traffic_for(name),
-                "peak_source": f"{peak_kind} hbm_gbs", "launches": st["count"],
-                "avg_launch_us": 1e3 * avg_ms, "algorithmic_bytes_per_launch": per_launch_bytes,
-                "share_of_step_time": st["ms"] / ms,
-                "timing": "CUDA event pair around every launch of this kernel in the timed region "
-                          "(the two preconditioner blocks run concurrently there, so this kernel "
-                          "shares HBM with the other block's V-cycle)"}
-        iso = warm_prof.get(name)
-        if iso and iso["ms"] > 0:
-            a_iso = iso["bytes"] / (iso["ms"] / 1e3) / 1e9
-            roof["isolated"] = {"achieved": a_iso, "frac": a_iso / peak, "launches": iso["count"],
-                                "timing": "last warm-up step, blocks one after the other, CUDA events"}
-    last = all_reps[-1]
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64+f32" if prec == pff.PFF_PREC_MIXED else "f64", "data": "synthetic",
+    if top_name and top_name in live:
+        r_live = rate(live[top_name])
+        roof = {"bound": "hbm", "kernel": top_name, "achieved": r_live["achieved"], "peak": peak,
+                "unit": "GB/s", "frac": r_live["frac"], "traffic": _traffic_for(top_name),
+                "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
+                "launches": r_live["launches"], "avg_launch_us": r_live["avg_launch_us"],
+                "algorithmic_bytes_per_launch": r_live["algorithmic_bytes_per_launch"],
+                "share_of_step_time": live[top_name]["ms"] / (ms / args.steps),
+                "timing": "CUDA event pair around every launch of this kernel during one "
+                          "instrumented step after the timed region, blocks concurrent as in the "
+                          "timed steps (the kernel shares HBM with the other block's V-cycle)"}
+        r_iso = rate(iso.get(top_name))
+        if r_iso:
+            roof["isolated"] = dict(r_iso, timing="instrumented step with the two preconditioner "
+                                                  "blocks one after the other, CUDA events")
+        coarse = {}
+        for name in COARSE:
+            r = rate(live.get(name))
+            ri = rate(iso.get(name))
+            if r:
+                coarse[name] = dict(r, isolated=ri,
+                                    note="one CUDA graph replay = every kernel of AMG levels >= 1 "
+                                         "of one V-cycle; bytes = their summed algorithmic bytes")
+        roof["coarse_levels"] = coarse
+    last = reps
+    out = {
+        "value": value, "ms_per_step": ms / args.steps,
+        "dtype": "f64+f32",
         "config": {"workload": w.name, "n_cells": "x".join(str(c) for c in w.n_cells),
-                   "n_dofs": w.n_dofs,
-                   "loading_steps_per_step": len(pressures), "precision": args.precision,
-                   "grading": "geometric from h_min=2e-4, ratio solved to fill [-10,10]",
-                   "l2": "working set (state, stencils, AMG, Krylov basis) is several GB, > L2",
+                   "n_dofs": w.n_dofs, "loading_steps_per_step": len(pressures),
+                   "precision": "mixed: FP32 AMG V-cycles (and FP32 views of the Krylov basis for "
+                                "the Gram-Schmidt coefficients) inside FP64 FGMRES / Newton; "
+                                "residuals, updates, active sets and TCV/COD in FP64",
+                   "grading": ("geometric from h_min=4e-3, ratio solved to fill [-2,2]" if kind == "penny3d"
+                               else "geometric from h_min=2e-4, ratio solved to fill [-10,10]"),
+                   "l2": "no flush: the working set (state, stencils, AMG, Krylov basis) is "
+                         "several GB, > L2",
                    "parallelism": f"replicas x{world}"},
         "solves_per_s": solves * world / (ms / 1e3),
         "newton_its": [r["newton_its"] for r in last],
         "krylov_its": [r["krylov_its"] for r in last],
         "krylov_its_max": [r["krylov_its_max"] for r in last],
+        "locked": [r["locked"] for r in last],
         "tcv": tcv, "cod_center": float(cod[len(cod) // 2]),
-        "rel_err_vs_fp64_path": err,
+        "fp64_path": fp64,
         "gpu_launches": int(launches),
         "e2e": {"value": dofs / (e2e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
         "roofline": roof,
-        "kernels_last_warmup_step": {
+        "kernels_isolated_step": {
             k: {"count": v["count"], "ms": round(v["ms"], 3),
                 "GB/s": (v["bytes"] / (v["ms"] / 1e3) / 1e9) if v["ms"] > 0 and v["bytes"] > 0 else None}
-            for k, v in sorted(warm_prof.items(), key=lambda kv: -kv[1]["ms"])[:14]},
+            for k, v in sorted(iso.items(), key=lambda kv: -kv[1]["ms"])[:16]},
         "clocks": clocks,
     }
+    return out
+
+
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    kinds = ["penny3d", "graded2d"] if args.workload == "default" else [args.workload]
+    results = {k: measure_problem(k, args, rank, world, local_rank, dist,
+                                  with_fp64=not args.no_fp64) for k in kinds}
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    main_kind = kinds[0]
+    r = results[main_kind]
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": r["dtype"],
+            "data": "synthetic"}
+    line.update({k: v for k, v in r.items() if k not in line})
     if world == 1 and not args.no_cpu_baseline:
-        try:
-            line["cpu_baseline"] = cpu_baseline()
-        except Exception as e:   # the CPU leg must not hide the GPU number
-            line["cpu_baseline"] = {"error": str(e)[:200]}
+        for k in kinds:
+            try:
+                results[k]["cpu_baseline"] = cpu_baseline(k)
+            except Exception as e:   # the CPU leg must not hide the GPU number
+                results[k]["cpu_baseline"] = {"error": str(e)[:200]}
+        line["cpu_baseline"] = results[main_kind]["cpu_baseline"]
+    if len(kinds) > 1:
+        line["workloads"] = {results[k]["config"]["workload"]: results[k] for k in kinds[1:]}
     print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -513,52 +616,64 @@ def served_arm(args, rank, world, local_rank):
     # the served form with every request queued at once (throughput bound)
     mixed_s, _ = closed_loop(pff.options(precision=pff.PFF_PREC_MIXED), args.workers)
     mu = len(reqs) / base_s
-    lam = args.load * mu
+    loads = [float(x) for x in args.loads.split(",") if x.strip()]
+    steps = sum(len(w.pressures) for w, _ in reqs)
+    dofs = sum(w.n_dofs * len(w.pressures) for w, _ in reqs)
+
+    def open_loop(load):
+        """Requests arrive at Poisson times (unit-rate gaps / lambda) while others run."""
+        lam = load * mu
+        S = pff.Server(budget, args.workers, pff.options(precision=pff.PFF_PREC_MIXED))
+        arrivals = np.cumsum([g for _, g in reqs]) / lam
+        t0 = time.perf_counter()
+        ids = []
+        for (w, _), ta in zip(reqs, arrivals):
+            delay = ta - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(S.submit(w, cod_x=cod_x))
+        res = [S.wait(i) for i in ids]
+        makespan = time.perf_counter() - t0
+        stats = S.stats()
+        S.close()
+        if any(r["status"] != 0 for r in res):
+            raise RuntimeError("a request failed")
+        lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
+        return {"load_vs_fp64_service_rate": load, "rate_per_s": lam, "makespan_s": makespan,
+                "solves_per_s": steps / makespan, "dof_per_s": dofs / makespan,
+                "latency_s": {"p50": float(np.percentile(lat, 50)),
+                              "p99": float(np.percentile(lat, 99)), "mean": float(lat.mean())},
+                "server": stats}
+
     sampler = ClockSampler(_gpu_id(torch, local_rank))
     sampler.start()
     launches0 = pff.launch_count()
-    S = pff.Server(budget, args.workers, pff.options(precision=pff.PFF_PREC_MIXED))
-    arrivals = np.cumsum([g for _, g in reqs]) / lam
-    t0 = time.perf_counter()
-    ids = []
-    for (w, _), ta in zip(reqs, arrivals):
-        delay = ta - (time.perf_counter() - t0)
-        if delay > 0:
-            time.sleep(delay)
-        ids.append(S.submit(w, cod_x=cod_x))
-    res = [S.wait(i) for i in ids]
-    makespan = time.perf_counter() - t0
-    stats = S.stats()
-    S.close()
+    sweep = [open_loop(x) for x in loads]
     launches = pff.launch_count() - launches0
     clocks = sampler.stop()
-    if any(r["status"] != 0 for r in res):
-        raise RuntimeError("a request failed")
-    lat = np.array([r["t_finish"] - r["t_submit"] for r in res])
-    steps = sum(len(w.pressures) for w, _ in reqs)
-    dofs = sum(w.n_dofs * len(w.pressures) for w, _ in reqs)
+    head = sweep[min(range(len(sweep)), key=lambda i: abs(loads[i] - 1.0))]
     base_lat = np.array([r["t_finish"] - r["t_submit"] for r in base])
     line = {
-        "metric": METRIC, "value": dofs / makespan, "unit": UNIT, "n_gpus": 1, "steps": 1,
-        "warmup": 0, "ms_per_step": 1e3 * makespan, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "metric": METRIC, "value": head["dof_per_s"], "unit": UNIT, "n_gpus": 1, "steps": 1,
+        "warmup": 0, "ms_per_step": 1e3 * head["makespan_s"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
         "config": {"workload": "served_mixed_2d3d", "requests": len(reqs),
                    "mix": f"{sum(1 for w, _ in reqs if w.dim == 2)} 2d (64^2..1024^2 graded), "
                           f"{sum(1 for w, _ in reqs if w.dim == 3)} 3d (32^3..128^3 graded), seed 1807",
                    "loading_steps_per_request": 10, "arrivals": "Poisson",
-                   "rate_per_s": lam, "load_vs_fp64_service_rate": args.load,
+                   "loads_vs_fp64_service_rate": loads, "headline_load": head["load_vs_fp64_service_rate"],
                    "budget_gb": args.budget_gb, "workers": args.workers},
-        "solves_per_s": steps / makespan,
-        "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
-                      "mean": float(lat.mean())},
+        "solves_per_s": head["solves_per_s"],
+        "latency_s": head["latency_s"],
+        "sweep": sweep,
         "closed_loop_mixed": {"value": dofs / mixed_s, "unit": UNIT, "solves_per_s": steps / mixed_s,
                               "note": "all requests queued at t = 0, same server"},
         "fp64_one_at_a_time": {"value": dofs / base_s, "unit": UNIT, "solves_per_s": steps / base_s,
                                "service_rate_per_s": mu,
                                "latency_s_closed_loop": {"p50": float(np.percentile(base_lat, 50)),
                                                          "p99": float(np.percentile(base_lat, 99))}},
-        "server": stats, "gpu_launches": int(launches), "clocks": clocks,
-        "timing": "host wall clock from the first arrival to the last completion",
+        "gpu_launches": int(launches), "clocks": clocks,
+        "timing": "host wall clock from the first arrival to the last completion, per load",
     }
     print(json.dumps(line), flush=True)
     return 0
@@ -570,28 +685,30 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 GPU path")
     ap.add_argument("--cells", type=int, default=0,
                     help="run the same recipe at this many cells per axis (profiling captures)")
-    ap.add_argument("--workload", default="graded2d", choices=["graded2d", "batched", "served"],
-                    help="graded2d: the 1024^2 graded ramp (default line); batched: 256 independent "
+    ap.add_argument("--workload", default="default",
+                    choices=["default", "penny3d", "graded2d", "batched", "served"],
+                    help="default: the 3d penny 128^3 line with the graded 2d 1024^2 ramp measured "
+                         "beside it; penny3d / graded2d: one of them; batched: 256 independent "
                          "instances; served: a Poisson request stream")
     ap.add_argument("--instances", type=int, default=256)
     ap.add_argument("--workers", type=int, default=16)
     ap.add_argument("--requests", type=int, default=12)
-    ap.add_argument("--load", type=float, default=1.0,
-                    help="served: arrival rate as a multiple of the FP64 one-at-a-time service rate")
+    ap.add_argument("--loads", default="0.5,1,2,4",
+                    help="served: arrival rates as multiples of the FP64 one-at-a-time service rate")
     ap.add_argument("--budget-gb", type=float, default=150.0)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
-        if args.workload != "graded2d":
+        if args.workload not in ("default", "penny3d", "graded2d"):
             if rank == 0:
                 print(json.dumps({"impl": "reference", "unavailable":
-                                  "the reference arm times the oracle on the graded 2d workload only"}))
+                                  "the reference arm times the oracle on single-problem workloads only"}))
             return 0
         return reference_arm(args, rank, world)
     if args.workload == "batched":

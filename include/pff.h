@@ -390,9 +390,12 @@ void pff_server_destroy(pff_server* srv);
  * moved once).  Adds a few microseconds per launch. */
 int pff_profile_enable(int on);
 
-/* Restrict the timing to launches of one kernel name (as reported by
- * pff_profile_report); NULL times every instrumented launch again.  Timing a
- * single kernel keeps the event overhead off the rest of the run. */
+/* Restrict the timing to launches of the named kernels (as reported by
+ * pff_profile_report; several names separated by commas); NULL times every
+ * instrumented launch again.  Timing a few kernels keeps the event overhead
+ * off the rest of the run.  The replays of a captured coarse-level graph
+ * ("coarse_levels_graph_u" / "_phi") are credited with the summed algorithmic
+ * bytes of the kernels captured in them. */
 int pff_profile_select(const char* name);
 
 /* Synchronize the device and write per-kernel totals as a JSON object

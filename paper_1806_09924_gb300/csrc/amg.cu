@@ -945,6 +945,7 @@ void coarse_cycle(Amg& amg, T* cb, T* cx, cudaStream_t s) {
       } catch (...) {
         ok = false;
       }
+      amg.graph_bytes = captured_bytes();
       set_capturing(false);
       cudaGraph_t g = nullptr;
       if (cudaStreamEndCapture(amg.cap_stream, &g) != cudaSuccess) ok = false;
@@ -970,8 +971,8 @@ void coarse_cycle(Amg& amg, T* cb, T* cx, cudaStream_t s) {
     if (!ok) amg.use_graph = false;
   }
   if (amg.graph) {
-    ProfScope ps(amg.lev[0].A.br > 1 ? "coarse_levels_graph_u" : "coarse_levels_graph_phi", 0.0, s,
-                 amg.graph_kernels);
+    ProfScope ps(amg.lev[0].A.br > 1 ? "coarse_levels_graph_u" : "coarse_levels_graph_phi",
+                 amg.graph_bytes, s, amg.graph_kernels);
     PFF_CUDA(cudaGraphLaunch(amg.graph, s));
   } else {
     vcycle_level<T>(amg, 1, cb, cx, s);

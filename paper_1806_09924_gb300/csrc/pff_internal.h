@@ -70,8 +70,10 @@ void check_cuda(cudaError_t e, const char* what);
 // algorithmic bytes (each input / output array moved once).
 void count_launch(int k = 1);
 // while a stream is being captured into a graph, launches are neither counted
-// nor timed (the graph's replays are)
+// nor timed (the graph's replays are); their algorithmic bytes are summed, and
+// captured_bytes() returns the sum since capture started (the bytes of one replay)
 void set_capturing(bool on);
+double captured_bytes();
 // diagnostics on stderr when the environment variable PFF_VERBOSE is set
 bool verbose();
 class ProfScope {
@@ -192,6 +194,7 @@ struct Amg {
   bool inline_levels = false; // run levels 1.. as ordinary launches (inside an outer capture)
   cudaGraphExec_t graph = nullptr;
   int graph_kernels = 0;
+  double graph_bytes = 0.0;   // algorithmic bytes of one replay (sum over its kernels)
   cudaStream_t cap_stream = nullptr;
   void release();
 };

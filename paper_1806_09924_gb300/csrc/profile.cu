@@ -39,7 +39,7 @@ struct Acc {
 struct Profiler {
   std::mutex mu;
   bool on = false;
-  std::string only;   // when set, only launches of this name are timed
+  std::vector<std::string> only;   // when not empty, only launches of these names are timed
   std::vector<Pending> pending;
   std::vector<cudaEvent_t> pool;
   std::map<std::string, Acc> acc;
@@ -92,9 +92,15 @@ bool verbose() {
 
 namespace {
 thread_local bool t_capturing = false;
+thread_local double t_capture_bytes = 0.0;
 }
 
-void set_capturing(bool on) { t_capturing = on; }
+void set_capturing(bool on) {
+  if (on && !t_capturing) t_capture_bytes = 0.0;
+  t_capturing = on;
+}
+
+double captured_bytes() { return t_capture_bytes; }
 
 void count_launch(int k) {
   if (!t_capturing) g_launches.fetch_add(k, std::memory_order_relaxed);
@@ -103,9 +109,13 @@ void count_launch(int k) {
 ProfScope::ProfScope(const char* name, double bytes, cudaStream_t s, int kernels)
     : name_(name), bytes_(bytes), s_(s), a_(nullptr) {
   count_launch(kernels);
+  if (t_capturing) {
+    t_capture_bytes += bytes;
+    return;
+  }
   Profiler& P = prof();
-  if (!P.on || t_capturing) return;
-  if (!P.only.empty() && P.only != name_) return;
+  if (!P.on) return;
+  if (!P.only.empty() && std::find(P.only.begin(), P.only.end(), name_) == P.only.end()) return;
   std::lock_guard<std::mutex> g(P.mu);
   if (P.pending.size() > 4096) P.flush(false);
   a_ = P.get();
@@ -138,7 +148,17 @@ int pff_profile_enable(int on) {
 int pff_profile_select(const char* name) {
   auto& P = pff::prof();
   std::lock_guard<std::mutex> g(P.mu);
-  P.only = name ? name : "";
+  P.only.clear();
+  if (name) {
+    const std::string all(name);
+    size_t a = 0;
+    while (a <= all.size()) {
+      size_t b = all.find(',', a);
+      if (b == std::string::npos) b = all.size();
+      if (b > a) P.only.push_back(all.substr(a, b - a));
+      a = b + 1;
+    }
+  }
   return PFF_OK;
 }
 
