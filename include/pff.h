@@ -79,12 +79,13 @@ typedef struct pff_options {
   int cycle_lock;       /* lock an index active after this many membership changes; 3 */
   int krylov_restart;   /* FGMRES restart length m; 40 */
   int max_krylov;       /* FGMRES iterations per linear solve; 600 */
-  int cheb_degree;      /* Chebyshev smoother degree; 2 */
+  int cheb_degree;      /* Chebyshev smoother degree on the finest level; 4 */
   double amg_theta;     /* strength threshold on the distance Laplacian of the mesh nodes
                            (w_ij = 1/|x_i - x_j|^2 strong iff w_ij^2 >= theta^2 wmax_i wmax_j);
-                           0.06 (0 treats every coupling as strong and fails on graded
-                           meshes; 0.25 and above lose semi-coarsening efficiency) */
-  int amg_coarse_max;   /* largest coarse level (scalar rows) solved directly; 320 */
+                           0.02 (0 treats every coupling as strong and fails on graded
+                           meshes; 0.06 and above coarsen the graded meshes less
+                           effectively: +10 % time on the graded 2d and 3d workloads) */
+  int amg_coarse_max;   /* largest coarse level (scalar rows) solved directly; 1000 */
   int apply_variant;    /* PFF_APPLY_*; PFF_APPLY_AUTO */
   int precond;          /* PFF_PC_*; PFF_PC_AMG */
   double cheb_ratio;    /* Chebyshev smoothing interval [lmax/ratio, 1.1 lmax]; 8 */
@@ -106,7 +107,7 @@ typedef struct pff_options {
   int precond_overlap;  /* 1: the displacement and phase-field V-cycles of the block
                            preconditioner run concurrently on two streams; 0: one after the
                            other; 1 */
-  int cheb_degree_coarse; /* Chebyshev degree on AMG levels >= 1; 0 = cheb_degree; 0 */
+  int cheb_degree_coarse; /* Chebyshev degree on AMG levels >= 1; 0 = cheb_degree; 2 */
   double forcing_max;   /* > 0: inexact Newton with the Eisenstat-Walker forcing term: the
                            first linear solve of a loading step to forcing_max, later ones to
                            0.9 (rho_k / rho_k-1)^2, never tighter than tol_linear; 0: every
@@ -118,6 +119,11 @@ typedef struct pff_options {
                            from the one it was built for in more than this fraction of the
                            nodes (otherwise only its finest level is refreshed); 1e-3 */
   int amg_age_phi;      /* ... or once it has served this many Newton iterations; 8 */
+  int amg_levels_phi;   /* at most this many levels in the phase-field hierarchy, the last
+                           one smoothing only (1: Chebyshev smoothing on the assembled
+                           stencil, no coarse levels); 0 = coarsen down to amg_coarse_max; 1 */
+  int cheb_degree_phi;  /* Chebyshev degree on the finest level of the phase-field block;
+                           0 = cheb_degree; 4 */
 } pff_options;
 
 /* Per loading step (or per Newton iteration for pff_newton_step) report. */

@@ -51,6 +51,7 @@ class PffOptions(ctypes.Structure):
         ("precond_overlap", ctypes.c_int), ("cheb_degree_coarse", ctypes.c_int),
         ("forcing_max", ctypes.c_double), ("iter_graph", ctypes.c_int),
         ("amg_rebuild_phi", ctypes.c_double), ("amg_age_phi", ctypes.c_int),
+        ("amg_levels_phi", ctypes.c_int), ("cheb_degree_phi", ctypes.c_int),
     ]
 
 

@@ -1421,6 +1421,21 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
     double* dnorm = dalloc<double>(nb);
     count_launch();
     k_diag<<<grid_for(nb, 256), 256, 0, s>>>(nb, br, A.rowptr, A.col, A.val, dnorm, L.dinv, sc.err);
+    if (level >= prm.max_levels) {
+      // level limit reached: this level only smooths (no strength or aggregation work)
+      L.terminal = true;
+      L.lmax = level_lmax(amg, L, s, partials, sc);
+      L.x = dalloc<double>(n);
+      L.b = dalloc<double>(n);
+      L.r = dalloc<double>(n);
+      L.d = dalloc<double>(n);
+      L.t = dalloc<double>(n);
+      PFF_CUDA(cudaStreamSynchronize(s));
+      dfree(dnorm);
+      amg.lev.push_back(L);
+      amg.nc = 0;
+      break;
+    }
     // strength
     uint8_t* s0 = dalloc<uint8_t>(A.nnzb);
     uint8_t* strong = dalloc<uint8_t>(A.nnzb);

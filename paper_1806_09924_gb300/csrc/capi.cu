@@ -270,6 +270,8 @@ pff_options resolve_options(const pff_options* opts) {
   need(o.amg_reuse_tol >= 0.0, "negative amg_reuse_tol");
   need(o.forcing_max >= 0.0 && o.forcing_max < 1.0, "forcing_max must be in [0, 1)");
   need(o.amg_rebuild_phi >= 0.0 && o.amg_age_phi >= 1, "amg_rebuild_phi < 0 or amg_age_phi < 1");
+  need(o.amg_levels_phi >= 0, "amg_levels_phi must be >= 0");
+  need(o.cheb_degree_phi >= 0, "cheb_degree_phi must be >= 0");
   need(o.precond == PFF_PC_AMG || o.precond == PFF_PC_JACOBI || o.precond == PFF_PC_AMG_TRI,
        "unknown precond");
   need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 1 || o.spmv_group == 2 ||
@@ -295,9 +297,12 @@ void pff_default_options(pff_options* o) {
   o->cycle_lock = 3;
   o->krylov_restart = 40;
   o->max_krylov = 600;
-  o->cheb_degree = 2;
-  o->amg_theta = 0.06;
-  o->amg_coarse_max = 320;
+  o->cheb_degree = 4;
+  o->cheb_degree_coarse = 2;
+  o->cheb_degree_phi = 4;
+  o->amg_levels_phi = 1;
+  o->amg_theta = 0.02;
+  o->amg_coarse_max = 1000;
   o->apply_variant = PFF_APPLY_AUTO;
   o->precond = PFF_PC_AMG;
   o->cheb_ratio = 8.0;

@@ -364,7 +364,10 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   if (rebuild) {
     ProfScope ps("amg_setup_phi", 0.0, P->stream, 0);
     launch_stencil_to_bsr(m, n, 1, P->Kpp, P->App, P->stream);
-    amg_build(P->amg_p, P->App, P->Bp, 1, ap, P->stream);
+    AmgParams app = ap;
+    if (o.amg_levels_phi > 0) app.max_levels = o.amg_levels_phi - 1;
+    if (o.cheb_degree_phi > 0) app.cheb_degree = o.cheb_degree_phi;
+    amg_build(P->amg_p, P->App, P->Bp, 1, app, P->stream);
     P->cur.amg_builds_phi += 1;
     if (!P->active_built) P->active_built = dalloc<uint8_t>(n);
     PFF_CUDA(cudaMemcpyAsync(P->active_built, P->active, n, cudaMemcpyDeviceToDevice, P->stream));
