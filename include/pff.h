@@ -336,8 +336,9 @@ typedef struct pff_request {
   double l0;                      /* crack half-length (2d) / radius (3d) (pff_set_crack) */
   int n_steps;                    /* loading steps */
   const double* schedule;         /* host, n_steps pressures; copied */
-  int n_cod;                      /* COD points, may be 0 */
-  const double* cod_x;            /* host, n_cod abscissae; copied */
+  int n_cod;                      /* COD lines, may be 0 */
+  const double* cod_x;            /* host, n_cod abscissae x; copied.  Each gives one COD
+                                     line: along y at x (2d), along z at (x, y = 0) (3d) */
   int keep_solution;              /* 1: keep u, phi, active on the host (pff_server_solution) */
   int reserved;
 } pff_request;

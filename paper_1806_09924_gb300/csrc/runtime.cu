@@ -122,8 +122,15 @@ void run_job(pff_server* srv, Job* J, cudaStream_t s) {
       J->res.converged_steps += r.converged;
     }
     if (rc == PFF_OK) {
+      // one COD line per abscissa: along y in 2d, along z through y = 0 in 3d
+      std::vector<double> pts;
+      pts.reserve(J->cod_x.size() * (J->dim - 1));
+      for (double x : J->cod_x) {
+        pts.push_back(x);
+        if (J->dim == 3) pts.push_back(0.0);
+      }
       J->cod.assign(J->cod_x.size(), 0.0);
-      rc = pff_eval_tcv_cod(P, (int)J->cod_x.size(), J->cod_x.data(), &J->res.tcv, J->cod.data());
+      rc = pff_eval_tcv_cod(P, (int)J->cod_x.size(), pts.data(), &J->res.tcv, J->cod.data());
     }
     if (rc == PFF_OK && J->keep) {
       const size_t n = (size_t)P->n_nodes;

@@ -305,7 +305,11 @@ void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T
   const double bytes = sizeof(T) * (double)n *
                        ((zero_x ? 0.0 : slots_stored(m.dim, sizeof(T)) * b * b) + b * (zero_x ? 4.0 : 6.0)) +
                        (rhs64 ? 8.0 * n * b : 0.0) + (out64 ? (8.0 - 2.0 * sizeof(T)) * n * b : 0.0);
-  ProfScope ps(sizeof(T) == 8 ? "cheb0_f64" : "cheb0_f32", bytes, s);
+  // the displacement (b = dim) and phase-field (b = 1) smoothers are timed apart: their
+  // V-cycles run concurrently on two streams
+  ProfScope ps(sizeof(T) == 8 ? (b == 1 ? "cheb0_phi_f64" : "cheb0_u_f64")
+                              : (b == 1 ? "cheb0_phi_f32" : "cheb0_u_f32"),
+               bytes, s);
   if constexpr (sizeof(T) == 4) {
     if (node_major && m.dim == 2 && b == 2) {
       const unsigned g = grid_for(n, Q2_BLK);
@@ -328,7 +332,9 @@ template <class T>
 void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const T* rhs, const T* x,
                           T* r, cudaStream_t s, bool node_major) {
   const double bytes = sizeof(T) * (double)n * (slots_stored(m.dim, sizeof(T)) * b * b + 3.0 * b);
-  ProfScope ps(sizeof(T) == 8 ? "resid0_f64" : "resid0_f32", bytes, s);
+  ProfScope ps(sizeof(T) == 8 ? (b == 1 ? "resid0_phi_f64" : "resid0_u_f64")
+                              : (b == 1 ? "resid0_phi_f32" : "resid0_u_f32"),
+               bytes, s);
   if constexpr (sizeof(T) == 4) {
     if (node_major && m.dim == 2 && b == 2) {
       const unsigned g = grid_for(n, Q2_BLK);

@@ -123,6 +123,15 @@ def test_server_result_is_the_same_alone_and_in_the_mix():
         assert rel(u, u0) <= 1e-12 and rel(phi, phi0) <= 1e-12, w.name
         assert np.array_equal(act, a0), w.name
         assert rel(res["tcv"], tcv0) <= 1e-12 and rel(S.cod(rid), cod0) <= 1e-12
+        # the served COD lines are those of pff_eval_tcv_cod on the returned solution:
+        # along y at each abscissa (2d), along z through y = 0 (3d)
+        Q = pff.Problem(w.coords)
+        Q.set_material(w.E, w.nu, w.Gc, w.kappa, w.eps)
+        Q.set_state(u, phi, phi, phi, 1)
+        pts = np.array(cod_x) if w.dim == 2 else np.stack([cod_x, np.zeros(len(cod_x))], 1).ravel()
+        tcv_q, cod_q = Q.eval_tcv_cod(pts)
+        Q.close()
+        assert rel(S.cod(rid), cod_q) <= 1e-12 and rel(res["tcv"], tcv_q) <= 1e-12
         S.release(rid)
     st = S.stats()
     assert st["finished"] == len(reqs) and st["max_running"] >= 2, st
