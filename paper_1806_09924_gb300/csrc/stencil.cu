@@ -77,6 +77,18 @@ __device__ __forceinline__ void stencil_apply(const MeshDev& m, int64_t n, int i
   }
 }
 
+// Launch shape per instantiation.  With __launch_bounds__(256) alone the compiler
+// packs the 3d displacement step into 32 registers and serialises its 27 x 9
+// stencil loads (2.0 TB/s on the 128^3 mesh, measured); capping it at 128
+// registers with 4 blocks of 128 threads per SM keeps every load of a node in
+// flight (4.5 TB/s, bit-identical results).  The phase-field steps (B = 1) run
+// best with 6 blocks of 256 threads per SM (2.5 -> 3.7 TB/s).
+template <int D, int B>
+struct StencilShape {
+  static constexpr int threads = (D == 3 && B == 3) ? 128 : 256;
+  static constexpr int min_blocks = B == 1 ? 6 : 4;
+};
+
 // One Chebyshev step fused with the operator apply:
 // res = dinv .* (rhs - K x_in),  d = cd d + cr res,  x_out = x_in + d.
 // With zero_x the iterate starts at 0 (no apply).  The first step of a mixed
@@ -84,7 +96,8 @@ __device__ __forceinline__ void stencil_apply(const MeshDev& m, int64_t n, int i
 // rhs_store for the later steps) and the last one writes the FP64 result
 // (out64, instead of x_out and d), which saves two conversion passes.
 template <class T, int D, int B, bool SK>
-__global__ void __launch_bounds__(256) k_stencil_cheb(MeshDev m, int64_t n,
+__global__ void __launch_bounds__(StencilShape<D, B>::threads, StencilShape<D, B>::min_blocks)
+    k_stencil_cheb(MeshDev m, int64_t n,
                                                       const T* __restrict__ K,
                                                       const T* __restrict__ dinv,
                                                       const T* __restrict__ rhs,
@@ -238,7 +251,8 @@ __global__ void k_stencil_to_q2(int64_t n, const double* __restrict__ K, float* 
 
 // r = rhs - K x
 template <class T, int D, int B, bool SK>
-__global__ void __launch_bounds__(256) k_stencil_resid(MeshDev m, int64_t n,
+__global__ void __launch_bounds__(StencilShape<D, B>::threads, StencilShape<D, B>::min_blocks)
+    k_stencil_resid(MeshDev m, int64_t n,
                                                        const T* __restrict__ K,
                                                        const T* __restrict__ rhs,
                                                        const T* __restrict__ x,
@@ -279,13 +293,15 @@ bool stream_stencil(int d, int b, size_t es, int64_t n) {
 }
 }  // namespace
 
+#define STENCIL_LAUNCH_(D_, B_, SK, KERNEL, ...)                                        \
+  KERNEL<T, D_, B_, SK><<<grid_for(n, StencilShape<D_, B_>::threads),                  \
+                          StencilShape<D_, B_>::threads, 0, s>>>(__VA_ARGS__)
 #define STENCIL_DISPATCH_SK(dim, b, SK, KERNEL, ...)                                    \
   do {                                                                                 \
-    const unsigned g_ = grid_for(n, 256);                                              \
-    if ((dim) == 2 && (b) == 2) KERNEL<T, 2, 2, SK><<<g_, 256, 0, s>>>(__VA_ARGS__);       \
-    else if ((dim) == 2 && (b) == 1) KERNEL<T, 2, 1, SK><<<g_, 256, 0, s>>>(__VA_ARGS__);  \
-    else if ((dim) == 3 && (b) == 3) KERNEL<T, 3, 3, SK><<<g_, 256, 0, s>>>(__VA_ARGS__);  \
-    else if ((dim) == 3 && (b) == 1) KERNEL<T, 3, 1, SK><<<g_, 256, 0, s>>>(__VA_ARGS__);  \
+    if ((dim) == 2 && (b) == 2) STENCIL_LAUNCH_(2, 2, SK, KERNEL, __VA_ARGS__);          \
+    else if ((dim) == 2 && (b) == 1) STENCIL_LAUNCH_(2, 1, SK, KERNEL, __VA_ARGS__);     \
+    else if ((dim) == 3 && (b) == 3) STENCIL_LAUNCH_(3, 3, SK, KERNEL, __VA_ARGS__);     \
+    else if ((dim) == 3 && (b) == 1) STENCIL_LAUNCH_(3, 1, SK, KERNEL, __VA_ARGS__);     \
     else fail(PFF_ERR_INVALID_ARG, "stencil block size must be dim or 1");           \
   } while (0)
 #define STENCIL_DISPATCH(dim, b, KERNEL, ...)                                         \
