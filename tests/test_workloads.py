@@ -6,6 +6,8 @@ The expected values are the recipe's own statements (sizes, ratios, ranges,
 DoF totals), closed forms (node counts of the cut cells) and invariants
 (symmetry, reproducibility), not re-evaluations of the generator code.
 """
+import math
+
 import numpy as np
 import pytest
 
@@ -136,3 +138,35 @@ def test_crack_field_3d_penny():
     hmax = np.max(np.diff(x))
     r = np.hypot(x[zi], x[zj])
     assert r.max() < w.l0 + 2 * hmax and r.min() == 0.0
+
+
+def test_plateau_axis_and_domain_study_recipe():
+    """Section 4.2 stand-in meshes: uniform cells of size h on the crack region,
+    geometric growth (ratio <= 1.05) to the box edges, eps = 2h, a node at 0."""
+    for K, h in ((5.0, 0.01), (40.0, 0.00125)):
+        x = W.plateau_axis(K, h, 1.25)
+        dx = np.diff(x)
+        assert x[0] == -K and x[-1] == K and np.all(dx > 0)
+        assert np.any(np.abs(x) < 1e-12)
+        plat = np.abs(x[:-1] + x[1:]) / 2 < 1.25
+        np.testing.assert_allclose(dx[plat], h, rtol=1e-9)
+        grow = dx[len(dx) // 2:][~plat[len(dx) // 2:]]
+        assert np.all(grow[1:] / grow[:-1] <= 1.05 + 1e-12) and np.all(np.diff(grow) > 0)
+        np.testing.assert_allclose(dx, dx[::-1], rtol=1e-9)
+        w = W.domain_study(K, h)
+        assert w.eps == 2 * h and w.l0 == 1.0 and w.pressures == [1e-3]
+        assert w.h_min() == pytest.approx(h, rel=1e-9)
+        # the crack |x| < 1 on y = 0 marks the nodes of its cut cells
+        phi0 = w.phi0()
+        assert phi0.min() == 0.0 and 0 < np.count_nonzero(phi0 == 0) < w.n_nodes // 10
+
+
+def test_cyclic_loading_recipe():
+    w = W.cyclic_loading(64)
+    assert w.Gc == 1e-4 and w.n_cells == [64, 64] and w.eps == pytest.approx(2 * 4.0 / 64)
+    p = w.pressures
+    assert p == list(W.CYCLIC_PRESSURES)
+    assert p[0] < p[1] < p[2] and p[2] > p[3] > p[4] and p[4] < p[5] < p[6] and p[6] > p[2]
+    # the critical pressure of the sharp crack lies inside the schedule
+    pc = math.sqrt(w.E * w.Gc / ((1 - w.nu ** 2) * math.pi * w.l0))
+    assert min(p) < pc < max(p)

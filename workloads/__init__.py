@@ -22,7 +22,8 @@ import numpy as np
 __all__ = [
     "uniform_axis", "graded_axis", "crack_phi", "Workload", "config",
     "CONFIG_NAMES", "batched_instances", "served_requests", "random_state",
-    "scaled_workload", "cyclic_loading", "CYCLIC_PRESSURES",
+    "scaled_workload", "cyclic_loading", "CYCLIC_PRESSURES", "plateau_axis",
+    "domain_study",
 ]
 
 
@@ -189,6 +190,36 @@ def scaled_workload(w: Workload, n_cells: int, graded: Optional[bool] = None) ->
         ax = uniform_axis(n_cells, -half, half)
         eps = w.eps * n0 / n_cells
     return replace(w, name=f"{w.name}@{n_cells}", coords=[ax.copy() for _ in range(w.dim)], eps=eps)
+
+
+def plateau_axis(half_width: float, h: float, plateau: float, ratio: float = 1.05) -> np.ndarray:
+    """Uniform cells of size h on [-plateau, plateau] (rounded to whole cells),
+    then cells growing geometrically from h to the edges of [-half_width,
+    half_width], with the smallest cell count whose ratio does not exceed
+    ``ratio`` (the ratio is then solved so the cells fill the half width)."""
+    n_plat = int(round(2.0 * plateau / h))
+    a = n_plat * h / 2.0
+    rest = half_width - a
+    m = int(math.ceil(math.log(1.0 + rest * (ratio - 1.0) / h) / math.log(ratio)))
+    r = _solve_ratio(m, h, rest)
+    right = a + np.concatenate([[0.0], np.cumsum(h * r ** np.arange(m, dtype=np.float64))])
+    right[-1] = half_width
+    return np.concatenate([-right[::-1][:-1], np.linspace(-a, a, n_plat + 1), right[1:]])
+
+
+def domain_study(K: float, h: float, l0: float = 1.0, ratio: float = 1.05) -> Workload:
+    """One mesh of the finite-domain study of Section 4.2 (2d Sneddon, l0 = 1).
+
+    The box (-K, K)^2 with cells of size h on the crack and around it in x
+    (uniform on |x| <= 1.25 l0) and next to the crack line in y, growing
+    geometrically (ratio <= 1.05) toward the edges; eps = 2h, E = 1, nu = 0.2,
+    G_c = 1, p = 1e-3, kappa = 1e-10.  The paper refines adaptively; this is
+    the tensor-product stand-in with the same finest cell size on the crack.
+    """
+    x = plateau_axis(K, h, 1.25 * l0, ratio)
+    m = int(math.ceil(math.log(1.0 + K * (ratio - 1.0) / h) / math.log(ratio)))
+    y = graded_axis(2 * m, K, h)
+    return Workload(f"domain2d_K{K:g}_h{h:g}", 2, [x, y], eps=2.0 * h, l0=l0, pressures=[1e-3])
 
 
 # load, unload, reload: the first three steps approach the critical pressure, the
