@@ -1384,8 +1384,9 @@ void amg_build(Amg& amg, const Bsr& Ain, const double* Bin, int nns, const AmgPa
 
   for (int level = 0;; ++level) {
     const int n = nb * br;
-    const bool too_big = n > 8 * prm.coarse_max;
-    if (n <= prm.coarse_max || (level >= prm.max_levels && !too_big)) {
+    // a direct (dense) coarse solve only up to coarse_max rows; a larger level at the
+    // level limit smooths only (below)
+    if (n <= prm.coarse_max) {
       // coarsest level: dense inverse
       ph.start("setup_coarse_inverse");
       amg.nc = n;

@@ -2,8 +2,8 @@
 
 Only the CPU oracle (``oracle/``) and the seeded input generators
 (``workloads/``) are called here; nothing comes from the CUDA path.  Each
-fixture records the sha256 of the oracle and generator sources it was made
-from, so a test can tell when the oracle changed and the fixture is stale.
+fixture records the sha256 of the oracle sources and of the inputs it was
+made from, so a test can tell when either changed and the fixture is stale.
 
     python tests/golden/make_oracle_fixtures.py            # every fixture
     python tests/golden/make_oracle_fixtures.py penny3d_32
@@ -28,10 +28,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 SOURCES = ("oracle/__init__.py", "oracle/fe.py", "oracle/model.py", "oracle/pdas.py",
-           "oracle/functionals.py", "workloads/__init__.py")
+           "oracle/functionals.py")
 
 
 def source_hash() -> str:
+    """sha256 of the oracle's sources."""
     h = hashlib.sha256()
     for rel in SOURCES:
         with open(os.path.join(ROOT, rel), "rb") as f:
@@ -40,21 +41,35 @@ def source_hash() -> str:
     return h.hexdigest()
 
 
+def input_hash(w, pressures) -> str:
+    """sha256 of a workload's inputs: mesh coordinates, material, crack field, loads."""
+    h = hashlib.sha256()
+    for c in w.coords:
+        h.update(np.ascontiguousarray(c, dtype=np.float64).tobytes())
+    h.update(np.array([w.E, w.nu, w.Gc, w.kappa, w.eps, w.l0, *pressures], dtype=np.float64).tobytes())
+    h.update(np.ascontiguousarray(w.phi0(), dtype=np.float64).tobytes())
+    return h.hexdigest()
+
+
+def penny3d_32_workload():
+    import workloads as W
+    return W.scaled_workload(W.config(2), 32), [1e-3]
+
+
 def fixture_path(name: str) -> str:
     return os.path.join(HERE, f"oracle_{name}.npz")
 
 
 def _penny3d_32():
-    import workloads as W
     from oracle import fe, functionals as fn, model, pdas
-    w = W.scaled_workload(W.config(2), 32)
+    w, pressures = penny3d_32_workload()
     mesh = fe.Mesh(w.coords)
-    pressures = [1e-3]
     prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=pressures[0])
     st = pdas.State.initial(mesh, prm, w.phi0())
     reps = pdas.solve_loading_steps(st, pressures)
     assert all(r.converged for r in reps)
-    return dict(name=w.name, n_dofs=w.n_dofs, pressures=np.array(pressures), u=st.u, phi=st.phi,
+    return dict(name=w.name, n_dofs=w.n_dofs, pressures=np.array(pressures),
+                input_sha256=input_hash(w, pressures), u=st.u, phi=st.phi,
                 active=st.active.astype(np.uint8), indicator=st.indicator,
                 tcv=fn.tcv(mesh, st.u, st.phi), locked=np.array([r.locked for r in reps]),
                 newton_its=np.array([r.newton_its for r in reps]))

@@ -289,9 +289,10 @@ def test_newton_solution_parity_3d_32_stored_oracle():
     sys.path.insert(0, os.path.join(os.path.dirname(__file__), "golden"))
     import make_oracle_fixtures as mf
     z = np.load(mf.fixture_path("penny3d_32"))
-    assert str(z["source_sha256"]) == mf.source_hash(), \
-        "stale fixture: run python tests/golden/make_oracle_fixtures.py penny3d_32"
-    w = W.scaled_workload(W.config(2), 32)
+    w, pressures = mf.penny3d_32_workload()
+    stale = "stale fixture: run python tests/golden/make_oracle_fixtures.py penny3d_32"
+    assert str(z["source_sha256"]) == mf.source_hash(), stale
+    assert str(z["input_sha256"]) == mf.input_hash(w, pressures), stale
     assert int(z["n_dofs"]) == w.n_dofs
     mesh = fe.Mesh(w.coords)
     prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=1e-3)
