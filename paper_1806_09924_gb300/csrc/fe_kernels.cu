@@ -18,6 +18,12 @@
 //   Kuu[((s*d + m)*d + n)*N + i]   (M_uu, d x d block per slot)
 //   Kpu[(s*d + n)*N + i]           (M_phi_u)
 //   Kpp[s*N + i]                   (M_phi_phi)
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+#include <tuple>
+
 #include "pff_internal.h"
 
 namespace pff {
@@ -179,8 +185,8 @@ __device__ __forceinline__ bool adjacent_cell_index(const int* idx, int c, const
   return in;
 }
 
-template <int D>
-__global__ void __launch_bounds__(BLK) k_residual_qp(MeshDev m, Material mat, int64_t ncell,
+template <int D, int TB = BLK>
+__global__ void __launch_bounds__(TB) k_residual_qp(MeshDev m, Material mat, int64_t ncell,
                                                      const double* __restrict__ u,
                                                      const double* __restrict__ phi,
                                                      const double* __restrict__ phit,
@@ -264,8 +270,8 @@ __global__ void __launch_bounds__(BLK) k_residual_qp(MeshDev m, Material mat, in
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(BLK) k_residual_gather(MeshDev m, int64_t n, int64_t ncell,
+template <int D, int TB = BLK>
+__global__ void __launch_bounds__(TB) k_residual_gather(MeshDev m, int64_t n, int64_t ncell,
                                                          const double* __restrict__ QP,
                                                          double* __restrict__ F) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -371,8 +377,8 @@ __global__ void k_invert(int64_t n, const double* __restrict__ S, double* __rest
 // --------------------------------------------------------------- assembly ---
 // (M_uu)_ij = (g(phi~) sigma(chi_j), e(chi_i)); Dirichlet rows -> identity,
 // Dirichlet columns -> 0.
-template <int D>
-__global__ void __launch_bounds__(BLK) k_assemble_uu(MeshDev m, Material mat, int64_t n,
+template <int D, int TB = BLK>
+__global__ void __launch_bounds__(TB) k_assemble_uu(MeshDev m, Material mat, int64_t n,
                                                      const double* __restrict__ phit,
                                                      double* __restrict__ Kuu) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -404,47 +410,48 @@ __global__ void __launch_bounds__(BLK) k_assemble_uu(MeshDev m, Material mat, in
     double te[NA];
 #pragma unroll
     for (int b = 0; b < NA; ++b) te[b] = phit[cell_node<D>(ci, b, m)];
-    double Ke[NA][D][D];
-#pragma unroll
-    for (int b = 0; b < NA; ++b)
-#pragma unroll
-      for (int a = 0; a < D; ++a)
-#pragma unroll
-        for (int e = 0; e < D; ++e) Ke[b][a][e] = 0.0;
     const double JxW = wq * vol;
+    // per Gauss point: the degraded weight and the test node's gradient
+    double wg[NA], dNa[NA][D];
 #pragma unroll
     for (int q = 0; q < NA; ++q) {
       double pt = 0.0;
 #pragma unroll
       for (int b = 0; b < NA; ++b) pt += shp<D>(b, q) * te[b];
-      const double wg = JxW * (k1 * pt * pt + mat.kappa);
-      double dNa[D];
+      wg[q] = JxW * (k1 * pt * pt + mat.kappa);
 #pragma unroll
-      for (int l = 0; l < D; ++l) dNa[l] = dshp<D>(ai, q, l) * ih[l];
+      for (int l = 0; l < D; ++l) dNa[q][l] = dshp<D>(ai, q, l) * ih[l];
+    }
+    // one trial node's D x D block at a time, summed over the Gauss points in order
+    // (only D x D accumulators live: no spills in 3d)
+#pragma unroll 1
+    for (int b = 0; b < NA; ++b) {
+      if (node_on_boundary<D>(ci, b, m)) continue;
+      double Kb[D][D];
 #pragma unroll
-      for (int b = 0; b < NA; ++b) {
+      for (int a = 0; a < D; ++a)
+#pragma unroll
+        for (int e = 0; e < D; ++e) Kb[a][e] = 0.0;
+#pragma unroll
+      for (int q = 0; q < NA; ++q) {
         double dNb[D], dd = 0.0;
 #pragma unroll
         for (int l = 0; l < D; ++l) {
           dNb[l] = dshp<D>(b, q, l) * ih[l];
-          dd += dNa[l] * dNb[l];
+          dd += dNa[q][l] * dNb[l];
         }
 #pragma unroll
         for (int a = 0; a < D; ++a)
 #pragma unroll
           for (int e = 0; e < D; ++e)
-            Ke[b][a][e] += wg * (mat.mu * ((a == e ? dd : 0.0) + dNa[e] * dNb[a]) +
-                                 mat.lam * dNa[a] * dNb[e]);
+            Kb[a][e] += wg[q] * (mat.mu * ((a == e ? dd : 0.0) + dNa[q][e] * dNb[a]) +
+                                 mat.lam * dNa[q][a] * dNb[e]);
       }
-    }
-#pragma unroll
-    for (int b = 0; b < NA; ++b) {
-      if (node_on_boundary<D>(ci, b, m)) continue;
       const int s = slot_of<D>(c, b);
 #pragma unroll
       for (int a = 0; a < D; ++a)
 #pragma unroll
-        for (int e = 0; e < D; ++e) Kuu[((int64_t)(s * D + a) * D + e) * n + i] += Ke[b][a][e];
+        for (int e = 0; e < D; ++e) Kuu[((int64_t)(s * D + a) * D + e) * n + i] += Kb[a][e];
     }
   }
 }
@@ -515,8 +522,8 @@ __device__ __forceinline__ void contract_dshp_add(int l, const double (&A)[1 << 
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(BLK) k_assemble_phi_qp(MeshDev m, Material mat, int64_t ncell,
+template <int D, int TB = BLK>
+__global__ void __launch_bounds__(TB) k_assemble_phi_qp(MeshDev m, Material mat, int64_t ncell,
                                                          const double* __restrict__ u,
                                                          const double* __restrict__ phi,
                                                          double* __restrict__ QP) {
@@ -585,8 +592,8 @@ __global__ void __launch_bounds__(BLK) k_assemble_phi_qp(MeshDev m, Material mat
   }
 }
 
-template <int D>
-__global__ void __launch_bounds__(BLK) k_assemble_phi_gather(MeshDev m, Material mat, int64_t n,
+template <int D, int TB = BLK>
+__global__ void __launch_bounds__(TB) k_assemble_phi_gather(MeshDev m, Material mat, int64_t n,
                                                              int64_t ncell,
                                                              const double* __restrict__ QP,
                                                              double* __restrict__ Kpu,
@@ -710,8 +717,8 @@ __global__ void k_reduce_phi(MeshDev m, int64_t n, const uint8_t* __restrict__ a
 }
 
 // y = Sinv .* (G~ x) from the assembled (reduced) stencils.
-template <int D>
-__global__ void __launch_bounds__(256) k_apply_assembled(MeshDev m, int64_t n,
+template <int D, int TB = 256>
+__global__ void __launch_bounds__(TB) k_apply_assembled(MeshDev m, int64_t n,
                                                          const double* __restrict__ Kuu,
                                                          const double* __restrict__ Kpu,
                                                          const double* __restrict__ Kpp,
@@ -1194,6 +1201,107 @@ constexpr double B8 = 8.0;
 inline double NSd(int d) { return d == 2 ? 9.0 : 27.0; }
 }  // namespace
 
+// ------------------------------------------------------ element-tile autotune --
+// The FP64 element kernels compute one node or one cell per thread with no
+// cross-thread sums, so their block size ("tile") changes only speed, never a
+// result.  Each is compiled for 64, 128 and 256 threads per block (launch bounds
+// to match); at its first use for a given dimension and size class (power of
+// two of the thread count), outside any stream capture, every tile is timed on
+// the call's own data and the fastest is kept for the process.  PFF_ELEM_TILE =
+// 64 | 128 | 256 forces one tile.
+namespace {
+constexpr int kTiles[3] = {64, 128, 256};
+enum TileKernel { TK_RESID_QP, TK_RESID_GATHER, TK_ASM_UU, TK_ASM_PHI_QP, TK_ASM_PHI_GATHER, TK_APPLY };
+const char* const kTileKernelNames[] = {"residual_qp", "residual_gather", "assemble_uu",
+                                        "assemble_phi_qp", "assemble_phi_gather", "apply_assembled"};
+std::mutex g_tile_mu;
+std::map<std::tuple<int, int, int>, int> g_tile_best;   // (kernel, dim, size class) -> tile index
+
+int forced_tile() {
+  static const int f = [] {
+    const char* e = std::getenv("PFF_ELEM_TILE");
+    if (!e) return -1;
+    const int v = std::atoi(e);
+    for (int t = 0; t < 3; ++t)
+      if (kTiles[t] == v) return t;
+    return -1;
+  }();
+  return f;
+}
+
+// tile index for kernel k over n threads; `launch(t)` launches it with tile t
+template <class F>
+int pick_tile(TileKernel k, int dim, int64_t n, int def, cudaStream_t s, F&& launch) {
+  const int f = forced_tile();
+  if (f >= 0) return f;
+  int cls = 0;
+  while (cls < 62 && (int64_t(1) << (cls + 1)) <= n) ++cls;
+  const auto key = std::make_tuple((int)k, dim, cls);
+  {
+    std::lock_guard<std::mutex> g(g_tile_mu);
+    auto it = g_tile_best.find(key);
+    if (it != g_tile_best.end()) return it->second;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return def;   // no timing inside a capture; decided at the next uncaptured call
+  }
+  cudaEvent_t a, b;
+  PFF_CUDA(cudaEventCreate(&a));
+  PFF_CUDA(cudaEventCreate(&b));
+  int best = def;
+  float best_ms = 1e30f;
+  for (int t = 0; t < 3; ++t) {
+    launch(t);   // warm
+    PFF_CUDA(cudaEventRecord(a, s));
+    launch(t);
+    launch(t);
+    PFF_CUDA(cudaEventRecord(b, s));
+    PFF_CUDA(cudaEventSynchronize(b));
+    PFF_LAUNCH("element tile tuning");
+    float ms = 0.f;
+    PFF_CUDA(cudaEventElapsedTime(&ms, a, b));
+    if (verbose())
+      std::fprintf(stderr, "[pff] tile tune %s %dd n=%lld tile %d: %.2f us\n", kTileKernelNames[k], dim,
+                   (long long)n, kTiles[t], 500.0f * ms);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  count_launch(9);
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  std::lock_guard<std::mutex> g(g_tile_mu);
+  g_tile_best[key] = best;
+  return best;
+}
+}  // namespace
+
+#define TILE_DISPATCH(t, ...)         \
+  do {                                \
+    if ((t) == 0) {                   \
+      constexpr int TB = kTiles[0];   \
+      __VA_ARGS__;                    \
+    } else if ((t) == 1) {            \
+      constexpr int TB = kTiles[1];   \
+      __VA_ARGS__;                    \
+    } else {                          \
+      constexpr int TB = kTiles[2];   \
+      __VA_ARGS__;                    \
+    }                                 \
+  } while (0)
+
+// launch kernel K (template <int D, int TB>) over `count` threads with its tuned tile
+#define TUNED_LAUNCH(kind, count, def, K, ...)                                                  \
+  do {                                                                                        \
+    auto launch_ = [&](int t_) {                                                              \
+      TILE_DISPATCH(t_, DISPATCH(m.dim, (K<D, TB><<<grid_for((count), TB), TB, 0, s>>>(__VA_ARGS__)))); \
+    };                                                                                        \
+    launch_(pick_tile(kind, m.dim, (count), (def), s, launch_));                              \
+  } while (0)
+
 void launch_phi_tilde(const MeshDev& /*m*/, int64_t n, int steps_done, const double* phi_old,
                       const double* phi_prev, double* phit, cudaStream_t s) {
   ProfScope ps("phi_tilde", 3.0 * B8 * n, s);
@@ -1221,16 +1329,15 @@ void launch_residual(const MeshDev& m, const Material& mat, int64_t n, int64_t n
                      double* F, cudaStream_t s) {
   // reads u, phi, phi~; writes F (the quadrature records stay in L2 / are not counted)
   ProfScope ps("residual", B8 * n * (2.0 * m.dim + 3.0), s, 2);
-  DISPATCH(m.dim, (k_residual_qp<D><<<grid_for(n_cells, BLK), BLK, 0, s>>>(m, mat, n_cells, u, phi,
-                                                                           phit, qp)));
-  DISPATCH(m.dim, (k_residual_gather<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, n, n_cells, qp, F)));
+  TUNED_LAUNCH(TK_RESID_QP, n_cells, 1, k_residual_qp, m, mat, n_cells, u, phi, phit, qp);
+  TUNED_LAUNCH(TK_RESID_GATHER, n, 1, k_residual_gather, m, n, n_cells, qp, F);
   PFF_LAUNCH("residual");
 }
 
 void launch_assemble_uu(const MeshDev& m, const Material& mat, int64_t n, const double* phit,
                         double* Kuu, cudaStream_t s) {
   ProfScope ps("assemble_uu", B8 * n * (1.0 + NSd(m.dim) * m.dim * m.dim), s);
-  DISPATCH(m.dim, (k_assemble_uu<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, phit, Kuu)));
+  TUNED_LAUNCH(TK_ASM_UU, n, 1, k_assemble_uu, m, mat, n, phit, Kuu);
   PFF_LAUNCH("assemble_uu");
 }
 
@@ -1238,10 +1345,8 @@ void launch_assemble_phi(const MeshDev& m, const Material& mat, int64_t n, int64
                          const double* u, const double* phi, double* qp, double* Kpu, double* Kpp,
                          cudaStream_t s) {
   ProfScope ps("assemble_phi", B8 * n * ((m.dim + 1.0) + NSd(m.dim) * (m.dim + 1.0)), s, 2);
-  DISPATCH(m.dim, (k_assemble_phi_qp<D><<<grid_for(n_cells, BLK), BLK, 0, s>>>(m, mat, n_cells, u,
-                                                                               phi, qp)));
-  DISPATCH(m.dim, (k_assemble_phi_gather<D><<<grid_for(n, BLK), BLK, 0, s>>>(m, mat, n, n_cells, qp,
-                                                                             Kpu, Kpp)));
+  TUNED_LAUNCH(TK_ASM_PHI_QP, n_cells, 1, k_assemble_phi_qp, m, mat, n_cells, u, phi, qp);
+  TUNED_LAUNCH(TK_ASM_PHI_GATHER, n, 1, k_assemble_phi_gather, m, mat, n, n_cells, qp, Kpu, Kpp);
   PFF_LAUNCH("assemble_phi");
 }
 
@@ -1272,8 +1377,7 @@ void launch_apply_assembled(const MeshDev& m, const int64_t n, const double* Kuu
   // stencils (d^2 + d + 1 values per slot), x, y, Sinv
   const double per = NSd(m.dim) * (m.dim * m.dim + m.dim + 1.0) + (m.dim + 1.0) * (Sinv ? 3.0 : 2.0);
   ProfScope ps("apply_assembled", B8 * n * per, s);
-  DISPATCH(m.dim, (k_apply_assembled<D><<<grid_for(n, 256), 256, 0, s>>>(m, n, Kuu, Kpu, Kpp, x, y,
-                                                                         Sinv)));
+  TUNED_LAUNCH(TK_APPLY, n, 2, k_apply_assembled, m, n, Kuu, Kpu, Kpp, x, y, Sinv);
   PFF_LAUNCH("apply_assembled");
 }
 
