@@ -226,13 +226,14 @@ def _source_hash(rel_path: str) -> str:
         return hashlib.sha256(fh.read()).hexdigest()[:16]
 
 
-def _traffic_for(kernel: str):
-    """DRAM bytes per launch of `kernel` from the committed ncu summary, or None
-    when the source file of the kernel changed since the counters were taken."""
+def _traffic_for(kernel: str, workload: str):
+    """DRAM bytes per launch of `kernel` on `workload` from the committed ncu
+    summary, or None when there is none or the source file of the kernel changed
+    since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
-            e = json.load(f).get(kernel)
+            e = json.load(f).get(f"{kernel}@{workload}")
         if not e or e.get("source_sha256") != _source_hash(e["source"]):
             return None
         return e.get("dram_bytes_per_launch_full_size")
@@ -396,7 +397,7 @@ def measure_problem(kind, args, rank, world, local_rank, dist, with_fp64=True):
     if top_name and top_name in live:
         r_live = rate(live[top_name])
         roof = {"bound": "hbm", "kernel": top_name, "achieved": r_live["achieved"], "peak": peak,
-                "unit": "GB/s", "frac": r_live["frac"], "traffic": _traffic_for(top_name),
+                "unit": "GB/s", "frac": r_live["frac"], "traffic": _traffic_for(top_name, w.name),
                 "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
                 "launches": r_live["launches"], "avg_launch_us": r_live["avg_launch_us"],
                 "algorithmic_bytes_per_launch": r_live["algorithmic_bytes_per_launch"],
