@@ -107,7 +107,8 @@ typedef struct pff_options {
   int precond_overlap;  /* 1: the displacement and phase-field V-cycles of the block
                            preconditioner run concurrently on two streams; 0: one after the
                            other; 1 */
-  int cheb_degree_coarse; /* Chebyshev degree on AMG levels >= 1; 0 = cheb_degree; 2 */
+  int cheb_degree_coarse; /* Chebyshev degree on AMG levels >= 1; 0 = cheb_degree; -1 = by
+                           dimension: 2 in 2d, 3 in 3d; -1 */
   double forcing_max;   /* > 0: inexact Newton with the Eisenstat-Walker forcing term: the
                            first linear solve of a loading step to forcing_max, later ones to
                            0.9 (rho_k / rho_k-1)^2, never tighter than tol_linear; 0: every
@@ -124,6 +125,12 @@ typedef struct pff_options {
                            stencil, no coarse levels); 0 = coarsen down to amg_coarse_max; 1 */
   int cheb_degree_phi;  /* Chebyshev degree on the finest level of the phase-field block;
                            0 = cheb_degree; 4 */
+  int amg_rotations;    /* near-null space of the displacement hierarchy: 1 = rigid-body
+                           modes (translations and rotations; coarse blocks of 3 x 3 in
+                           2d, 6 x 6 in 3d), 0 = translations only (d x d blocks),
+                           -1 = by dimension: 1 in 2d, 0 in 3d (measured faster there:
+                           the 6 x 6 coarse operators cost more than the iterations
+                           they save); -1 */
 } pff_options;
 
 /* Per loading step (or per Newton iteration for pff_newton_step) report. */

@@ -52,6 +52,7 @@ class PffOptions(ctypes.Structure):
         ("forcing_max", ctypes.c_double), ("iter_graph", ctypes.c_int),
         ("amg_rebuild_phi", ctypes.c_double), ("amg_age_phi", ctypes.c_int),
         ("amg_levels_phi", ctypes.c_int), ("cheb_degree_phi", ctypes.c_int),
+        ("amg_rotations", ctypes.c_int),
     ]
 
 

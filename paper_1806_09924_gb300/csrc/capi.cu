@@ -272,6 +272,8 @@ pff_options resolve_options(const pff_options* opts) {
   need(o.amg_rebuild_phi >= 0.0 && o.amg_age_phi >= 1, "amg_rebuild_phi < 0 or amg_age_phi < 1");
   need(o.amg_levels_phi >= 0, "amg_levels_phi must be >= 0");
   need(o.cheb_degree_phi >= 0, "cheb_degree_phi must be >= 0");
+  need(o.amg_rotations >= -1 && o.amg_rotations <= 1, "amg_rotations must be -1, 0 or 1");
+  need(o.cheb_degree_coarse >= -1, "cheb_degree_coarse must be >= -1");
   need(o.precond == PFF_PC_AMG || o.precond == PFF_PC_JACOBI || o.precond == PFF_PC_AMG_TRI,
        "unknown precond");
   need(o.spmv_group == 0 || o.spmv_group == -1 || o.spmv_group == 1 || o.spmv_group == 2 ||
@@ -298,9 +300,10 @@ void pff_default_options(pff_options* o) {
   o->krylov_restart = 40;
   o->max_krylov = 600;
   o->cheb_degree = 4;
-  o->cheb_degree_coarse = 2;
+  o->cheb_degree_coarse = -1;
   o->cheb_degree_phi = 4;
   o->amg_levels_phi = 1;
+  o->amg_rotations = -1;
   o->amg_theta = 0.02;
   o->amg_coarse_max = 1000;
   o->apply_variant = PFF_APPLY_AUTO;

@@ -290,7 +290,10 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   ap.theta = o.amg_theta;
   ap.coarse_max = o.amg_coarse_max;
   ap.cheb_degree = o.cheb_degree;
-  ap.cheb_degree_coarse = o.cheb_degree_coarse > 0 ? o.cheb_degree_coarse : o.cheb_degree;
+  // -1: by dimension (measured on the graded 2d and 3d workloads)
+  ap.cheb_degree_coarse = o.cheb_degree_coarse > 0    ? o.cheb_degree_coarse
+                          : o.cheb_degree_coarse == 0 ? o.cheb_degree
+                                                      : (P->dim == 3 ? 3 : 2);
   ap.cheb_ratio = o.cheb_ratio > 1.0 ? o.cheb_ratio : 30.0;
   ap.coords = P->xyz;
   ap.coord_dim = P->dim;
@@ -340,7 +343,10 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   if (!reuse_u) {
     ProfScope ps("amg_setup_u", 0.0, P->stream, 0);   // wall time of the build (syncs inside)
     launch_stencil_to_bsr(m, n, P->dim, P->Kuu, P->Auu, P->stream);
-    amg_build(P->amg_u, P->Auu, P->Bu, P->dim == 2 ? 3 : 6, ap, P->stream);
+    // near-null space: the rigid-body modes (translations first in Bu), or translations only
+    const bool rot = o.amg_rotations < 0 ? P->dim == 2 : o.amg_rotations == 1;
+    const int nns = rot ? (P->dim == 2 ? 3 : 6) : P->dim;
+    amg_build(P->amg_u, P->Auu, P->Bu, nns, ap, P->stream);
     use_stencil(P->amg_u, P->Kuu, P->Kuu_f, P->dim);
     if (!P->phit_built) P->phit_built = dalloc<double>(n);
     PFF_CUDA(cudaMemcpyAsync(P->phit_built, P->phit, sizeof(double) * n, cudaMemcpyDeviceToDevice,
