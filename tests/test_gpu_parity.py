@@ -552,3 +552,50 @@ def test_block_triangular_preconditioner_reaches_the_same_solution():
         P.close()
     assert rel(out[1][0], out[0][0]) <= 1e-9 and rel(out[1][1], out[0][1]) <= 1e-9
 
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_coarse_space_with_or_without_rotations_reaches_the_same_solution(dim):
+    """The near-null space of the displacement hierarchy (rigid-body modes, or
+    translations only) shapes the FGMRES path, not the converged Newton solution."""
+    w = W.scaled_workload(W.config(1), 64) if dim == 2 else W.scaled_workload(W.config(2), 12)
+    pressures = w.pressures[:2]
+    out = []
+    for rot in (0, 1):
+        P = pff.problem_from_workload(w)
+        reps = P.solve_loading_steps(pressures, pff.options(precision=1, amg_rotations=rot))
+        assert all(r["converged"] == 1 for r in reps)
+        out.append(P.get_solution())
+        P.close()
+    assert rel(out[1][0], out[0][0]) <= 1e-9 and rel(out[1][1], out[0][1]) <= 1e-9
+
+
+_TILE_CHILD = r"""
+import sys, numpy as np
+sys.path.insert(0, {root!r})
+import paper_1806_09924_gb300 as pff, workloads as W
+w = W.scaled_workload(W.config(2), 10)
+P = pff.problem_from_workload(w)
+P.solve_loading_steps(w.pressures, pff.options(precision=1))
+u, phi, act = P.get_solution()
+np.savez({out!r}, u=u, phi=phi, act=act)
+"""
+
+
+def test_element_tiles_do_not_change_results(tmp_path):
+    """The element kernels (residual, assembly, assembled apply) give bit-identical
+    results whatever tile the autotuner picks: one 3d solve with each tile forced
+    (PFF_ELEM_TILE, read once per process, so each runs in a child process)."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    res = []
+    for tile in (64, 256):
+        out = str(tmp_path / f"tile{tile}.npz")
+        env = dict(os.environ, PFF_ELEM_TILE=str(tile))
+        subprocess.run([sys.executable, "-c", _TILE_CHILD.format(root=root, out=out)], env=env,
+                       check=True, timeout=600)
+        res.append(np.load(out))
+    for k in ("u", "phi", "act"):
+        assert np.array_equal(res[0][k], res[1][k]), k
