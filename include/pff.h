@@ -404,6 +404,13 @@ void pff_server_destroy(pff_server* srv);
  * moved once).  Adds a few microseconds per launch. */
 int pff_profile_enable(int on);
 
+/* Autotuner choices (sparse-kernel formats of the AMG hierarchy, element-kernel
+ * tiles, Jacobian apply variant) are timed with CUDA events at first use.  With
+ * the environment variable PFF_TUNE_CACHE naming a file, every choice is also
+ * written there and choices found there are reused without timing, so a run under
+ * a profiler (whose serialised, instrumented launches make such timings
+ * meaningless) executes the kernels of the plain run that wrote the file. */
+
 /* Restrict the timing to launches of the named kernels (as reported by
  * pff_profile_report; several names separated by commas); NULL times every
  * instrumented launch again.  Timing a few kernels keeps the event overhead

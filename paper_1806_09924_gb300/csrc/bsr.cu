@@ -381,6 +381,16 @@ int tune_one(Bsr& A, cudaStream_t s) {
       return it->second;
     }
   }
+  char rkey[96];
+  std::snprintf(rkey, sizeof(rkey), "spmv:%d:%d:%d:%d", std::get<0>(key), std::get<1>(key),
+                std::get<2>(key), std::get<3>(key));
+  int recorded = 0;
+  if (tune_lookup(rkey, &recorded)) {
+    if (recorded == BSR_SELL) bsr_make_sell(A, s);
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune[key] = recorded;
+    return recorded;
+  }
   const int64_t nx = (int64_t)A.ncols * A.bc, ny = (int64_t)A.nrows * A.br;
   T* x = dalloc<T>(nx);
   T* y = dalloc<T>(ny);
@@ -428,6 +438,7 @@ int tune_one(Bsr& A, cudaStream_t s) {
     A.sell_off = A.sell_col = nullptr;
     A.sell_valf = nullptr;
   }
+  tune_store(rkey, best);
   std::lock_guard<std::mutex> lk(g_tune_mu);
   g_tune[key] = best;
   return best;

@@ -1242,6 +1242,14 @@ int pick_tile(TileKernel k, int dim, int64_t n, int def, cudaStream_t s, F&& lau
     auto it = g_tile_best.find(key);
     if (it != g_tile_best.end()) return it->second;
   }
+  char rkey[96];
+  std::snprintf(rkey, sizeof(rkey), "tile:%s:%d:%d", kTileKernelNames[k], dim, cls);
+  int recorded = 0;
+  if (tune_lookup(rkey, &recorded) && recorded >= 0 && recorded < 3) {
+    std::lock_guard<std::mutex> g(g_tile_mu);
+    g_tile_best[key] = recorded;
+    return recorded;
+  }
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
     cudaGetLastError();
@@ -1273,6 +1281,7 @@ int pick_tile(TileKernel k, int dim, int64_t n, int def, cudaStream_t s, F&& lau
   count_launch(9);
   cudaEventDestroy(a);
   cudaEventDestroy(b);
+  tune_store(rkey, best);
   std::lock_guard<std::mutex> g(g_tile_mu);
   g_tile_best[key] = best;
   return best;

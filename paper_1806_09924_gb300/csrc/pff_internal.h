@@ -76,6 +76,10 @@ void set_capturing(bool on);
 double captured_bytes();
 // diagnostics on stderr when the environment variable PFF_VERBOSE is set
 bool verbose();
+// Autotuner choices kept in the file named by PFF_TUNE_CACHE (when set): a choice
+// found there is reused without timing, every new choice is written there.
+bool tune_lookup(const std::string& key, int* value);
+void tune_store(const std::string& key, int value);
 class ProfScope {
  public:
   ProfScope(const char* name, double bytes, cudaStream_t s, int kernels = 1);

@@ -131,6 +131,64 @@ ProfScope::~ProfScope() {
   P.pending.push_back({name_, bytes_, static_cast<cudaEvent_t>(a_), b});
 }
 
+// --------------------------------------------------- persistent tuning record --
+// The autotuners (sparse-kernel formats, element-kernel tiles, Jacobian apply
+// variant) time their candidates with CUDA events.  Under a profiler that
+// serialises and instruments every launch those timings mean nothing, and a
+// profiled run would execute different kernels than the run it documents.  With
+// PFF_TUNE_CACHE naming a file, every choice made is written there, and choices
+// found there are reused without timing: a plain run of a command records them,
+// the same command under the profiler replays them.
+namespace {
+struct TuneRecord {
+  std::mutex mu;
+  bool loaded = false;
+  std::string path;
+  std::map<std::string, int> entries;
+
+  void load() {   // mu held
+    if (loaded) return;
+    loaded = true;
+    const char* e = std::getenv("PFF_TUNE_CACHE");
+    if (!e || !*e) return;
+    path = e;
+    if (FILE* f = std::fopen(path.c_str(), "r")) {
+      char key[256];
+      int v = 0;
+      while (std::fscanf(f, "%255s %d", key, &v) == 2) entries[key] = v;
+      std::fclose(f);
+    }
+  }
+};
+
+TuneRecord& tune_record() {
+  static TuneRecord* t = new TuneRecord();
+  return *t;
+}
+}  // namespace
+
+bool tune_lookup(const std::string& key, int* value) {
+  TuneRecord& t = tune_record();
+  std::lock_guard<std::mutex> g(t.mu);
+  t.load();
+  auto it = t.entries.find(key);
+  if (it == t.entries.end()) return false;
+  *value = it->second;
+  return true;
+}
+
+void tune_store(const std::string& key, int value) {
+  TuneRecord& t = tune_record();
+  std::lock_guard<std::mutex> g(t.mu);
+  t.load();
+  t.entries[key] = value;
+  if (t.path.empty()) return;
+  if (FILE* f = std::fopen(t.path.c_str(), "w")) {
+    for (const auto& kv : t.entries) std::fprintf(f, "%s %d\n", kv.first.c_str(), kv.second);
+    std::fclose(f);
+  }
+}
+
 }  // namespace pff
 
 extern "C" {

@@ -237,6 +237,16 @@ static void choose_apply(pff_problem* P) {
       return;
     }
   }
+  const std::string rkey = "apply:" + std::to_string(key.first) + ":" + std::to_string(key.second);
+  int recorded = 0;
+  if (tune_lookup(rkey, &recorded) &&
+      (recorded == PFF_APPLY_ASSEMBLED || recorded == PFF_APPLY_MATFREE)) {
+    P->apply_variant = recorded;
+    P->apply_auto = false;
+    std::lock_guard<std::mutex> g(mu);
+    cache[key] = recorded;
+    return;
+  }
   cudaEvent_t e0, e1;
   PFF_CUDA(cudaEventCreate(&e0));
   PFF_CUDA(cudaEventCreate(&e1));
@@ -263,6 +273,7 @@ static void choose_apply(pff_problem* P) {
   cudaEventDestroy(e1);
   P->apply_variant = best;
   P->apply_auto = false;
+  tune_store(rkey, best);
   std::lock_guard<std::mutex> g(mu);
   cache[key] = best;
 }

@@ -599,3 +599,27 @@ def test_element_tiles_do_not_change_results(tmp_path):
         res.append(np.load(out))
     for k in ("u", "phi", "act"):
         assert np.array_equal(res[0][k], res[1][k]), k
+
+
+def test_tuning_record_replays_the_same_choices(tmp_path):
+    """PFF_TUNE_CACHE: a first process records every autotuner choice (sparse
+    formats, element tiles, apply variant); a second process with the same file
+    reuses them without timing and reaches a bit-identical solution."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    rec = str(tmp_path / "tune.txt")
+    res = []
+    for k in range(2):
+        out = str(tmp_path / f"run{k}.npz")
+        env = dict(os.environ, PFF_TUNE_CACHE=rec)
+        env.pop("PFF_ELEM_TILE", None)
+        subprocess.run([sys.executable, "-c", _TILE_CHILD.format(root=root, out=out)], env=env,
+                       check=True, timeout=600)
+        res.append(np.load(out))
+        if k == 0:
+            text = open(rec).read()
+            assert "spmv:" in text and "tile:" in text and "apply:" in text, text
+    for k in ("u", "phi", "act"):
+        assert np.array_equal(res[0][k], res[1][k]), k
