@@ -137,6 +137,7 @@ void refresh_phi_tilde(pff_problem* P) {
   P->amg_u_valid = false;
   P->amg_p_valid = false;
   P->in_step = false;
+  P->F_ready = false;
 }
 
 void release(pff_problem* P) {
@@ -479,6 +480,7 @@ int pff_set_material(pff_problem* P, double E, double nu, double Gc, double kapp
   P->amg_u_valid = false;
   P->amg_p_valid = false;
   P->in_step = false;
+  P->F_ready = false;
   API_END
 }
 

@@ -418,6 +418,7 @@ struct pff_problem {
   // work vectors (n_dofs)
   double *F = nullptr, *Ft = nullptr, *dU = nullptr, *dUA = nullptr;
   double *ut = nullptr, *phit_trial = nullptr, *Ftrial = nullptr;
+  bool F_ready = false;   // F already holds the residual of the current (u, phi), p, phi~
 
   // preconditioner
   pff::Bsr Auu, App;

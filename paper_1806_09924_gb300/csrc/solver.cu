@@ -696,6 +696,7 @@ void begin_loading_step(pff_problem* P, double p) {
   launch_scaling(P->mesh(), P->mat, P->n_nodes, P->Kuu, P->S, P->Sinv, P->stream);
   P->uu_assembled = true;
   P->in_step = true;
+  P->F_ready = false;
   P->k = 0;
   P->have_prev = false;
   P->last_small = false;
@@ -748,8 +749,10 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   const int dim = P->dim;
   const int64_t N = P->n_dofs;
   pff_step_report& R = P->cur;
-  // 1-2. residual and active set
-  compute_residual(P, P->u, P->phi, P->F);
+  // 1-2. residual and active set (the line search of the previous iteration may
+  // already have evaluated it at the accepted state: same kernel, same inputs)
+  if (!P->F_ready) compute_residual(P, P->u, P->phi, P->F);
+  P->F_ready = false;
   compute_active_set(P, o.c, o.tol_active, o.tol_change, o.cycle_lock, P->have_prev);
   PFF_CUDA(cudaMemcpyAsync(P->h_counters, P->counters, 4 * sizeof(int), cudaMemcpyDeviceToHost, s));
   double rho_l2 = 0.0;
@@ -857,6 +860,7 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
   const double step_phi = hs[3] > 0 ? hs[2] / hs[3] : hs[2];
   // 6. line search
   double omega = 1.0;
+  bool trial_is_next = false;   // Ftrial holds the residual at the accepted state
   if (!small) {
     for (int t = 0; t <= o.max_halvings; ++t) {
       if (t > 0)
@@ -865,7 +869,10 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
       compute_residual(P, P->ut, P->phit_trial, P->Ftrial);
       double l2 = 0.0;
       scaled_norms(P, P->Ftrial, &l2);
-      if (l2 < rho_l2) break;
+      if (l2 < rho_l2) {
+        trial_is_next = true;
+        break;
+      }
       if (t == o.max_halvings) {
         omega = 1.0;
         R.linesearch_fails += 1;
@@ -884,6 +891,10 @@ int newton_iteration(pff_problem* P, const pff_options& o, pff_step_report* rep)
                  (int)small, omega);
   std::swap(P->u, P->ut);
   std::swap(P->phi, P->phit_trial);
+  if (trial_is_next) {
+    std::swap(P->F, P->Ftrial);
+    P->F_ready = true;
+  }
   P->last_small = small;
   P->have_prev = true;
   P->k += 1;
