@@ -269,6 +269,49 @@ int pff_linear_solve_dev(pff_problem* prob, const pff_options* opts, const doubl
 int pff_set_state_dev(pff_problem* prob, const double* u_dev, const double* phi_dev,
                       const double* phi_old_dev, const double* phi_prev_dev, int steps_done);
 
+/* Adaptive refinement (Section 3, refinement strategy) ------------------------
+ *
+ * The paper refines octree meshes with hanging nodes: cells of the crack region
+ * until eps = 2h holds there, the rest by a gradient-jump estimator for the
+ * displacements.  Here the mesh stays a tensor product, so refinement splits
+ * whole axis intervals (slabs of cells); a refined mesh is a new problem, and
+ * the state moves to it by Q1 interpolation. */
+
+/* Gradient-jump (Kelly-type) indicator of the current displacements per cell,
+ * eta2[c] = (h_c / 24) * sum over the interior faces F of cell c of the
+ * integral over F of |[du/dn]|^2 (h_c the cell diameter, [du/dn] the jump of
+ * the normal derivative of every component; boundary faces contribute
+ * nothing).  eta2_dev: n_cells doubles on the device, cells numbered like
+ * nodes (x fastest).  Asynchronous on the problem's stream. */
+int pff_cell_indicators_dev(pff_problem* prob, double* eta2_dev);
+
+/* One refinement pass of the axes.  With S_a[i] the sum of eta2 over the
+ * cells whose a-index is i, and minphi_a[i] the smallest phi on those cells'
+ * nodes, interval i of axis a is split at its midpoint when
+ *   S_a[i] > 0 and S_a[i] >= theta * max_i S_a[i]          (estimator), or
+ *   minphi_a[i] < phi_band and its length exceeds h_band   (crack region:
+ *                                                         h_band = eps / 2).
+ * theta >= 0 (theta > 1 disables the estimator rule), h_band >= 0.
+ * Outputs (host, caller-owned): n_cells_out[dim] and coords_out[a], each with
+ * room for 2 * n_cells[a] + 1 doubles, strictly increasing and containing the
+ * old coordinates.  The problem is not changed.  Synchronous. */
+int pff_refine_axes(pff_problem* prob, double theta, double h_band, double phi_band,
+                    int32_t* n_cells_out, double* const* coords_out);
+
+/* Move nodal fields of src onto the nodes of dst by Q1 interpolation (the
+ * finite element function of src evaluated at dst's nodes; each value is the
+ * corner sum of prod(t or 1 - t) times the corner values, in corner order,
+ * rounded product by product).  dst's box must lie inside src's; both problems
+ * must have the same dimension.  fields: any of the flags below.  With
+ * PFF_FIELD_PHI_OLD, dst also takes src's count of finished loading steps (the
+ * phi~ extrapolation).  Clears dst's assembled operators and preconditioner.
+ * Synchronizes both streams. */
+#define PFF_FIELD_U 1
+#define PFF_FIELD_PHI 2
+#define PFF_FIELD_PHI_OLD 4
+#define PFF_FIELD_PHI_PREV 8
+int pff_transfer_state(pff_problem* src, pff_problem* dst, int fields);
+
 /* Allocation-free TCV / COD ------------------------------------------------ */
 
 /* The paper has no counterpart of this entry point.  It exists for callers

@@ -17,10 +17,12 @@ Contents (each function cites the passage of the paper it follows):
                      loop (Section 3, commented algorithm) with exact block
                      solves, line search and cycle locking.
 * ``functionals`` -- TCV and COD (Section 4) and Sneddon's closed forms.
+* ``adapt``       -- refinement strategy of Section 3 on tensor-product meshes:
+                     gradient-jump indicator, slab marking, Q1 transfer.
 
 Pins (tests/test_oracle_*.py) tie every function to something other than
 itself: exact symbolic integration, rigid-body and patch invariants, finite
 differences of the energy and of the residual, brute-force dense and staggered
 solves, KKT conditions, Table 1 DoF counts and Sneddon's closed forms.
 """
-from . import fe, model, pdas, functionals  # noqa: F401
+from . import fe, model, pdas, functionals, adapt  # noqa: F401

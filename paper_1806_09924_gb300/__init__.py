@@ -146,6 +146,10 @@ _SIGS = {
     "pff_profile_report": (ctypes.c_int, [ctypes.c_char_p, ctypes.c_int]),
     "pff_launch_count": (ctypes.c_longlong, []),
     "pff_eval_tcv_cod_noalloc": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "pff_cell_indicators_dev": (ctypes.c_int, [_P, _P]),
+    "pff_refine_axes": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_D)]),
+    "pff_transfer_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
     "pff_batch_solve": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(_D), ctypes.POINTER(PffOptions),
                                        ctypes.POINTER(ctypes.POINTER(PffStepReport)), ctypes.c_int,
@@ -167,6 +171,8 @@ _SIGS = {
 }
 
 PFF_NOALLOC_MAX_POINTS = 1024
+PFF_FIELD_U, PFF_FIELD_PHI, PFF_FIELD_PHI_OLD, PFF_FIELD_PHI_PREV = 1, 2, 4, 8
+PFF_FIELD_ALL = 15
 
 _lib = None
 
@@ -337,6 +343,30 @@ class Problem:
                                           phi.ctypes.data_as(ctypes.c_void_p),
                                           act.ctypes.data_as(ctypes.c_void_p)))
         return u, phi, act
+
+    # ---- adaptive refinement
+    @property
+    def coords(self):
+        return [c.copy() for c in self._coords]
+
+    @property
+    def n_cells(self) -> int:
+        return int(np.prod([len(c) - 1 for c in self._coords]))
+
+    def cell_indicators_dev(self, eta2):
+        _check(self._lib.pff_cell_indicators_dev(self._h, _dev(eta2, "torch.float64", self.n_cells)))
+
+    def refine_axes(self, theta, h_band, phi_band):
+        """pff_refine_axes: the refined axis coordinates (the problem is unchanged)."""
+        outs = [np.empty(2 * (len(c) - 1) + 1) for c in self._coords]
+        ptrs = (_D * self.dim)(*[o.ctypes.data_as(_D) for o in outs])
+        nc = (ctypes.c_int32 * self.dim)()
+        _check(self._lib.pff_refine_axes(self._h, float(theta), float(h_band), float(phi_band), nc, ptrs))
+        return [outs[a][:nc[a] + 1].copy() for a in range(self.dim)]
+
+    def transfer_state(self, dst: "Problem", fields: int = PFF_FIELD_ALL):
+        """pff_transfer_state: interpolate this problem's fields onto dst's nodes."""
+        _check(self._lib.pff_transfer_state(self._h, dst._h, int(fields)))
 
     # ---- component entry points (device buffers)
     def residual_dev(self, F):

@@ -628,6 +628,124 @@ int pff_eval_tcv_cod(pff_problem* P, int n_pts, const double* pts, double* tcv, 
   API_END
 }
 
+int pff_cell_indicators_dev(pff_problem* P, double* eta2_dev) {
+  API_BEGIN
+  need(P != nullptr && eta2_dev != nullptr, "NULL argument");
+  pff::jump_indicator_dev(P->mesh(), P->n_cells, P->u, eta2_dev, P->stream);
+  API_END
+}
+
+int pff_refine_axes(pff_problem* P, double theta, double h_band, double phi_band,
+                    int32_t* n_cells_out, double* const* coords_out) {
+  API_BEGIN
+  need(P != nullptr && n_cells_out != nullptr && coords_out != nullptr, "NULL argument");
+  need(theta >= 0 && std::isfinite(theta), "theta must be finite and >= 0");
+  need(h_band >= 0 && std::isfinite(h_band), "h_band must be finite and >= 0");
+  need(std::isfinite(phi_band), "phi_band must be finite");
+  for (int a = 0; a < P->dim; ++a) need(coords_out[a] != nullptr, "coords_out[a] is NULL");
+  pff::AllocStream alloc_scope(P->stream);
+  const auto m = P->mesh();
+  int slabs = 0;
+  for (int a = 0; a < P->dim; ++a) slabs += P->nc[a];
+  double* eta2 = pff::dalloc<double>(P->n_cells);
+  double* red = pff::dalloc<double>(2 * (size_t)slabs);
+  pff::jump_indicator_dev(m, P->n_cells, P->u, eta2, P->stream);
+  pff::slab_reduce_dev(m, eta2, P->phi, red, red + slabs, P->stream);
+  std::vector<double> h(2 * (size_t)slabs);
+  PFF_CUDA(cudaMemcpyAsync(h.data(), red, sizeof(double) * 2 * slabs, cudaMemcpyDeviceToHost,
+                           P->stream));
+  sync(P);
+  pff::dfree(eta2);
+  pff::dfree(red);
+  // marking and splitting: an interval is split when its slab sum reaches
+  // theta times the axis maximum (and is positive), or when the slab reaches
+  // the crack region (min phi < phi_band) while the interval is longer than
+  // h_band; a split adds the midpoint when it lies strictly inside
+  int off = 0;
+  for (int a = 0; a < P->dim; ++a) {
+    const std::vector<double>& x = P->hX[a];
+    const double* S = h.data() + off;
+    const double* mp = h.data() + slabs + off;
+    double smax = 0.0;
+    for (int i = 0; i < P->nc[a]; ++i) smax = std::max(smax, S[i]);
+    int k = 0;
+    double* out = coords_out[a];
+    for (int i = 0; i < P->nc[a]; ++i) {
+      out[k++] = x[i];
+      const bool by_eta = smax > 0.0 && S[i] > 0.0 && S[i] >= theta * smax;
+      const bool by_band = mp[i] < phi_band && x[i + 1] - x[i] > h_band;
+      const double mid = 0.5 * (x[i] + x[i + 1]);
+      if ((by_eta || by_band) && mid > x[i] && mid < x[i + 1]) out[k++] = mid;
+    }
+    out[k++] = x[P->nc[a]];
+    n_cells_out[a] = k - 1;
+    off += P->nc[a];
+  }
+  API_END
+}
+
+int pff_transfer_state(pff_problem* src, pff_problem* dst, int fields) {
+  API_BEGIN
+  need(src != nullptr && dst != nullptr, "problem is NULL");
+  need(src != dst, "src and dst must be different problems");
+  need(src->dim == dst->dim, "src and dst differ in dimension");
+  need((fields & ~(PFF_FIELD_U | PFF_FIELD_PHI | PFF_FIELD_PHI_OLD | PFF_FIELD_PHI_PREV)) == 0,
+       "unknown field flag");
+  const int dim = src->dim;
+  for (int a = 0; a < dim; ++a)
+    need(dst->hX[a].front() >= src->hX[a].front() && dst->hX[a].back() <= src->hX[a].back(),
+         "dst mesh leaves the src mesh's box");
+  // per axis: source interval (last one whose left end is <= the new coordinate)
+  // and local coordinate of every new axis coordinate
+  std::vector<int> hc[3];
+  std::vector<double> ht[3];
+  for (int a = 0; a < dim; ++a) {
+    const std::vector<double>& x = src->hX[a];
+    const int n = (int)x.size() - 1;
+    for (double xn : dst->hX[a]) {
+      int i = (int)(std::upper_bound(x.begin(), x.end(), xn) - x.begin()) - 1;
+      i = std::min(std::max(i, 0), n - 1);
+      hc[a].push_back(i);
+      ht[a].push_back((xn - x[i]) / (x[i + 1] - x[i]));
+    }
+  }
+  sync(src);
+  pff::AllocStream alloc_scope(dst->stream);
+  const int* dc[3] = {nullptr, nullptr, nullptr};
+  const double* dt[3] = {nullptr, nullptr, nullptr};
+  std::vector<void*> temps;
+  for (int a = 0; a < dim; ++a) {
+    int* c = pff::dalloc<int>(hc[a].size());
+    double* t = pff::dalloc<double>(ht[a].size());
+    PFF_CUDA(cudaMemcpyAsync(c, hc[a].data(), sizeof(int) * hc[a].size(), cudaMemcpyHostToDevice,
+                             dst->stream));
+    PFF_CUDA(cudaMemcpyAsync(t, ht[a].data(), sizeof(double) * ht[a].size(), cudaMemcpyHostToDevice,
+                             dst->stream));
+    dc[a] = c;
+    dt[a] = t;
+    temps.push_back(c);
+    temps.push_back(t);
+  }
+  struct Field {
+    int flag;
+    const double* s;
+    double* d;
+    int ncomp;
+  } list[] = {{PFF_FIELD_U, src->u, dst->u, dim},
+              {PFF_FIELD_PHI, src->phi, dst->phi, 1},
+              {PFF_FIELD_PHI_OLD, src->phi_old, dst->phi_old, 1},
+              {PFF_FIELD_PHI_PREV, src->phi_prev, dst->phi_prev, 1}};
+  for (const Field& f : list)
+    if (fields & f.flag)
+      pff::transfer_dev(dim, dst->nn, src->nn, dc, dt, f.s, f.ncomp, f.d, dst->stream);
+  sync(dst);
+  for (void* p : temps) pff::dfree(p);
+  if (fields & PFF_FIELD_PHI_OLD) dst->steps_done = src->steps_done;
+  refresh_phi_tilde(dst);
+  sync(dst);
+  API_END
+}
+
 int pff_get_solution(pff_problem* P, double* u, double* phi, uint8_t* active) {
   API_BEGIN
   need(P != nullptr, "problem is NULL");

@@ -377,6 +377,18 @@ struct CodColumn {
 };
 void cod_dev(const MeshDev& m, const CodColumn* cols, int ncols, const double* u,
              const double* phi, double* out, int npts, cudaStream_t s);
+// adaptive refinement (Section 3, refinement strategy): gradient-jump indicator
+// eta_K^2 per cell; per axis slab the sum of eta2 and the smallest nodal phi
+// (slabs of all axes numbered consecutively); Q1 transfer of a nodal field
+// (ncomp values per node) given each new axis coordinate's source interval and
+// local coordinate
+void jump_indicator_dev(const MeshDev& m, int64_t n_cells, const double* u, double* eta2,
+                        cudaStream_t s);
+void slab_reduce_dev(const MeshDev& m, const double* eta2, const double* phi, double* S,
+                     double* minphi, cudaStream_t s);
+void transfer_dev(int dim, const int* dst_nn, const int* src_nn, const int* const* cell,
+                  const double* const* t, const double* src, int ncomp, double* dst,
+                  cudaStream_t s);
 
 }  // namespace pff
 
@@ -442,8 +454,8 @@ struct pff_problem {
   double *V = nullptr, *Z = nullptr, *w = nullptr, *h = nullptr, *tmp = nullptr;
   float* gs_part = nullptr;   // partial sums of the mixed-precision Gram-Schmidt
   float* Vf = nullptr;        // f32_view of the Krylov basis (mixed Gram-Schmidt)
-  double* pc_tmp = nullptr;
-  double* qp = nullptr;       // per-cell quadrature records (residual, phase-field assembly)   // work vector of the block lower-triangular preconditioner
+  double* pc_tmp = nullptr;   // work vector of the block lower-triangular preconditioner
+  double* qp = nullptr;       // per-cell quadrature records (residual, phase-field assembly)
   // one FGMRES iteration's device work (preconditioner + Jacobian apply) as a
   // CUDA graph on fixed buffers, for problems small enough to be launch-bound
   cudaGraphExec_t iter_graph = nullptr;

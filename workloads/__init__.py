@@ -245,6 +245,26 @@ def cyclic_loading(n_cells: int = 64) -> Workload:
                     pressures=list(CYCLIC_PRESSURES))
 
 
+def adaptive_sneddon2d(n0: int = 32, cycles: int = 6):
+    """Adaptive 2d Sneddon sequence (Section 3 refinement strategy, Section 4.4 study).
+
+    Config 0's geometry and material ([-2,2]^2, l0 = 0.25, p = 1e-3) starting
+    from a uniform n0^2 mesh.  Cycle k solves one loading step with
+    eps_k = 2 h_k, h_k = h_0 / 2^k, and the next mesh keeps the crack region
+    at h <= h_{k+1} (h_band = eps_{k+1} / 2) besides the gradient-jump marking
+    (theta = 0.3, crack region = slabs with min phi < 0.5).  Returns the cycle-0
+    workload and a list of (h_k, eps_k) for k = 0 .. cycles - 1.
+    """
+    ax = uniform_axis(n0, -2.0, 2.0)
+    h0 = 4.0 / n0
+    w = Workload(f"adaptive_sneddon2d_{n0}", 2, [ax, ax.copy()], eps=2.0 * h0)
+    return w, [(h0 / 2 ** k, 2.0 * h0 / 2 ** k) for k in range(cycles)]
+
+
+ADAPT_THETA = 0.3
+ADAPT_PHI_BAND = 0.5
+
+
 def batched_instances(count: int = 256, seed: int = 1806) -> List[Workload]:
     """Independent 2d Sneddon instances of mixed size (seeded, numpy PCG64).
 
