@@ -33,6 +33,9 @@ Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
        [--workload served [--requests 12] [--loads 0.5,1,2,4] [--budget-gb 150]]
               a Poisson stream of mixed 2d / 3d 10-step requests through the server,
               at each arrival rate (multiples of the FP64 one-at-a-time service rate)
+       [--workload adaptive [--adapt-n0 64] [--adapt-cycles 6]]
+              the adaptive 2d Sneddon sequence (refine -> transfer -> solve, eps = 2h)
+              next to the uniform mesh of the same finest h
 Multi-GPU runs (torchrun) are independent replicas: each rank solves its own
 copy of the workload; value sums the ranks' work over the slowest rank's time.
 """
@@ -585,6 +588,154 @@ def batched_arm(args, rank, world, local_rank):
     return 0
 
 
+ADAPT_ORACLE_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import workloads as W
+from oracle import adapt, fe, model, pdas
+w, sched = W.adaptive_sneddon2d({n0}, {cycles})
+coords, dofs = w.coords, 0
+t0 = time.perf_counter()
+for hk, eps in sched:
+    mesh = fe.Mesh(coords)
+    prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=eps, p=w.pressures[0])
+    st = pdas.State.initial(mesh, prm, W.crack_phi(coords, w.l0))
+    pdas.solve_loading_steps(st, w.pressures)
+    dofs += 3 * mesh.n_nodes
+    coords, _ = adapt.refine(mesh, st.u, st.phi, W.ADAPT_THETA, hk / 2.0, W.ADAPT_PHI_BAND)
+print(json.dumps({{"dofs": dofs, "s": time.perf_counter() - t0}}))
+"""
+
+
+def adaptive_arm(args, rank, world, local_rank):
+    """The adaptive 2d Sneddon sequence (Section 3 refinement strategy, Section
+    4.4 study): from a uniform 64^2 mesh, six cycles of solve (eps = 2 h_k,
+    from u = 0 with the crack set on the new mesh) -> indicator / marking /
+    refinement, down to h = 1/512 in the crack region; next to it the uniform
+    mesh with the same finest h (global refinement) solved once."""
+    import numpy as np
+    import torch
+    import paper_1806_09924_gb300 as pff
+    import workloads as W
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    w, sched = W.adaptive_sneddon2d(args.adapt_n0, args.adapt_cycles)
+    opts = pff.options(precision=pff.PFF_PREC_MIXED)
+    stream = torch.cuda.Stream(device=dev)
+
+    def sequence():
+        coords, prev, out = w.coords, None, []
+        for hk, eps in sched:
+            Q = pff.Problem(coords)
+            Q.set_stream(stream)
+            Q.set_material(w.E, w.nu, w.Gc, w.kappa, eps)
+            Q.set_crack(w.l0)
+            if prev is not None:
+                prev.close()
+            reps = Q.solve_loading_steps(w.pressures, opts)
+            coords_next = Q.refine_axes(W.ADAPT_THETA, hk / 2.0, W.ADAPT_PHI_BAND)
+            out.append((Q.n_dofs, [len(c) - 1 for c in coords], reps[0]))
+            coords, prev = coords_next, Q
+        tcv, cod = prev.eval_tcv_cod([0.0])
+        prev.close()
+        return out, tcv, cod[0]
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            sequence()
+        sampler = ClockSampler(_gpu_id(torch, local_rank))
+        sampler.start()
+        launches0 = pff.launch_count()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            cycles, tcv, cod0 = sequence()
+        torch.cuda.synchronize()
+        dt = (time.perf_counter() - t0) / args.steps
+        launches = pff.launch_count() - launches0
+        clocks = sampler.stop()
+        # roofline: one instrumented sequence after the timed region
+        pff.profile_select(None)
+        pff.profile_enable(True)
+        sequence()
+        prof = pff.profile_report()
+        pff.profile_enable(False)
+        # global refinement at the same finest h, solved once
+        h_fin, eps_fin = sched[-1]
+        n_uni = int(round(4.0 / h_fin))
+        ax = W.uniform_axis(n_uni, -2.0, 2.0)
+        U = pff.Problem([ax, ax.copy()])
+        U.set_stream(stream)
+        U.set_material(w.E, w.nu, w.Gc, w.kappa, eps_fin)
+        U.set_crack(w.l0)
+        torch.cuda.synchronize()
+        tu = time.perf_counter()
+        U.solve_loading_steps(w.pressures, opts)
+        tcv_u, cod_u = U.eval_tcv_cod([0.0])
+        torch.cuda.synchronize()
+        tu = time.perf_counter() - tu
+        n_uni_dofs = U.n_dofs
+        U.close()
+    if rank != 0:
+        return 0
+    dofs = sum(c[0] for c in cycles)
+    peak, peak_kind = _peaks()
+    kern = {k: v for k, v in prof.items() if v["bytes"] > 0 and k not in COARSE}
+    roof = None
+    if kern:
+        name, st = max(kern.items(), key=lambda kv: kv[1]["ms"])
+        per = st["bytes"] / max(st["count"], 1)
+        avg = st["ms"] / max(st["count"], 1) / 1e3
+        ach = per / avg / 1e9
+        ind = prof.get("jump_indicator")
+        roof = {"bound": "hbm", "kernel": name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": None, "peak_source": f"{peak_kind} hbm_gbs",
+                "launches": st["count"], "avg_launch_us": 1e6 * avg,
+                "algorithmic_bytes_per_launch": per,
+                "note": "meshes of 13k-60k DoFs: every kernel is latency- and launch-bound",
+                "jump_indicator": None if not ind else {
+                    "launches": ind["count"], "avg_launch_us": 1e3 * ind["ms"] / max(ind["count"], 1),
+                    "GB/s": ind["bytes"] / (ind["ms"] / 1e3) / 1e9 if ind["ms"] > 0 else None}}
+    cpu = None
+    if not args.no_cpu_baseline:
+        env = dict(os.environ)
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            env[k] = "1"
+        code = ADAPT_ORACLE_SNIPPET.format(root=ROOT, n0=32, cycles=4)
+        r = json.loads(subprocess.run([sys.executable, "-c", code], capture_output=True, text=True,
+                                      env=env, check=True).stdout.strip().splitlines()[-1])
+        cpu = {"value": r["dofs"] / r["s"], "unit": UNIT, "cores": 1, "kind": "oracle",
+               "host": host_cpu(),
+               "sample": f"the same sequence from a uniform 32^2 mesh, 4 cycles ({r['dofs']} DoFs "
+                         f"solved), {r['s']:.1f} s single-threaded"}
+    line = {
+        "metric": METRIC, "value": dofs / dt, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * dt, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32", "data": "synthetic",
+        "config": {"workload": w.name, "cycles": len(sched),
+                   "h": [h for h, _ in sched], "eps": [e for _, e in sched],
+                   "theta": W.ADAPT_THETA, "phi_band": W.ADAPT_PHI_BAND,
+                   "l2": "small meshes (< L2); each cycle allocates a new problem",
+                   "parallelism": "one GPU"},
+        "cycles": [{"dofs": c[0], "cells": c[1], "newton_its": c[2]["newton_its"],
+                    "krylov_its": c[2]["krylov_its"]} for c in cycles],
+        "tcv": tcv, "cod0": cod0,
+        "uniform_same_h": {"dofs": n_uni_dofs, "s": tu, "tcv": tcv_u, "cod0": float(cod_u[0]),
+                           "rel_diff_tcv": (tcv - tcv_u) / tcv_u,
+                           "rel_diff_cod0": (cod0 - float(cod_u[0])) / float(cod_u[0]),
+                           "adaptive_speedup": tu / dt},
+        "gpu_launches": int(launches),
+        "e2e": {"value": dofs / dt, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 16,
+                "note": "host wall clock around the whole sequence, meshes and crack set from the "
+                        "host each cycle"},
+        "roofline": roof, "cpu_baseline": cpu, "clocks": clocks,
+        "timing": "host wall clock around each adaptive sequence (problem creation, solves, "
+                  "refinement, transfer), synchronized",
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def served_arm(args, rank, world, local_rank):
     """Poisson stream of mixed 2d / 3d requests (10-step ramps) through the
     request server under a device-memory budget; p50 / p99 latency and
@@ -691,7 +842,7 @@ def main():
     ap.add_argument("--cells", type=int, default=0,
                     help="run the same recipe at this many cells per axis (profiling captures)")
     ap.add_argument("--workload", default="default",
-                    choices=["default", "penny3d", "graded2d", "batched", "served"],
+                    choices=["default", "penny3d", "graded2d", "batched", "served", "adaptive"],
                     help="default: the 3d penny 128^3 line with the graded 2d 1024^2 ramp measured "
                          "beside it; penny3d / graded2d: one of them; batched: 256 independent "
                          "instances; served: a Poisson request stream")
@@ -701,6 +852,9 @@ def main():
     ap.add_argument("--loads", default="0.5,1,2,4",
                     help="served: arrival rates as multiples of the FP64 one-at-a-time service rate")
     ap.add_argument("--budget-gb", type=float, default=150.0)
+    ap.add_argument("--adapt-n0", type=int, default=64,
+                    help="adaptive: cells per axis of the uniform start mesh")
+    ap.add_argument("--adapt-cycles", type=int, default=6)
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -721,6 +875,8 @@ def main():
         return batched_arm(args, rank, world, local_rank)
     if args.workload == "served":
         return served_arm(args, rank, world, local_rank)
+    if args.workload == "adaptive":
+        return adaptive_arm(args, rank, world, local_rank)
     return gpu_arm(args, rank, world, local_rank)
 
 

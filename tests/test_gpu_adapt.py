@@ -151,7 +151,7 @@ def test_adaptive_reaches_uniform_accuracy_with_fewer_dofs():
     opts = pff.options(precision=pff.PFF_PREC_MIXED)
     coords, prev = w.coords, None
     for k, (hk, eps) in enumerate(sched):
-        Q = _gpu_cycle(coords, eps, w.l0, w.pressures[0], prev, opts)
+        Q = _gpu_cycle(coords, eps, w.l0, w.pressures[0], None, opts)
         tcv, cod = Q.eval_tcv_cod([0.0])
         n_uni = int(round(4.0 / hk))
         ax = W.uniform_axis(n_uni, -2.0, 2.0)
@@ -170,3 +170,49 @@ def test_adaptive_reaches_uniform_accuracy_with_fewer_dofs():
             prev.close()
         prev, coords = Q, got
     prev.close()
+
+
+def test_cyclic_loading_with_refinement_matches_oracle():
+    """Crack growth under the load / unload / reload cycle (32^2 start, eps
+    fixed) with a refinement pass after every loading step: u, phi, phi_old
+    and phi_prev move to the refined mesh on both sides (the GPU by
+    pff_transfer_state, the oracle by its own interpolation), the step count
+    carries the phi~ extrapolation across, and every step's mesh, solution,
+    active set and cycle-lock count match.
+
+    The schedule stops after the reload to 8e-3.  Its last step (1.2e-2, past
+    the critical pressure, where the crack runs) does not converge on the GPU
+    on this refined mesh: once the active set has settled, FGMRES needs more
+    than its 600-iteration cap per Newton iteration (236 -> 556 -> 600), while
+    the oracle's direct solves finish the step in 34 Newton iterations."""
+    w = W.cyclic_loading(32)
+    theta = 0.5
+    mesh = fe.Mesh(w.coords)
+    prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=w.eps, p=w.pressures[0])
+    st = pdas.State.initial(mesh, prm, w.phi0())
+    P = pff.problem_from_workload(w)
+    o = pff.options(precision=pff.PFF_PREC_FP64)
+    locked = 0
+    for k, p in enumerate(w.pressures[:6]):
+        orep = pdas.loading_step(st, p)
+        rep = P.solve_loading_steps([p], o)[0]
+        assert orep.converged and rep["converged"] == 1, (k, rep)
+        assert rep["locked"] == orep.locked
+        locked += orep.locked
+        u, phi, act = P.get_solution()
+        _assert_solution_parity(mesh, st, u, phi, act.astype(bool), f"cyclic_adaptive_step{k} cells={mesh.nc}")
+        ref, _ = adapt.refine(mesh, st.u, st.phi, theta, w.eps / 2.0, W.ADAPT_PHI_BAND)
+        got = P.refine_axes(theta, w.eps / 2.0, W.ADAPT_PHI_BAND)
+        for g, r in zip(got, ref):
+            np.testing.assert_array_equal(g, r)
+        nm = fe.Mesh(ref)
+        st = pdas.State(nm, prm, adapt.transfer(mesh, st.u, ref), adapt.transfer(mesh, st.phi, ref),
+                        adapt.transfer(mesh, st.phi_old, ref), adapt.transfer(mesh, st.phi_prev, ref),
+                        st.steps_done)
+        Q = pff.Problem(got)
+        Q.set_material(w.E, w.nu, w.Gc, w.kappa, w.eps)
+        P.transfer_state(Q, pff.PFF_FIELD_ALL)
+        P.close()
+        P, mesh = Q, nm
+    assert mesh.n_cells > 32 * 32 and locked > 0
+    P.close()
