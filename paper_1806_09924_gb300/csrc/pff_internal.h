@@ -218,6 +218,13 @@ struct AmgParams {
   double mdrop = 1e-3;
   bool use_graph = true;
   int spmv_group = 0;         // Bsr::group of every level's A, P and R
+  // the finest level's assembled node stencil (slot-major, A's block size; the
+  // FP32 copy in the layout stf_node_major names): when given, the Lanczos
+  // estimate of that level applies it instead of the BSR copy
+  MeshDev mesh{};
+  const double* st = nullptr;
+  const float* stf = nullptr;
+  bool stf_node_major = false;
 };
 
 // Build a hierarchy for the block matrix A (FP64 values, block size br) with

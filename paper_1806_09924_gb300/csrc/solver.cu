@@ -312,18 +312,30 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
   ap.spmv_group = o.spmv_group;
   const auto m = P->mesh();
   const int64_t n = P->n_nodes;
-  // the finest level of each hierarchy smooths on the assembled stencil itself
-  auto use_stencil = [&](Amg& amg, const double* K, float*& Kf, int b) {
+  // the finest level of each hierarchy smooths on the assembled stencil itself;
+  // its FP32 copy (mixed precision) is made before a build, whose Lanczos
+  // estimate of the finest level then applies the stencil too
+  auto convert_stencil = [&](const double* K, float*& Kf, int b) {
+    if (!ap.mixed) return;
+    if (!Kf) Kf = dalloc<float>(stencil_f32_count(P->dim, b, n));
+    if (P->dim == 2 && b == 2) stencil_to_node_major(K, Kf, n, P->stream);
+    else stencil_to_f32(P->dim, b, K, Kf, n, P->stream);
+  };
+  auto with_stencil = [&](AmgParams q, const double* K, const float* Kf, int b) {
+    q.mesh = m;
+    q.st = K;
+    q.stf = ap.mixed ? Kf : nullptr;
+    q.stf_node_major = P->dim == 2 && b == 2;
+    return q;
+  };
+  auto use_stencil = [&](Amg& amg, const double* K, const float* Kf, int b) {
     if (amg.lev.empty()) return;
     AmgLevel& L0 = amg.lev[0];
     L0.stencil = true;
     L0.mesh = m;
     L0.st = K;
     if (ap.mixed) {
-      if (!Kf) Kf = dalloc<float>(stencil_f32_count(P->dim, b, n));
       L0.stf_node_major = P->dim == 2 && b == 2;
-      if (L0.stf_node_major) stencil_to_node_major(K, Kf, n, P->stream);
-      else stencil_to_f32(P->dim, b, K, Kf, n, P->stream);
       L0.stf = Kf;
     }
   };
@@ -346,6 +358,7 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     if (reuse_u) {
       AmgLevel& L0 = P->amg_u.lev[0];
       launch_stencil_dinv(m, n, P->dim, P->Kuu, L0.dinv, ap.mixed ? L0.dinvf : nullptr, P->stream);
+      convert_stencil(P->Kuu, P->Kuu_f, P->dim);
       use_stencil(P->amg_u, P->Kuu, P->Kuu_f, P->dim);
       P->amg_u_age += 1;
     }
@@ -357,7 +370,8 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     // near-null space: the rigid-body modes (translations first in Bu), or translations only
     const bool rot = o.amg_rotations < 0 ? P->dim == 2 : o.amg_rotations == 1;
     const int nns = rot ? (P->dim == 2 ? 3 : 6) : P->dim;
-    amg_build(P->amg_u, P->Auu, P->Bu, nns, ap, P->stream);
+    convert_stencil(P->Kuu, P->Kuu_f, P->dim);
+    amg_build(P->amg_u, P->Auu, P->Bu, nns, with_stencil(ap, P->Kuu, P->Kuu_f, P->dim), P->stream);
     use_stencil(P->amg_u, P->Kuu, P->Kuu_f, P->dim);
     if (!P->phit_built) P->phit_built = dalloc<double>(n);
     PFF_CUDA(cudaMemcpyAsync(P->phit_built, P->phit, sizeof(double) * n, cudaMemcpyDeviceToDevice,
@@ -378,10 +392,11 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
                  P->amg_p.mixed != ap.mixed || P->phi_amg_age >= o.amg_age_phi ||
                  P->amg_p.lev.empty() || !P->active_built;
   if (!rebuild) rebuild = (double)count_diff(P, P->active, P->active_built, n) > o.amg_rebuild_phi * n;
+  convert_stencil(P->Kpp, P->Kpp_f, 1);
   if (rebuild) {
     ProfScope ps("amg_setup_phi", 0.0, P->stream, 0);
     launch_stencil_to_bsr(m, n, 1, P->Kpp, P->App, P->stream);
-    AmgParams app = ap;
+    AmgParams app = with_stencil(ap, P->Kpp, P->Kpp_f, 1);
     if (o.amg_levels_phi > 0) app.max_levels = o.amg_levels_phi - 1;
     if (o.cheb_degree_phi > 0) app.cheb_degree = o.cheb_degree_phi;
     amg_build(P->amg_p, P->App, P->Bp, 1, app, P->stream);

@@ -585,15 +585,20 @@ np.savez({out!r}, u=u, phi=phi, act=act)
 def test_element_tiles_do_not_change_results(tmp_path):
     """The element kernels (residual, assembly, assembled apply) give bit-identical
     results whatever tile the autotuner picks: one 3d solve with each tile forced
-    (PFF_ELEM_TILE, read once per process, so each runs in a child process)."""
+    (PFF_ELEM_TILE, read once per process, so each runs in a child process).
+    The two children share a tuning record, so that the other timed choices
+    (sparse-kernel variants, which sum in different orders, and the apply
+    variant) are the same in both: on matrices this small their timings are
+    within noise and may fall either way in two processes."""
     import os
     import subprocess
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     res = []
+    rec = str(tmp_path / "tune.txt")
     for tile in (64, 256):
         out = str(tmp_path / f"tile{tile}.npz")
-        env = dict(os.environ, PFF_ELEM_TILE=str(tile))
+        env = dict(os.environ, PFF_ELEM_TILE=str(tile), PFF_TUNE_CACHE=rec)
         subprocess.run([sys.executable, "-c", _TILE_CHILD.format(root=root, out=out)], env=env,
                        check=True, timeout=600)
         res.append(np.load(out))
