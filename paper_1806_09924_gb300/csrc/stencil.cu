@@ -4,6 +4,11 @@
 // node-major FP32 copy of the 2d displacement stencil and the inverse
 // diagonals.  These are the bandwidth-bound kernels of every V-cycle (Section
 // 3.1: block-diagonal AMG preconditioner), kept in a file of their own.
+#include <cstdio>
+#include <cstdlib>
+#include <map>
+#include <mutex>
+
 #include "pff_internal.h"
 
 namespace pff {
@@ -33,6 +38,44 @@ template <bool SK, class T>
 __device__ __forceinline__ T ld_stencil(const T* p) {
   if constexpr (SK) return __ldcs(p);
   else return *p;
+}
+
+// Explicitly rounded arithmetic (no contraction left to the compiler): the
+// kernel variants of one step then produce bit-identical results.
+__device__ __forceinline__ float rn_mul(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double rn_mul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float rn_add(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double rn_add(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float rn_sub(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ double rn_sub(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ float rn_fma(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ double rn_fma(double a, double b, double c) { return __fma_rn(a, b, c); }
+
+// One Chebyshev update of component r: res = dinv (b - acc), d = cd d + cr res,
+// x_out = x_in + d (zero start: d = cr res, x_out = d).
+template <class T>
+__device__ __forceinline__ void cheb_update(int64_t r, T acc, const T* __restrict__ dinv,
+                                            const T* __restrict__ rhs, const T* __restrict__ xin,
+                                            T* __restrict__ xout, T* __restrict__ d, T cd, T cr,
+                                            int zero_x, const double* __restrict__ rhs64,
+                                            T* __restrict__ rhs_store, double* __restrict__ out64) {
+  T bv;
+  if (rhs64) {
+    bv = (T)rhs64[r];
+    rhs_store[r] = bv;
+  } else {
+    bv = rhs[r];
+  }
+  const T res = rn_mul(dinv[r], rn_sub(bv, acc));
+  const T crr = rn_mul(cr, res);
+  const T dn = zero_x ? crr : rn_fma(cd, d[r], crr);
+  const T xo = zero_x ? dn : rn_add(xin[r], dn);
+  if (out64) {
+    out64[r] = (double)xo;
+  } else {
+    d[r] = dn;
+    xout[r] = xo;
+  }
 }
 
 template <class T, int D, int B, bool SK>
@@ -72,7 +115,7 @@ __device__ __forceinline__ void stencil_apply(const MeshDev& m, int64_t n, int i
         if (!HALF) k = ld_stencil<SK>(K + ((int64_t)(s * B + a) * B + c) * n + i);
         else if (s >= C) k = ld_stencil<SK>(K + ((int64_t)((s - C) * B + a) * B + c) * n + i);
         else k = ld_stencil<SK>(K + ((int64_t)((NS - 1 - s - C) * B + c) * B + a) * n + j);
-        acc[a] += (ok ? k : T(0)) * xj[c];
+        acc[a] = rn_fma(ok ? k : T(0), xj[c], acc[a]);
       }
   }
 }
@@ -117,25 +160,9 @@ __global__ void __launch_bounds__(StencilShape<D, B>::threads, StencilShape<D, B
     stencil_apply<T, D, B, SK>(m, n, i, K, xin, acc);
   }
 #pragma unroll
-  for (int a = 0; a < B; ++a) {
-    const int64_t r = (int64_t)i * B + a;
-    T bv;
-    if (rhs64) {
-      bv = (T)rhs64[r];
-      rhs_store[r] = bv;
-    } else {
-      bv = rhs[r];
-    }
-    const T res = dinv[r] * (bv - acc[a]);
-    const T dn = (zero_x ? T(0) : cd * d[r]) + cr * res;
-    const T xo = (zero_x ? T(0) : xin[r]) + dn;
-    if (out64) {
-      out64[r] = (double)xo;
-    } else {
-      d[r] = dn;
-      xout[r] = xo;
-    }
-  }
+  for (int a = 0; a < B; ++a)
+    cheb_update<T>((int64_t)i * B + a, acc[a], dinv, rhs, xin, xout, d, cd, cr, zero_x, rhs64,
+                   rhs_store, out64);
 }
 
 // 2d displacement block in FP32 with the node-major layout Kq[(h n + i) * 4 + 2a + c]
@@ -262,7 +289,68 @@ __global__ void __launch_bounds__(StencilShape<D, B>::threads, StencilShape<D, B
   T acc[B];
   stencil_apply<T, D, B, SK>(m, n, i, K, x, acc);
 #pragma unroll
-  for (int a = 0; a < B; ++a) r[(int64_t)i * B + a] = rhs[(int64_t)i * B + a] - acc[a];
+  for (int a = 0; a < B; ++a) r[(int64_t)i * B + a] = rn_sub(rhs[(int64_t)i * B + a], acc[a]);
+}
+
+// 3d displacement block in FP32, one output component per warp ("rows"): the
+// three warps of a group of 32 nodes compute rows a = 0, 1, 2 of the same 32
+// nodes.  Each thread then carries one accumulator and 27 x 3 stencil loads
+// instead of 3 accumulators and 27 x 9 loads, so four times as many threads
+// fit in the register file and more loads are in flight per SM; the three
+// warps read the same x values (from L1).  Every row accumulates its products
+// in the same order as the node-per-thread kernel, so both give bit-identical
+// results.  RESID: out = rhs - K x; otherwise one Chebyshev step.
+constexpr int ROWS_GROUPS = 4;                 // groups of 32 nodes per block
+constexpr int ROWS_THREADS = 96 * ROWS_GROUPS;
+
+template <bool RESID, bool SK, int MINB>
+__global__ void __launch_bounds__(ROWS_THREADS, MINB)
+    k_stencil_rows3(MeshDev m, int n, const float* __restrict__ K, const float* __restrict__ dinv,
+                    const float* __restrict__ rhs, const float* __restrict__ xin,
+                    float* __restrict__ out, float* __restrict__ d, float cd, float cr, int zero_x,
+                    const double* __restrict__ rhs64, float* __restrict__ rhs_store,
+                    double* __restrict__ out64) {
+  constexpr int NS = 27, C = 13, B = 3;
+  const int w = threadIdx.x >> 5;
+  const int a = w % 3;
+  const int i = (blockIdx.x * ROWS_GROUPS + w / 3) * 32 + (threadIdx.x & 31);
+  if (i >= n) return;
+  float acc = 0.f;
+  if (RESID || !zero_x) {
+    const int n0 = m.nn[0], n1 = m.nn[1];
+    const int ix = i % n0;
+    const int r = i / n0;
+    const int iy = r % n1, iz = r / n1;
+    const bool lo[3] = {ix > 0, iy > 0, iz > 0};
+    const bool hi[3] = {ix < n0 - 1, iy < n1 - 1, iz < m.nn[2] - 1};
+#pragma unroll
+    for (int s = 0; s < NS; ++s) {
+      const int ox = s % 3 - 1, oy = (s / 3) % 3 - 1, oz = s / 9 - 1;
+      const bool ok = (ox < 0 ? lo[0] : ox > 0 ? hi[0] : true) &&
+                      (oy < 0 ? lo[1] : oy > 0 ? hi[1] : true) &&
+                      (oz < 0 ? lo[2] : oz > 0 ? hi[2] : true);
+      const int j = ok ? i + ox + oy * n0 + oz * n0 * n1 : i;
+      float xj[B];
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        const float v = xin[(int64_t)j * B + c];
+        xj[c] = ok ? v : 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < B; ++c) {
+        float k;
+        if (s >= C) k = ld_stencil<SK>(K + ((int64_t)((s - C) * B + a) * B + c) * n + i);
+        else k = ld_stencil<SK>(K + ((int64_t)((NS - 1 - s - C) * B + c) * B + a) * n + j);
+        acc = rn_fma(ok ? k : 0.f, xj[c], acc);
+      }
+    }
+  }
+  const int64_t r = (int64_t)i * B + a;
+  if (RESID) {
+    out[r] = rn_sub(rhs[r], acc);
+    return;
+  }
+  cheb_update<float>(r, acc, dinv, rhs, xin, out, d, cd, cr, zero_x, rhs64, rhs_store, out64);
 }
 
 // inverse diagonal of a node stencil (block size B, centre slot c0)
@@ -290,6 +378,137 @@ inline double slots_stored(int d, size_t es) { return es == 4 ? (NSd(d) + 1.0) /
 // 2.7 times the L2)
 bool stream_stencil(int d, int b, size_t es, int64_t n) {
   return slots_stored(d, es) * b * b * es * (double)n <= (double)l2_cache_bytes();
+}
+}  // namespace
+
+namespace {
+// Kernel variant of the 3d FP32 displacement steps: node per thread (0) or
+// component rows with 4 (1) or 3 (2) resident blocks of 384 threads per SM
+// (at most 40 or 56 registers).  Chosen per operation (Chebyshev step or
+// residual) and size class at the first call outside a stream capture by
+// timing each variant on scratch vectors (the results are bit-identical, only
+// the speed differs); PFF_STENCIL_VARIANT = 0 | 1 | 2 forces one.  The choice
+// goes to the tuning record (PFF_TUNE_CACHE).
+constexpr int N_VARIANTS = 3;
+std::mutex g_variant_mu;
+std::map<std::pair<int, int>, int> g_variant;   // (op: 0 Chebyshev, 1 residual, size class) -> variant
+
+int forced_variant() {
+  static const int f = [] {
+    const char* e = std::getenv("PFF_STENCIL_VARIANT");
+    if (!e) return -1;
+    const int v = std::atoi(e);
+    return v >= 0 && v < N_VARIANTS ? v : -1;
+  }();
+  return f;
+}
+
+template <bool RESID, int MINB>
+void launch_rows3_b(const MeshDev& m, int64_t n, const float* K, const float* dinv, const float* rhs,
+                    const float* xin, float* out, float* d, float cd, float cr, int zero_x,
+                    const double* rhs64, float* rhs_store, double* out64, cudaStream_t s) {
+  const unsigned g = grid_for(n, 32 * ROWS_GROUPS);
+  if (stream_stencil(3, 3, 4, n))
+    k_stencil_rows3<RESID, true, MINB><<<g, ROWS_THREADS, 0, s>>>(m, (int)n, K, dinv, rhs, xin, out, d,
+                                                                cd, cr, zero_x, rhs64, rhs_store, out64);
+  else
+    k_stencil_rows3<RESID, false, MINB><<<g, ROWS_THREADS, 0, s>>>(m, (int)n, K, dinv, rhs, xin, out, d,
+                                                                 cd, cr, zero_x, rhs64, rhs_store, out64);
+}
+
+// variant 1 or 2
+template <bool RESID>
+void launch_rows3(int variant, const MeshDev& m, int64_t n, const float* K, const float* dinv,
+                  const float* rhs, const float* xin, float* out, float* d, float cd, float cr,
+                  int zero_x, const double* rhs64, float* rhs_store, double* out64, cudaStream_t s) {
+  if (variant == 1)
+    launch_rows3_b<RESID, 4>(m, n, K, dinv, rhs, xin, out, d, cd, cr, zero_x, rhs64, rhs_store, out64, s);
+  else
+    launch_rows3_b<RESID, 3>(m, n, K, dinv, rhs, xin, out, d, cd, cr, zero_x, rhs64, rhs_store, out64, s);
+}
+
+int rows_variant(bool resid, const MeshDev& m, int64_t n, const float* K, cudaStream_t s) {
+  const int f = forced_variant();
+  if (f >= 0) return f;
+  int cls = 0;
+  while (cls < 62 && (int64_t(1) << (cls + 1)) <= n) ++cls;
+  const auto key = std::make_pair(resid ? 1 : 0, cls);
+  {
+    std::lock_guard<std::mutex> g(g_variant_mu);
+    auto it = g_variant.find(key);
+    if (it != g_variant.end()) return it->second;
+  }
+  char rkey[64];
+  std::snprintf(rkey, sizeof(rkey), "stencil_rows:%s:3:3:%d", resid ? "resid" : "cheb", cls);
+  int recorded = 0;
+  if (tune_lookup(rkey, &recorded) && recorded >= 0 && recorded < N_VARIANTS) {
+    std::lock_guard<std::mutex> g(g_variant_mu);
+    g_variant[key] = recorded;
+    return recorded;
+  }
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(s, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return 0;   // no timing inside a capture; decided at the next uncaptured call
+  }
+  // scratch x, rhs, output, inverse diagonal and Chebyshev direction (zeros)
+  float* x = dalloc<float>(3 * n);
+  float* b = dalloc<float>(3 * n);
+  float* r = dalloc<float>(3 * n);
+  float* dv = dalloc<float>(3 * n);
+  float* dd = dalloc<float>(3 * n);
+  for (float* v : {x, b, dv, dd}) PFF_CUDA(cudaMemsetAsync(v, 0, sizeof(float) * 3 * n, s));
+  cudaEvent_t e0, e1;
+  PFF_CUDA(cudaEventCreate(&e0));
+  PFF_CUDA(cudaEventCreate(&e1));
+  float ms[N_VARIANTS] = {0.f, 0.f, 0.f};
+  for (int v = 0; v < N_VARIANTS; ++v) {
+    auto run = [&]() {
+      const unsigned g = grid_for(n, StencilShape<3, 3>::threads);
+      constexpr int tb = StencilShape<3, 3>::threads;
+      const bool sk = stream_stencil(3, 3, 4, n);
+      if (resid) {
+        if (v > 0)
+          launch_rows3<true>(v, m, n, K, nullptr, b, x, r, nullptr, 0.f, 0.f, 0, nullptr, nullptr, nullptr, s);
+        else if (sk)
+          k_stencil_resid<float, 3, 3, true><<<g, tb, 0, s>>>(m, n, K, b, x, r);
+        else
+          k_stencil_resid<float, 3, 3, false><<<g, tb, 0, s>>>(m, n, K, b, x, r);
+      } else {
+        if (v > 0)
+          launch_rows3<false>(v, m, n, K, dv, b, x, r, dd, 0.5f, 0.5f, 0, nullptr, nullptr, nullptr, s);
+        else if (sk)
+          k_stencil_cheb<float, 3, 3, true><<<g, tb, 0, s>>>(m, n, K, dv, b, x, r, dd, 0.5f, 0.5f, 0,
+                                                              nullptr, nullptr, nullptr);
+        else
+          k_stencil_cheb<float, 3, 3, false><<<g, tb, 0, s>>>(m, n, K, dv, b, x, r, dd, 0.5f, 0.5f, 0,
+                                                               nullptr, nullptr, nullptr);
+      }
+    };
+    run();   // warm
+    PFF_CUDA(cudaEventRecord(e0, s));
+    run();
+    run();
+    PFF_CUDA(cudaEventRecord(e1, s));
+    PFF_CUDA(cudaEventSynchronize(e1));
+    PFF_LAUNCH("stencil variant tuning");
+    PFF_CUDA(cudaEventElapsedTime(&ms[v], e0, e1));
+  }
+  count_launch(3 * N_VARIANTS);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (float* v : {x, b, r, dv, dd}) dfree(v);
+  int best = 0;
+  for (int v = 1; v < N_VARIANTS; ++v)
+    if (ms[v] < ms[best]) best = v;
+  if (verbose())
+    std::fprintf(stderr, "[pff] stencil variant 3d %s n=%lld: node %.2f us, rows/4 %.2f us, rows/3 %.2f us -> %d\n",
+                 resid ? "residual" : "Chebyshev", (long long)n, 500.0f * ms[0], 500.0f * ms[1],
+                 500.0f * ms[2], best);
+  tune_store(rkey, best);
+  std::lock_guard<std::mutex> g(g_variant_mu);
+  g_variant[key] = best;
+  return best;
 }
 }  // namespace
 
@@ -339,6 +558,15 @@ void launch_stencil_cheb(const MeshDev& m, int64_t n, int b, const T* K, const T
       return;
     }
   }
+  if constexpr (sizeof(T) == 4) {
+    const int v = m.dim == 3 && b == 3 ? rows_variant(false, m, n, K, s) : 0;
+    if (v > 0) {
+      launch_rows3<false>(v, m, n, K, dinv, rhs, xin, xout, d, (float)cd, (float)cr, zero_x, rhs64,
+                          rhs_store, out64, s);
+      PFF_LAUNCH("stencil_cheb");
+      return;
+    }
+  }
   STENCIL_DISPATCH(m.dim, b, k_stencil_cheb, m, n, K, dinv, rhs, xin, xout, d, (T)cd, (T)cr, zero_x,
                    rhs64, rhs_store, out64);
   PFF_LAUNCH("stencil_cheb");
@@ -358,6 +586,14 @@ void launch_stencil_resid(const MeshDev& m, int64_t n, int b, const T* K, const 
         k_stencil_resid_q2<true><<<g, Q2_BLK, 0, s>>>(m, (int)n, K, rhs, x, r);
       else
         k_stencil_resid_q2<false><<<g, Q2_BLK, 0, s>>>(m, (int)n, K, rhs, x, r);
+      PFF_LAUNCH("stencil_resid");
+      return;
+    }
+  }
+  if constexpr (sizeof(T) == 4) {
+    const int v = m.dim == 3 && b == 3 ? rows_variant(true, m, n, K, s) : 0;
+    if (v > 0) {
+      launch_rows3<true>(v, m, n, K, nullptr, rhs, x, r, nullptr, 0.f, 0.f, 0, nullptr, nullptr, nullptr, s);
       PFF_LAUNCH("stencil_resid");
       return;
     }

@@ -606,6 +606,29 @@ def test_element_tiles_do_not_change_results(tmp_path):
         assert np.array_equal(res[0][k], res[1][k]), k
 
 
+def test_stencil_variants_do_not_change_results(tmp_path):
+    """The 3d displacement smoother and residual have three kernel variants
+    (node per thread; component rows with 4 or 3 resident blocks per SM) that
+    accumulate in the same order: one 3d mixed-precision solve with each forced
+    (PFF_STENCIL_VARIANT, read once per process) gives bit-identical results.
+    The children share a tuning record, as in the element-tile test."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    rec = str(tmp_path / "tune.txt")
+    res = []
+    for v in (0, 1, 2):
+        out = str(tmp_path / f"variant{v}.npz")
+        env = dict(os.environ, PFF_STENCIL_VARIANT=str(v), PFF_TUNE_CACHE=rec)
+        subprocess.run([sys.executable, "-c", _TILE_CHILD.format(root=root, out=out)], env=env,
+                       check=True, timeout=600)
+        res.append(np.load(out))
+    for r in res[1:]:
+        for k in ("u", "phi", "act"):
+            assert np.array_equal(res[0][k], r[k]), k
+
+
 def test_tuning_record_replays_the_same_choices(tmp_path):
     """PFF_TUNE_CACHE: a first process records every autotuner choice (sparse
     formats, element tiles, apply variant); a second process with the same file
