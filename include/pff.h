@@ -122,7 +122,11 @@ typedef struct pff_options {
   int amg_age_phi;      /* ... or once it has served this many Newton iterations; 8 */
   int amg_levels_phi;   /* at most this many levels in the phase-field hierarchy, the last
                            one smoothing only (1: Chebyshev smoothing on the assembled
-                           stencil, no coarse levels); 0 = coarsen down to amg_coarse_max; 1 */
+                           stencil, no coarse levels); 0 = coarsen down to amg_coarse_max;
+                           -1 = by resolution: 1 while the smallest cell is at least eps/4
+                           (the block is dominated by its mass term G_c/eps M), else 0
+                           (finer cells: its eps-scaled Laplacian takes over, which
+                           smoothing alone resolves poorly); -1 */
   int cheb_degree_phi;  /* Chebyshev degree on the finest level of the phase-field block;
                            0 = cheb_degree; 4 */
   int amg_rotations;    /* near-null space of the displacement hierarchy: 1 = rigid-body

@@ -271,7 +271,7 @@ pff_options resolve_options(const pff_options* opts) {
   need(o.amg_reuse_tol >= 0.0, "negative amg_reuse_tol");
   need(o.forcing_max >= 0.0 && o.forcing_max < 1.0, "forcing_max must be in [0, 1)");
   need(o.amg_rebuild_phi >= 0.0 && o.amg_age_phi >= 1, "amg_rebuild_phi < 0 or amg_age_phi < 1");
-  need(o.amg_levels_phi >= 0, "amg_levels_phi must be >= 0");
+  need(o.amg_levels_phi >= -1, "amg_levels_phi must be >= -1");
   need(o.cheb_degree_phi >= 0, "cheb_degree_phi must be >= 0");
   need(o.amg_rotations >= -1 && o.amg_rotations <= 1, "amg_rotations must be -1, 0 or 1");
   need(o.cheb_degree_coarse >= -1, "cheb_degree_coarse must be >= -1");
@@ -303,7 +303,7 @@ void pff_default_options(pff_options* o) {
   o->cheb_degree = 4;
   o->cheb_degree_coarse = -1;
   o->cheb_degree_phi = 4;
-  o->amg_levels_phi = 1;
+  o->amg_levels_phi = -1;
   o->amg_rotations = -1;
   o->amg_theta = 0.02;
   o->amg_coarse_max = 1000;

@@ -397,7 +397,18 @@ void precond_setup(pff_problem* P, const pff_options& o, bool allow_reuse) {
     ProfScope ps("amg_setup_phi", 0.0, P->stream, 0);
     launch_stencil_to_bsr(m, n, 1, P->Kpp, P->App, P->stream);
     AmgParams app = with_stencil(ap, P->Kpp, P->Kpp_f, 1);
-    if (o.amg_levels_phi > 0) app.max_levels = o.amg_levels_phi - 1;
+    // -1: smoothing only while the mass term G_c/eps M dominates the block (cells of
+    // at least eps/4; the workloads here have eps = 2-4 h_min), the full hierarchy on
+    // meshes refined below that (measured: a refined 32^2 cyclic-loading step past
+    // the critical pressure needs it, FGMRES stalls at its cap with smoothing only)
+    int levels_phi = o.amg_levels_phi;
+    if (levels_phi < 0) {
+      double hmin = INFINITY;
+      for (int a = 0; a < P->dim; ++a)
+        for (size_t i = 0; i + 1 < P->hX[a].size(); ++i) hmin = std::min(hmin, P->hX[a][i + 1] - P->hX[a][i]);
+      levels_phi = hmin >= 0.25 * P->mat.eps ? 1 : 0;
+    }
+    if (levels_phi > 0) app.max_levels = levels_phi - 1;
     if (o.cheb_degree_phi > 0) app.cheb_degree = o.cheb_degree_phi;
     amg_build(P->amg_p, P->App, P->Bp, 1, app, P->stream);
     P->cur.amg_builds_phi += 1;

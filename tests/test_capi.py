@@ -80,7 +80,7 @@ def test_defaults_and_argument_errors_without_gpu(lib):
     assert o.spmv_group == 0 and o.amg_reuse == 1 and o.amg_reuse_tol == 0.05
     assert o.precond_overlap == 1 and o.iter_graph == 1 and o.cheb_degree_coarse == -1
     assert o.amg_rotations == -1
-    assert o.cheb_degree == 4 and o.cheb_degree_phi == 4 and o.amg_levels_phi == 1
+    assert o.cheb_degree == 4 and o.cheb_degree_phi == 4 and o.amg_levels_phi == -1
     assert o.amg_coarse_max == 1000
     assert o.forcing_max == 0.0
     assert o.amg_rebuild_phi == 1e-3 and o.amg_age_phi == 8
@@ -133,7 +133,7 @@ def test_option_ranges_without_gpu(lib):
     bad = [dict(precision=7), dict(krylov_restart=0), dict(cheb_degree=0), dict(max_newton=-1),
            dict(tol_change=-1.0), dict(amg_reuse_tol=-0.1), dict(forcing_max=1.0), dict(precond=9),
            dict(spmv_group=3), dict(amg_rebuild_phi=-1e-3), dict(amg_age_phi=0),
-           dict(amg_levels_phi=-1), dict(cheb_degree_phi=-1), dict(amg_rotations=2),
+           dict(amg_levels_phi=-2), dict(cheb_degree_phi=-1), dict(amg_rotations=2),
            dict(amg_rotations=-2), dict(cheb_degree_coarse=-2)]
     for kw in bad:
         with pytest.raises(pff.PffError) as e:

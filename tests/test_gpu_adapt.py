@@ -180,11 +180,12 @@ def test_cyclic_loading_with_refinement_matches_oracle():
     carries the phi~ extrapolation across, and every step's mesh, solution,
     active set and cycle-lock count match.
 
-    The schedule stops after the reload to 8e-3.  Its last step (1.2e-2, past
-    the critical pressure, where the crack runs) does not converge on the GPU
-    on this refined mesh: once the active set has settled, FGMRES needs more
-    than its 600-iteration cap per Newton iteration (236 -> 556 -> 600), while
-    the oracle's direct solves finish the step in 34 Newton iterations."""
+    The refinement takes the cells below eps/4, where the phase-field block's
+    Laplacian dominates its mass term; the default phase-field preconditioner
+    then switches from smoothing to the full hierarchy.  With smoothing only,
+    the last step (1.2e-2, past the critical pressure, where the crack runs)
+    stalled FGMRES at its 600-iteration cap; with the hierarchy it takes 34
+    Newton iterations, as in the oracle."""
     w = W.cyclic_loading(32)
     theta = 0.5
     mesh = fe.Mesh(w.coords)
@@ -193,7 +194,7 @@ def test_cyclic_loading_with_refinement_matches_oracle():
     P = pff.problem_from_workload(w)
     o = pff.options(precision=pff.PFF_PREC_FP64)
     locked = 0
-    for k, p in enumerate(w.pressures[:6]):
+    for k, p in enumerate(w.pressures):
         orep = pdas.loading_step(st, p)
         rep = P.solve_loading_steps([p], o)[0]
         assert orep.converged and rep["converged"] == 1, (k, rep)
