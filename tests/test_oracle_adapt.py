@@ -219,3 +219,34 @@ def test_transfer_keeps_bounds_and_irreversibility():
     assert np.all(p <= po + 1e-15) and np.all(p >= 0) and np.all(po <= 1)
     with pytest.raises(ValueError):
         adapt.transfer(m, phi, [np.append(new[0], new[0][-1] + 1.0), new[1]])
+
+
+def test_adaptive_sequence_tracks_global_refinement():
+    """Section 4.4 on the oracle alone: the adaptive Sneddon sequence (eps = 2 h_k,
+    crack region refined to h_k, gradient-jump marking) gives TCV and COD(0)
+    within 0.5 % of the uniform mesh with the same finest h, at a fraction of
+    its unknowns."""
+    import workloads as W
+    from oracle import functionals as fn, model, pdas
+    w, sched = W.adaptive_sneddon2d(32, 3)
+    coords = w.coords
+    for k, (hk, eps) in enumerate(sched):
+        prm = model.Params(E=w.E, nu=w.nu, Gc=w.Gc, kappa=w.kappa, eps=eps, p=w.pressures[0])
+        mesh = fe.Mesh(coords)
+        st = pdas.State.initial(mesh, prm, W.crack_phi(coords, w.l0))
+        assert all(r.converged for r in pdas.solve_loading_steps(st, w.pressures))
+        tcv, cod0 = fn.tcv(mesh, st.u, st.phi), fn.cod(mesh, st.u, st.phi, [0.0])[0]
+        if k > 0:
+            n = int(round(4.0 / hk))
+            ax = W.uniform_axis(n, -2.0, 2.0)
+            um = fe.Mesh([ax, ax.copy()])
+            su = pdas.State.initial(um, prm, W.crack_phi([ax, ax], w.l0))
+            pdas.solve_loading_steps(su, w.pressures)
+            tcv_u, cod_u = fn.tcv(um, su.u, su.phi), fn.cod(um, su.u, su.phi, [0.0])[0]
+            assert abs(tcv - tcv_u) <= 5e-3 * tcv_u and abs(cod0 - cod_u) <= 5e-3 * cod_u
+            assert mesh.n_nodes < (0.4 if k == 1 else 0.2) * um.n_nodes
+            # the crack region is resolved to h_k
+            P = adapt.slab_min_phi(mesh, st.phi)
+            for a in range(2):
+                assert np.all(np.diff(coords[a])[P[a] < W.ADAPT_PHI_BAND] <= hk * (1 + 1e-12))
+        coords, _ = adapt.refine(mesh, st.u, st.phi, W.ADAPT_THETA, hk / 2.0, W.ADAPT_PHI_BAND)
