@@ -27,6 +27,10 @@ estimator or marking rule.  These functions state the readings used here:
 
 The face integrals use the 2^(d-1)-point Gauss rule on the face, exact for the
 squared jump of a Q1 gradient (degree 2 in each face coordinate).
+
+Parity unpinned against the paper for the readings themselves (the paper prints
+neither the estimator nor the marking rule); the functions are pinned to these
+definitions by closed forms and brute force in tests/test_oracle_adapt.py.
 """
 from __future__ import annotations
 
