@@ -302,6 +302,15 @@ int pff_cell_indicators_dev(pff_problem* prob, double* eta2_dev);
 int pff_refine_axes(pff_problem* prob, double theta, double h_band, double phi_band,
                     int32_t* n_cells_out, double* const* coords_out);
 
+/* The marking and splitting step of pff_refine_axes on host arrays, without a
+ * problem or a device: for callers that form the slab quantities themselves.
+ * Per axis a (dim of them): coords[a] (n_cells[a] + 1 strictly increasing
+ * values), slab_eta2[a] and slab_minphi[a] (n_cells[a] values each); outputs
+ * as for pff_refine_axes.  All arrays host, caller-owned. */
+int pff_mark_axes(int dim, const int32_t* n_cells, const double* const* coords,
+                  const double* const* slab_eta2, const double* const* slab_minphi, double theta,
+                  double h_band, double phi_band, int32_t* n_cells_out, double* const* coords_out);
+
 /* Move nodal fields of src onto the nodes of dst by Q1 interpolation (the
  * finite element function of src evaluated at dst's nodes; each value is the
  * corner sum of prod(t or 1 - t) times the corner values, in corner order,

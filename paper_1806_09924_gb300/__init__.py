@@ -150,6 +150,10 @@ _SIGS = {
     "pff_refine_axes": (ctypes.c_int, [_P, ctypes.c_double, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_D)]),
     "pff_transfer_state": (ctypes.c_int, [_P, _P, ctypes.c_int]),
+    "pff_mark_axes": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(_D),
+                                     ctypes.POINTER(_D), ctypes.POINTER(_D), ctypes.c_double,
+                                     ctypes.c_double, ctypes.c_double, ctypes.POINTER(ctypes.c_int32),
+                                     ctypes.POINTER(_D)]),
     "pff_batch_solve": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(ctypes.c_int),
                                        ctypes.POINTER(_D), ctypes.POINTER(PffOptions),
                                        ctypes.POINTER(ctypes.POINTER(PffStepReport)), ctypes.c_int,
@@ -443,6 +447,25 @@ def batch_solve(problems, schedules, opts: Optional[PffOptions] = None, workers:
     lib.pff_batch_solve(n, handles, steps, sp, ctypes.byref(o), rp, int(workers), st)
     return ([[reps[i][k].as_dict() for k in range(len(scheds[i]))] for i in range(n)],
             [st[i] for i in range(n)])
+
+
+def mark_axes(coords, slab_eta2, slab_minphi, theta, h_band, phi_band):
+    """pff_mark_axes: refined axis coordinates from host slab sums and minima (no device)."""
+    lib = load_library()
+    dim = len(coords)
+    xs = [np.ascontiguousarray(c, dtype=np.float64) for c in coords]
+    ss = [np.ascontiguousarray(v, dtype=np.float64) for v in slab_eta2]
+    ms = [np.ascontiguousarray(v, dtype=np.float64) for v in slab_minphi]
+    for x, sv, mv in zip(xs, ss, ms):
+        if sv.size != x.size - 1 or mv.size != x.size - 1:
+            raise ValueError("slab arrays need one value per interval")
+    outs = [np.empty(2 * (x.size - 1) + 1) for x in xs]
+    nc = (ctypes.c_int32 * dim)(*[x.size - 1 for x in xs])
+    arr = lambda lst: (_D * dim)(*[v.ctypes.data_as(_D) for v in lst])  # noqa: E731
+    nout = (ctypes.c_int32 * dim)()
+    _check(lib.pff_mark_axes(dim, nc, arr(xs), arr(ss), arr(ms), float(theta), float(h_band),
+                             float(phi_band), nout, arr(outs)))
+    return [outs[a][:nout[a] + 1].copy() for a in range(dim)]
 
 
 def memory_usage(reset_peak: bool = False):

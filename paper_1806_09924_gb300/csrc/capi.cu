@@ -635,13 +635,64 @@ int pff_cell_indicators_dev(pff_problem* P, double* eta2_dev) {
   API_END
 }
 
+}  // extern "C"
+
+namespace {
+// Marking and splitting of one axis (Section 3 refinement strategy, tensor-product
+// form): interval i is split when its slab sum S[i] is positive and reaches theta
+// times the axis maximum, or when the slab reaches the crack region
+// (minphi[i] < phi_band) while the interval is longer than h_band; a split adds
+// the midpoint when it lies strictly inside.  out holds up to 2 nc + 1 values;
+// returns the new cell count.
+int mark_axis(int nc, const double* x, const double* S, const double* minphi, double theta,
+              double h_band, double phi_band, double* out) {
+  double smax = 0.0;
+  for (int i = 0; i < nc; ++i) smax = std::max(smax, S[i]);
+  int k = 0;
+  for (int i = 0; i < nc; ++i) {
+    out[k++] = x[i];
+    const bool by_eta = smax > 0.0 && S[i] > 0.0 && S[i] >= theta * smax;
+    const bool by_band = minphi[i] < phi_band && x[i + 1] - x[i] > h_band;
+    const double mid = 0.5 * (x[i] + x[i + 1]);
+    if ((by_eta || by_band) && mid > x[i] && mid < x[i + 1]) out[k++] = mid;
+  }
+  out[k++] = x[nc];
+  return k - 1;
+}
+
+void check_refine_args(double theta, double h_band, double phi_band) {
+  need(theta >= 0 && std::isfinite(theta), "theta must be finite and >= 0");
+  need(h_band >= 0 && std::isfinite(h_band), "h_band must be finite and >= 0");
+  need(std::isfinite(phi_band), "phi_band must be finite");
+}
+}  // namespace
+
+extern "C" {
+
+int pff_mark_axes(int dim, const int32_t* n_cells, const double* const* coords,
+                  const double* const* slab_eta2, const double* const* slab_minphi, double theta,
+                  double h_band, double phi_band, int32_t* n_cells_out, double* const* coords_out) {
+  API_BEGIN
+  need(dim == 2 || dim == 3, "dim must be 2 or 3");
+  need(n_cells && coords && slab_eta2 && slab_minphi && n_cells_out && coords_out, "NULL argument");
+  check_refine_args(theta, h_band, phi_band);
+  for (int a = 0; a < dim; ++a) {
+    need(n_cells[a] >= 1, "n_cells must be >= 1");
+    need(coords[a] && slab_eta2[a] && slab_minphi[a] && coords_out[a], "NULL axis array");
+    for (int i = 0; i < n_cells[a]; ++i)
+      need(coords[a][i + 1] > coords[a][i], "axis coordinates must be strictly increasing");
+  }
+  for (int a = 0; a < dim; ++a)
+    n_cells_out[a] = mark_axis(n_cells[a], coords[a], slab_eta2[a], slab_minphi[a], theta, h_band,
+                               phi_band, coords_out[a]);
+  API_END
+}
+
 int pff_refine_axes(pff_problem* P, double theta, double h_band, double phi_band,
                     int32_t* n_cells_out, double* const* coords_out) {
   API_BEGIN
   need(P != nullptr && n_cells_out != nullptr && coords_out != nullptr, "NULL argument");
-  need(theta >= 0 && std::isfinite(theta), "theta must be finite and >= 0");
-  need(h_band >= 0 && std::isfinite(h_band), "h_band must be finite and >= 0");
-  need(std::isfinite(phi_band), "phi_band must be finite");
+  check_refine_args(theta, h_band, phi_band);
   for (int a = 0; a < P->dim; ++a) need(coords_out[a] != nullptr, "coords_out[a] is NULL");
   pff::AllocStream alloc_scope(P->stream);
   const auto m = P->mesh();
@@ -657,28 +708,10 @@ int pff_refine_axes(pff_problem* P, double theta, double h_band, double phi_band
   sync(P);
   pff::dfree(eta2);
   pff::dfree(red);
-  // marking and splitting: an interval is split when its slab sum reaches
-  // theta times the axis maximum (and is positive), or when the slab reaches
-  // the crack region (min phi < phi_band) while the interval is longer than
-  // h_band; a split adds the midpoint when it lies strictly inside
   int off = 0;
   for (int a = 0; a < P->dim; ++a) {
-    const std::vector<double>& x = P->hX[a];
-    const double* S = h.data() + off;
-    const double* mp = h.data() + slabs + off;
-    double smax = 0.0;
-    for (int i = 0; i < P->nc[a]; ++i) smax = std::max(smax, S[i]);
-    int k = 0;
-    double* out = coords_out[a];
-    for (int i = 0; i < P->nc[a]; ++i) {
-      out[k++] = x[i];
-      const bool by_eta = smax > 0.0 && S[i] > 0.0 && S[i] >= theta * smax;
-      const bool by_band = mp[i] < phi_band && x[i + 1] - x[i] > h_band;
-      const double mid = 0.5 * (x[i] + x[i + 1]);
-      if ((by_eta || by_band) && mid > x[i] && mid < x[i + 1]) out[k++] = mid;
-    }
-    out[k++] = x[P->nc[a]];
-    n_cells_out[a] = k - 1;
+    n_cells_out[a] = mark_axis(P->nc[a], P->hX[a].data(), h.data() + off, h.data() + slabs + off,
+                               theta, h_band, phi_band, coords_out[a]);
     off += P->nc[a];
   }
   API_END
