@@ -112,7 +112,9 @@ typedef struct pff_options {
   double forcing_max;   /* > 0: inexact Newton with the Eisenstat-Walker forcing term: the
                            first linear solve of a loading step to forcing_max, later ones to
                            0.9 (rho_k / rho_k-1)^2, never tighter than tol_linear; 0: every
-                           solve to tol_linear (as in Table 1); 0 */
+                           solve to tol_linear (as in Table 1); 0.  Faster (1e-3 halves the
+                           3d penny step), but along the other Newton path the cycle rule
+                           locks other indices and the converged phi can move by ~1e-5 */
   int iter_graph;       /* 1: problems up to 10^6 DoFs on a non-default stream run each
                            FGMRES iteration's preconditioner and Jacobian apply as one CUDA
                            graph (same kernels, same order); 0: ordinary launches; 1 */
